@@ -626,7 +626,10 @@ int orc_solve(orc_hier* H, int order_opt, int n_pre, int n_post, int n_cycles, i
   if (hist) hist[0] = r_init;
   int status = 1, cycles = 0;
   double r_prev = r_init, r_n = r_init, rel = r_zero > 0 ? r_init / r_zero : 0.0;
-  if (r_zero == 0.0) {
+  if (!isfinite(r_zero) || !isfinite(r_init)) {
+    status = 2; /* non-finite data: nothing to iterate on */
+    rel = r_init / r_zero;
+  } else if (r_zero == 0.0) {
     memset(H->phi[0], 0, n * sizeof(double));
     r_n = 0.0;
     rel = 0.0;

@@ -364,6 +364,15 @@ def test_zero_problem_returns_zero(oracle):
     assert st == 0 and info["cycles"] == 0 and (H.get_phi() == 0).all()
 
 
+def test_non_finite_data_is_divergence(oracle):
+    rho = np.ones((4, 4, 4))
+    rho[1, 2, 3] = np.nan
+    H = oracle.Hierarchy(np.ones((4, 4, 4), dtype=np.int8), 0.25)
+    H.set_rhs(rho)
+    st, info = H.solve(1e-8, 10)
+    assert st == 2 and info["cycles"] == 0
+
+
 def test_deepest_levels_ball32(oracle):
     """The r = 0.4 ball at 32^3 has no active cell at 2^3 (second order) and
     no full cell at 4^3 (first order)."""
