@@ -1,0 +1,262 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) masked-domain multigrid Poisson solver.
+ *
+ * Method: Guillet & Teyssier, "A Simple Multigrid Scheme for Solving the
+ * Poisson Equation with Arbitrary Domain Boundaries", arXiv:1104.1703.
+ * The library solves Laplacian(Phi) = rho on the active cells of one AMR
+ * level inside a Cartesian box, with Dirichlet values on the outer faces of
+ * the active domain (Section 2, problem statement; Fig. 1), by multigrid
+ * iterations (Section 2 recipe) with red-black Gauss-Seidel smoothing, R1
+ * restriction and P2 prolongation (Fig. 3), the mask-based second-order
+ * boundary reconstruction (Section 3, Fig. 5), the first-order coarse fix
+ * for sub-cell boundary features (Section 4) and its run-time switch
+ * (Section 4, threshold eta).
+ *
+ * Conventions for every entry point:
+ *  - Grids are cell centred, x fastest: element (i, j, k) of an nx*ny*nz array
+ *    is at index (k*ny + j)*nx + i.  Cell (i,j,k) has its centre at
+ *    ((i+1/2)h, (j+1/2)h, (k+1/2)h).
+ *  - `where` says whether a pointer is host memory (MG_MEM_HOST, any pageable
+ *    or pinned host pointer) or device memory of the hierarchy's GPU
+ *    (MG_MEM_DEVICE).  The caller owns every buffer it passes; the library
+ *    copies what it needs before returning and never keeps a caller pointer.
+ *    All library memory is device memory owned by the hierarchy.
+ *  - Work is issued on the hierarchy's CUDA stream.  Calls that return host
+ *    data (solve, norms, copies to MG_MEM_HOST) synchronise that stream; calls
+ *    that write device data into caller buffers (MG_MEM_DEVICE) are ordered
+ *    on the stream and complete asynchronously.
+ *  - Values at inactive cells are ignored on input and written as 0 on output.
+ *  - Every call returns an mg_status; nothing is thrown across the ABI.  On
+ *    error mg_last_error() describes the failure.  A hierarchy stays usable
+ *    after MG_ERR_NOT_CONVERGED and MG_ERR_DIVERGED; after MG_ERR_CUDA the
+ *    CUDA context may be unusable.
+ *  - One hierarchy must not be used from two host threads at once.
+ */
+#ifndef GBMG_MG_H
+#define GBMG_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_hierarchy mg_hierarchy; /* opaque, library-owned */
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or level index */
+  MG_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  MG_ERR_OOM = 3,           /* device allocation failed; nothing leaked */
+  MG_ERR_EMPTY_DOMAIN = 4,  /* the mask has no active cell */
+  MG_ERR_NOT_CONVERGED = 5, /* max_cycles reached above the tolerance */
+  MG_ERR_DIVERGED = 6,      /* a residual norm became non-finite */
+  MG_ERR_INTERNAL = 7
+} mg_status;
+
+typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
+
+/* Parameters of the multigrid iteration.
+ *  n_pre, n_post   Gauss-Seidel sweeps before and after the coarse correction
+ *                  (Section 2, recipe steps 1 and 8; the paper uses 2 and 2).
+ *  n_cycles        coarse iterations per level: 1 = V-cycle, 2 = W-cycle
+ *                  (Section 5.3, N_cycles).
+ *  coarse_sweeps   red-black sweeps on the deepest level that has an active
+ *                  cell (the paper does not specify the coarsest solve).
+ *  order           0 = automatic switch (start in second order, Section 4),
+ *                  1 = always first order on coarse levels, 2 = always second.
+ *  eta             switch threshold on ||r_{n+1}|| / ||r_n|| (Section 4; 0.5).
+ *  hold_solves     solves that stay in first order after a switch
+ *                  (Section 4: "for the next 10 solves").
+ *  use_graphs      1 = replay each V-cycle from a captured CUDA graph. */
+typedef struct {
+  int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
+  double eta;
+  int order;
+  int use_graphs;
+} mg_options;
+
+#define MG_HIST_MAX 256
+
+/* Result of mg_solve.  hist[n] = ||r_n|| for n = 0..min(cycles, MG_HIST_MAX)
+ * with r_0 the residual of the initial guess; r_zero = ||r(Phi = 0)|| is the
+ * reference of the relative residual rel = ||r_final|| / r_zero.  Norms are
+ * unscaled L2 norms of r = Laplacian(Phi) - rho over the active fine cells. */
+typedef struct {
+  int cycles;     /* multigrid iterations performed */
+  int order_used; /* coarse reconstruction order at exit (1 or 2) */
+  int switched;   /* 1 if this solve switched from second to first order */
+  int status;     /* the mg_status returned by mg_solve */
+  long long cell_updates; /* Gauss-Seidel updates of active cells, all levels */
+  double r_zero, r_init, r_final, rel;
+  double hist[MG_HIST_MAX + 1];
+} mg_solve_info;
+
+/* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
+ * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1. */
+void mg_default_options(mg_options* opt);
+
+/* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):
+ * levels of size ceil(n/2) down to at most 2 cells per axis, the mask
+ * averaged recursively (Section 3; kept as exact integer sums of the +1/-1
+ * colours), the per-level active sets of both reconstruction orders and the
+ * modified-Laplacian diagonals (Sections 3 and 4).
+ *  mask         nx*ny*nz int8: > 0 active, <= 0 inactive (Omega = {m > 0}).
+ *  nx, ny, nz   1..2048 each.
+ *  h            fine cell size, > 0.
+ *  opt          NULL for mg_default_options.
+ *  cuda_stream  a cudaStream_t of the current device, or NULL for a stream
+ *               the library creates (and destroys with the hierarchy); that
+ *               stream synchronises with the legacy default stream.
+ *  out          receives the new hierarchy (NULL on failure).
+ * The solution starts at 0, rho at 0 and the Dirichlet values at 0.
+ * Errors: INVALID_ARG, EMPTY_DOMAIN (no active cell), OOM, CUDA. */
+mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, int nz, double h,
+                              const mg_options* opt, void* cuda_stream, mg_hierarchy** out);
+
+/* Rebuilds the mask hierarchy for a new mask of the same dimensions without
+ * reallocating (the AMR level changed shape).  The solution is reset to 0
+ * and the right-hand side and Dirichlet values must be set again.
+ * Errors: INVALID_ARG, EMPTY_DOMAIN (the previous mask stays in force), CUDA. */
+mg_status mg_update_mask(mg_hierarchy* hier, const int8_t* mask, mg_mem where);
+
+/* Releases every device buffer, graph and (if library-created) the stream.
+ * NULL is accepted. */
+mg_status mg_destroy_hierarchy(mg_hierarchy* hier);
+
+/* rho: nx*ny*nz doubles, the right-hand side of Laplacian(Phi) = rho
+ * (Section 1, Poisson equation).  Errors: INVALID_ARG, CUDA. */
+mg_status mg_set_rhs(mg_hierarchy* hier, const double* rho, mg_mem where);
+
+/* Dirichlet values on the faces of the fine level (Fig. 1: the boundary
+ * conditions live at the border cell faces).
+ *  bx  (nx+1)*ny*nz: value on the x-face between cells (i-1,j,k) and (i,j,k),
+ *      at index (k*ny + j)*(nx+1) + i, centred at (i h, (j+1/2) h, (k+1/2) h);
+ *  by  nx*(ny+1)*nz, index (k*(ny+1) + j)*nx + i;  bz nx*ny*(nz+1), index
+ *      (k*ny + j)*nx + i with k in 0..nz.
+ * Only faces between an active cell and an inactive or out-of-box cell are
+ * read.  A NULL array means 0 on that face family.
+ * Errors: INVALID_ARG, CUDA. */
+mg_status mg_set_dirichlet(mg_hierarchy* hier, const double* bx, const double* by, const double* bz,
+                           mg_mem where);
+
+/* One-way interface (Section 1; Fig. 1 caption): the Dirichlet values are
+ * linearly (trilinearly) interpolated, at each boundary face centre, from
+ * the solution of the coarser AMR level.
+ *  phi_c        cnx*cny*cnz doubles, the coarse-level potential, cell size 2h.
+ *  ox, oy, oz   lower corner of coarse cell (0,0,0) in fine-cell units: the
+ *               coarse cell (I,J,K) spans [ox+2I, ox+2I+2] x ... so its
+ *               centre is at ox+2I+1.  Typical: -2 (one coarse ghost cell).
+ * Errors: INVALID_ARG (including a boundary face outside the coarse centres),
+ * CUDA. */
+mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* hier, const double* phi_c, mg_mem where, int cnx,
+                                       int cny, int cnz, int ox, int oy, int oz);
+
+/* Initial guess (NULL = 0) and read-back of the fine solution, nx*ny*nz.
+ * Errors: INVALID_ARG, CUDA. */
+mg_status mg_set_solution(mg_hierarchy* hier, const double* phi, mg_mem where);
+mg_status mg_get_solution(mg_hierarchy* hier, double* phi, mg_mem where);
+
+/* One multigrid iteration (Section 2 recipe, applied recursively N_cycles
+ * times per level) in the current order (option order 1 or 2; for order 0,
+ * first order while the hold counter is positive, else second order).  No
+ * order switching happens here.  rel_residual_out (nullable) receives
+ * ||r|| / ||r(Phi = 0)|| after the iteration; passing NULL keeps the call
+ * asynchronous.  Errors: CUDA, DIVERGED (non-finite norm). */
+mg_status mg_vcycle(mg_hierarchy* hier, double* rel_residual_out);
+
+/* Iterates until ||r_n|| / ||r(Phi = 0)|| < tol (relative residual, Section
+ * 5.2 measures the reduction from a zero first guess), with the run-time
+ * order switch of Section 4 when option order = 0: a solve starts in second
+ * order unless the hold counter is positive (then first order, counter - 1);
+ * when ||r_n|| / ||r_{n-1}|| > eta it switches to first order for the rest of
+ * the solve and for the next hold_solves solves.  On a switch the iterate is
+ * kept unless its residual exceeds the initial one, in which case the
+ * initial guess is restored.  The ratio test is skipped once ||r_n|| <
+ * 100 * DBL_EPSILON * ||r(0)||.  If rho and the Dirichlet values are all 0 the
+ * solution is set to 0 and the call returns at once.
+ *  tol > 0, max_cycles >= 0; info nullable.
+ * Errors: INVALID_ARG, NOT_CONVERGED (the best iterate is kept), DIVERGED,
+ * CUDA. */
+mg_status mg_solve(mg_hierarchy* hier, double tol, int max_cycles, mg_solve_info* info);
+
+/* ||r|| and ||r(Phi = 0)|| (unscaled L2 over the active fine cells) for the
+ * current solution.  Either output may be NULL.  Errors: CUDA. */
+mg_status mg_residual_norm(mg_hierarchy* hier, double* norm_out, double* norm_zero_out);
+
+/* Order-switch state: solves left in forced first order. */
+mg_status mg_get_hold(const mg_hierarchy* hier, int* hold);
+mg_status mg_set_hold(mg_hierarchy* hier, int hold);
+
+/* Message of the last failed call on this hierarchy, or of the last failed
+ * create on this thread when hier is NULL.  Never NULL. */
+const char* mg_last_error(const mg_hierarchy* hier);
+const char* mg_status_string(mg_status status);
+
+/* ---------------------------------------------------------------------------
+ * Level access.  These expose the individual steps of the Section 2 recipe
+ * on one level of the hierarchy, for verification and for callers that
+ * drive their own schedule.  Level 0 is the fine level.
+ * ------------------------------------------------------------------------- */
+
+/* Number of levels built, and the deepest level with an active cell in
+ * second (deepest2) and first (deepest1) order.  Any output may be NULL. */
+mg_status mg_num_levels(const mg_hierarchy* hier, int* nlev, int* deepest2, int* deepest1);
+
+/* dims3 receives {nx, ny, nz} of the level; active2/active1 the number of
+ * unknowns in second and first order (Omega^l = {m > 0}, Section 3; cells
+ * with m = 1, Section 4).  Outputs nullable. */
+mg_status mg_level_info(const mg_hierarchy* hier, int level, int* dims3, long long* active2,
+                        long long* active1);
+
+/* Fields of a level, in natural x-fastest layout of the level's dimensions:
+ *  MG_FIELD_PHI     double  level 0: Phi; level >= 1: the correction dPhi
+ *  MG_FIELD_RHS     double  the right-hand side scaled by the level's cell
+ *                           size squared: level 0 h^2 rho minus the folded
+ *                           Dirichlet terms, level l >= 1 h_l^2 times the
+ *                           coarse right-hand side -R(r)
+ *  MG_FIELD_MASKSUM int32   sum of the +1/-1 fine colours under each cell
+ *                           (m_l = S / 8^l; Section 3)
+ *  MG_FIELD_INVDIAG double  1 / D of the second-order operator, D the sum
+ *                           over the six faces of 1 (active neighbour) or
+ *                           1/theta (ghost) (Section 3), 0 on inactive cells
+ * mg_level_set accepts MG_FIELD_PHI and MG_FIELD_RHS only. */
+enum { MG_FIELD_PHI = 0, MG_FIELD_RHS = 1, MG_FIELD_MASKSUM = 2, MG_FIELD_INVDIAG = 3 };
+mg_status mg_level_get(mg_hierarchy* hier, int level, int field, void* out, mg_mem where);
+mg_status mg_level_set(mg_hierarchy* hier, int level, int field, const void* in, mg_mem where);
+
+/* Recipe step 1/8 on one level: `sweeps` red-black Gauss-Seidel sweeps
+ * (red = (i+j+k) even first) in the given order (1 or 2).  Inactive cells
+ * are not touched.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_level_smooth(mg_hierarchy* hier, int level, int order, int sweeps);
+
+/* Recipe steps 2-5 on one level: the residual of level `level` is restricted
+ * by R1 into the right-hand side of level+1 (as -R(r)) and the correction of
+ * level+1 is zeroed.  The residual is taken at every active cell.
+ * Errors: INVALID_ARG (no coarser level), CUDA. */
+mg_status mg_level_restrict(mg_hierarchy* hier, int level, int order);
+
+/* Recipe steps 6-7 on one level: Phi_level += P2(dPhi_{level+1}) on the
+ * active cells of `level` in the given order.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_level_prolong(mg_hierarchy* hier, int level, int order);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation
+ * ------------------------------------------------------------------------- */
+
+/* Number of kernels this library has launched in the process (a graph
+ * replay counts each of its kernel nodes). */
+unsigned long long mg_launch_count(void);
+
+/* Kernel timing: when enabled, every launch of the fine-level (level 0)
+ * Gauss-Seidel half-sweep kernel issued outside a graph is bracketed by CUDA
+ * events on the hierarchy's stream.  mg_timing_read synchronises the stream
+ * and returns the number of timed launches and their total time in ms, then
+ * resets the accumulators.  Errors: CUDA. */
+mg_status mg_timing_enable(mg_hierarchy* hier, int enable);
+mg_status mg_timing_read(mg_hierarchy* hier, long long* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMG_MG_H */

@@ -1,0 +1,394 @@
+"""ctypes binding of the C ABI declared in include/mg.h.
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in libgbmg.so (built by ``paper_1104_1703_gb300.build``).  Arrays
+may be torch tensors (CUDA tensors are passed as device pointers) or numpy
+arrays (host pointers), indexed [k, j, i] with x fastest.  There is no CPU
+path: if the CUDA library cannot be built or loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_EMPTY_DOMAIN = 0, 1, 2, 3, 4
+MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, MG_ERR_INTERNAL = 5, 6, 7
+MG_MEM_HOST, MG_MEM_DEVICE = 0, 1
+MG_FIELD_PHI, MG_FIELD_RHS, MG_FIELD_MASKSUM, MG_FIELD_INVDIAG = 0, 1, 2, 3
+MG_HIST_MAX = 256
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+class MGOptions(ctypes.Structure):
+    _fields_ = [("n_pre", _i), ("n_post", _i), ("n_cycles", _i), ("coarse_sweeps", _i), ("hold_solves", _i),
+                ("eta", _d), ("order", _i), ("use_graphs", _i)]
+
+
+class MGSolveInfo(ctypes.Structure):
+    _fields_ = [("cycles", _i), ("order_used", _i), ("switched", _i), ("status", _i),
+                ("cell_updates", ctypes.c_longlong), ("r_zero", _d),
+                ("r_init", _d), ("r_final", _d), ("rel", _d), ("hist", _d * (MG_HIST_MAX + 1))]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (status %d)" % (message, status))
+        self.status = status
+        self.message = message
+
+
+# name -> (restype, argtypes); the exported symbols of include/mg.h
+SIGNATURES = {
+    "mg_default_options": (None, [_vp]),
+    "mg_create_hierarchy": (_i, [_vp, _i, _i, _i, _i, _d, _vp, _vp, _vp]),
+    "mg_update_mask": (_i, [_vp, _vp, _i]),
+    "mg_destroy_hierarchy": (_i, [_vp]),
+    "mg_set_rhs": (_i, [_vp, _vp, _i]),
+    "mg_set_dirichlet": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "mg_set_dirichlet_from_coarse": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i]),
+    "mg_set_solution": (_i, [_vp, _vp, _i]),
+    "mg_get_solution": (_i, [_vp, _vp, _i]),
+    "mg_vcycle": (_i, [_vp, _vp]),
+    "mg_solve": (_i, [_vp, _d, _i, _vp]),
+    "mg_residual_norm": (_i, [_vp, _vp, _vp]),
+    "mg_get_hold": (_i, [_vp, _vp]),
+    "mg_set_hold": (_i, [_vp, _i]),
+    "mg_last_error": (ctypes.c_char_p, [_vp]),
+    "mg_status_string": (ctypes.c_char_p, [_i]),
+    "mg_num_levels": (_i, [_vp, _vp, _vp, _vp]),
+    "mg_level_info": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "mg_level_get": (_i, [_vp, _i, _i, _vp, _i]),
+    "mg_level_set": (_i, [_vp, _i, _i, _vp, _i]),
+    "mg_level_smooth": (_i, [_vp, _i, _i, _i]),
+    "mg_level_restrict": (_i, [_vp, _i, _i]),
+    "mg_level_prolong": (_i, [_vp, _i, _i]),
+    "mg_launch_count": (ctypes.c_ulonglong, []),
+    "mg_timing_enable": (_i, [_vp, _i]),
+    "mg_timing_read": (_i, [_vp, _vp, _vp]),
+}
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libgbmg.so, building it first if it is missing or stale."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(st, h=None):
+    if st != MG_OK:
+        raise MGError(st, mg_last_error(h))
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _in(a, dtype, shape, name):
+    """(pointer, where, keepalive) for an input array."""
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int8: torch.int8, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError("%s: expected a contiguous %s tensor of shape %s" % (name, tdt, shape))
+        return _vp(a.data_ptr()), (MG_MEM_DEVICE if a.is_cuda else MG_MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.shape != tuple(shape):
+        raise ValueError("%s: expected shape %s, got %s" % (name, tuple(shape), arr.shape))
+    return arr.ctypes.data_as(_vp), MG_MEM_HOST, arr
+
+
+def _out(a, dtype, shape, name):
+    if a is None:
+        a = np.zeros(shape, dtype=dtype)
+    if _is_torch(a):
+        return _in(a, dtype, shape, name)[:2] + (a,)
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous and a.shape == tuple(shape)):
+        raise ValueError("%s: expected a contiguous %s array of shape %s" % (name, np.dtype(dtype), shape))
+    return a.ctypes.data_as(_vp), MG_MEM_HOST, a
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            s = torch.cuda.current_stream().cuda_stream
+            return _vp(s) if s else None
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+
+def mg_default_options() -> MGOptions:
+    o = MGOptions()
+    lib().mg_default_options(ctypes.byref(o))
+    return o
+
+
+def mg_last_error(h=None) -> str:
+    return lib().mg_last_error(h).decode()
+
+
+def mg_status_string(st) -> str:
+    return lib().mg_status_string(st).decode()
+
+
+def mg_create_hierarchy(mask, h, options=None, stream="auto"):
+    """Returns an opaque handle; dims are taken from mask.shape = (nz, ny, nx)."""
+    nz, ny, nx = mask.shape
+    p, where, keep = _in(mask, np.int8, (nz, ny, nx), "mask")
+    if stream == "auto":
+        stream = _default_stream()
+    out = _vp()
+    st = lib().mg_create_hierarchy(p, where, nx, ny, nz, float(h),
+                                   ctypes.byref(options) if options is not None else None, stream, ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def mg_destroy_hierarchy(h):
+    _check(lib().mg_destroy_hierarchy(h))
+
+
+def mg_update_mask(h, mask):
+    p, where, keep = _in(mask, np.int8, mask.shape, "mask")
+    _check(lib().mg_update_mask(h, p, where), h)
+
+
+def mg_set_rhs(h, rho):
+    p, where, keep = _in(rho, np.float64, rho.shape, "rho")
+    _check(lib().mg_set_rhs(h, p, where), h)
+
+
+def mg_set_dirichlet(h, bx=None, by=None, bz=None):
+    ptrs, keeps, wheres = [], [], set()
+    for name, a in (("bx", bx), ("by", by), ("bz", bz)):
+        if a is None:
+            ptrs.append(None)
+            continue
+        p, where, keep = _in(a, np.float64, a.shape, name)
+        ptrs.append(p)
+        keeps.append(keep)
+        wheres.add(where)
+    if len(wheres) > 1:
+        raise ValueError("face arrays must all be host or all be device arrays")
+    where = wheres.pop() if wheres else MG_MEM_HOST
+    _check(lib().mg_set_dirichlet(h, ptrs[0], ptrs[1], ptrs[2], where), h)
+
+
+def mg_set_dirichlet_from_coarse(h, phi_c, origin):
+    cz, cy, cx = phi_c.shape
+    p, where, keep = _in(phi_c, np.float64, (cz, cy, cx), "phi_c")
+    _check(lib().mg_set_dirichlet_from_coarse(h, p, where, cx, cy, cz, int(origin[0]), int(origin[1]),
+                                              int(origin[2])), h)
+
+
+def mg_set_solution(h, phi=None):
+    if phi is None:
+        _check(lib().mg_set_solution(h, None, MG_MEM_HOST), h)
+        return
+    p, where, keep = _in(phi, np.float64, phi.shape, "phi")
+    _check(lib().mg_set_solution(h, p, where), h)
+
+
+def mg_get_solution(h, shape, out=None):
+    p, where, keep = _out(out, np.float64, shape, "out")
+    _check(lib().mg_get_solution(h, p, where), h)
+    return keep
+
+
+def mg_vcycle(h, want_rel=True):
+    rel = _d()
+    _check(lib().mg_vcycle(h, ctypes.byref(rel) if want_rel else None), h)
+    return rel.value if want_rel else None
+
+
+def mg_solve(h, tol, max_cycles=100, raise_on_failure=False):
+    """Returns (status, info dict); raises MGError for argument and CUDA
+    errors, and for NOT_CONVERGED / DIVERGED only if raise_on_failure."""
+    info = MGSolveInfo()
+    st = lib().mg_solve(h, float(tol), int(max_cycles), ctypes.byref(info))
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED) or (raise_on_failure and st != MG_OK):
+        _check(st, h)
+    n = min(info.cycles, MG_HIST_MAX)
+    return st, {"cycles": info.cycles, "order": info.order_used, "switched": info.switched,
+                "cell_updates": info.cell_updates,
+                "r_zero": info.r_zero, "r_init": info.r_init, "r_final": info.r_final, "rel": info.rel,
+                "hist": np.array(info.hist[: n + 1])}
+
+
+def mg_residual_norm(h):
+    r, r0 = _d(), _d()
+    _check(lib().mg_residual_norm(h, ctypes.byref(r), ctypes.byref(r0)), h)
+    return r.value, r0.value
+
+
+def mg_get_hold(h):
+    v = _i()
+    _check(lib().mg_get_hold(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def mg_set_hold(h, hold):
+    _check(lib().mg_set_hold(h, int(hold)), h)
+
+
+def mg_num_levels(h):
+    n, d2, d1 = _i(), _i(), _i()
+    _check(lib().mg_num_levels(h, ctypes.byref(n), ctypes.byref(d2), ctypes.byref(d1)), h)
+    return n.value, d2.value, d1.value
+
+
+def mg_level_info(h, level):
+    dims = (_i * 3)()
+    a2, a1 = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().mg_level_info(h, level, dims, ctypes.byref(a2), ctypes.byref(a1)), h)
+    return (dims[2], dims[1], dims[0]), a2.value, a1.value
+
+
+def mg_level_get(h, level, field, out=None):
+    shape = mg_level_info(h, level)[0]
+    dtype = np.int32 if field == MG_FIELD_MASKSUM else np.float64
+    p, where, keep = _out(out, dtype, shape, "out")
+    _check(lib().mg_level_get(h, level, field, p, where), h)
+    return keep
+
+
+def mg_level_set(h, level, field, arr):
+    shape = mg_level_info(h, level)[0]
+    p, where, keep = _in(arr, np.float64, shape, "arr")
+    _check(lib().mg_level_set(h, level, field, p, where), h)
+
+
+def mg_level_smooth(h, level, order, sweeps):
+    _check(lib().mg_level_smooth(h, level, order, sweeps), h)
+
+
+def mg_level_restrict(h, level, order):
+    _check(lib().mg_level_restrict(h, level, order), h)
+
+
+def mg_level_prolong(h, level, order):
+    _check(lib().mg_level_prolong(h, level, order), h)
+
+
+def mg_launch_count() -> int:
+    return int(lib().mg_launch_count())
+
+
+def mg_timing_enable(h, enable=True):
+    _check(lib().mg_timing_enable(h, 1 if enable else 0), h)
+
+
+def mg_timing_read(h):
+    n, ms = ctypes.c_longlong(), _d()
+    _check(lib().mg_timing_read(h, ctypes.byref(n), ctypes.byref(ms)), h)
+    return n.value, ms.value
+
+
+class Hierarchy:
+    """Owns one handle; methods forward to the functions above."""
+
+    def __init__(self, mask, h, options=None, stream="auto", **opts):
+        if options is None and opts:
+            options = mg_default_options()
+            for k, v in opts.items():
+                setattr(options, k, v)
+        self.shape = tuple(mask.shape)
+        self.h = float(h)
+        self.handle = mg_create_hierarchy(mask, h, options, stream)
+
+    def close(self):
+        if self.handle:
+            mg_destroy_hierarchy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_rhs(self, rho):
+        mg_set_rhs(self.handle, rho)
+
+    def set_dirichlet(self, bx=None, by=None, bz=None):
+        mg_set_dirichlet(self.handle, bx, by, bz)
+
+    def set_dirichlet_from_coarse(self, phi_c, origin):
+        mg_set_dirichlet_from_coarse(self.handle, phi_c, origin)
+
+    def set_solution(self, phi=None):
+        mg_set_solution(self.handle, phi)
+
+    def get_solution(self, out=None):
+        return mg_get_solution(self.handle, self.shape, out)
+
+    def update_mask(self, mask):
+        mg_update_mask(self.handle, mask)
+
+    def vcycle(self, want_rel=True):
+        return mg_vcycle(self.handle, want_rel)
+
+    def solve(self, tol, max_cycles=100):
+        return mg_solve(self.handle, tol, max_cycles)
+
+    def residual_norm(self):
+        return mg_residual_norm(self.handle)
+
+    @property
+    def hold(self):
+        return mg_get_hold(self.handle)
+
+    @hold.setter
+    def hold(self, v):
+        mg_set_hold(self.handle, v)
+
+    def levels(self):
+        return mg_num_levels(self.handle)
+
+    def level_info(self, level):
+        return mg_level_info(self.handle, level)
+
+    def level_get(self, level, field, out=None):
+        return mg_level_get(self.handle, level, field, out)
+
+    def level_set(self, level, field, arr):
+        mg_level_set(self.handle, level, field, arr)
+
+    def smooth(self, level, order, sweeps):
+        mg_level_smooth(self.handle, level, order, sweeps)
+
+    def restrict_to(self, level, order):
+        mg_level_restrict(self.handle, level, order)
+
+    def prolong_from(self, level, order):
+        mg_level_prolong(self.handle, level, order)

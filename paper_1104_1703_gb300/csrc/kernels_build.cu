@@ -1,0 +1,346 @@
+// Hierarchy construction, layout conversion and boundary-data kernels.
+//
+// Guillet & Teyssier, arXiv:1104.1703:
+//  - Section 3: the mask is +1 on active and -1 on inactive fine cells and is
+//    averaged (R1) level by level; Omega^l = {m^l > 0}.  We keep the exact
+//    integer sums S_l (m_l = S_l / 8^l).
+//  - Section 3, Fig. 5: across a boundary the neighbour value is replaced by
+//    a ghost extrapolated through Phi_b at distance theta = m_i / (m_i - m_j).
+//    Solving a cell's row for Phi_i turns each ghost face into a diagonal
+//    contribution 1/theta and a right-hand-side contribution Phi_b/theta.
+//    At level 0 theta = 1/2 (the boundary is on the face); at coarse levels
+//    Phi_b = 0, so only the diagonal changes.
+//  - Section 4: first-order coarse levels keep as unknowns only the cells
+//    with m = 1 (S = 8^l); every other cell holds 0, so D = 6.
+//  - Section 1 / Fig. 1: the fine Dirichlet values sit on the boundary faces
+//    and come from the coarser AMR level by linear interpolation.
+#include "mg_internal.h"
+
+namespace gbmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int colour_of(int i, int j, int k) { return (i + j + k) & 1; }
+
+__device__ __forceinline__ void natural_coords(long long idx, int nx, int ny, int& i, int& j, int& k) {
+  i = (int)(idx % nx);
+  long long t = idx / nx;
+  j = (int)(t % ny);
+  k = (int)(t / ny);
+}
+
+__device__ __forceinline__ long long pow8(int l) { return 1LL << (3 * l); }
+
+// Warp-aggregated increment of a 64-bit counter.
+__device__ __forceinline__ void count_add(unsigned long long* ctr, bool pred) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+// Level 0: code byte (active bits and ghost-face flags) from the int8 mask,
+// and the active-cell count.
+__global__ void build_fine_kernel(LevelDev L, const int8_t* __restrict__ mask, unsigned long long* counts2) {
+  const Geom g = L.g;
+  const long long n = g.ncells();
+  const int lane = threadIdx.x & 31;
+  // the trip count is uniform across each warp (blockDim is a multiple of 32),
+  // so every lane reaches the __ballot_sync in count_add
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx - lane < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    bool act = false;
+    if (idx < n) {
+      int i, j, k;
+      natural_coords(idx, g.nx, g.ny, i, j, k);
+      act = mask[idx] > 0;
+      uint8_t code = 0;
+      if (act) {
+        code = kActive2 | kActive1;
+        const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+        bool nb[6] = {i > 0 && mask[idx - 1] > 0, i + 1 < g.nx && mask[idx + 1] > 0,
+                      j > 0 && mask[idx - sy] > 0, j + 1 < g.ny && mask[idx + sy] > 0,
+                      k > 0 && mask[idx - sz] > 0, k + 1 < g.nz && mask[idx + sz] > 0};
+        for (int d = 0; d < 6; ++d)
+          if (!nb[d]) code |= (uint8_t)(1u << (kGhostShift + d));
+      }
+      L.code[colour_of(i, j, k)][g.at(i >> 1, j, k)] = code;
+    }
+    count_add(&counts2[0], act);
+  }
+}
+
+// K1: S_c = sum of the 8 children (missing children of an odd dimension are
+// outside the box: -8^l each).  Level 0 children are read from the mask.
+__global__ void mask_coarsen_kernel(Geom gf, int level_f, const int8_t* __restrict__ mask,
+                                    const int32_t* __restrict__ Sf, Geom gc, int32_t* __restrict__ Sc) {
+  const long long n = gc.ncells();
+  const int out_val = -(int)pow8(level_f);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int I, J, K;
+    natural_coords(idx, gc.nx, gc.ny, I, J, K);
+    int sum = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+      if (i < gf.nx && j < gf.ny && k < gf.nz) {
+        long long f = ((long long)k * gf.ny + j) * gf.nx + i;
+        sum += mask ? (mask[f] > 0 ? 1 : -1) : Sf[f];
+      } else {
+        sum += out_val;
+      }
+    }
+    Sc[idx] = sum;
+  }
+}
+
+// K2 for a coarse level: active bits, D and 1/D of the second-order operator.
+// D = sum over faces of 1 (active neighbour) or 1/theta = (S_i - S_j)/S_i
+// (inactive or out-of-box neighbour, S_j = -8^l), computed exactly in integer
+// form D = N / S_i, so 1/D = S_i / N and D = N / S_i each round once.
+__global__ void coarse_coeffs_kernel(LevelDev L, unsigned long long* counts2) {
+  const Geom g = L.g;
+  const long long n = g.ncells();
+  const long long p8 = pow8(L.level);
+  const int lane = threadIdx.x & 31;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx - lane < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    bool a2 = false, a1 = false;
+    if (idx < n) {
+      int i, j, k;
+      natural_coords(idx, g.nx, g.ny, i, j, k);
+      const long long Si = L.S[idx];
+      a2 = Si > 0;
+      a1 = Si == p8;
+      uint8_t code = (a2 ? kActive2 : 0) | (a1 ? kActive1 : 0);
+      double invd = 0.0, diag = 0.0;
+      if (a2) {
+        const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+        long long Sj[6] = {i > 0 ? L.S[idx - 1] : -p8, i + 1 < g.nx ? L.S[idx + 1] : -p8,
+                           j > 0 ? L.S[idx - sy] : -p8, j + 1 < g.ny ? L.S[idx + sy] : -p8,
+                           k > 0 ? L.S[idx - sz] : -p8, k + 1 < g.nz ? L.S[idx + sz] : -p8};
+        long long N = 0;
+        for (int d = 0; d < 6; ++d) N += Sj[d] > 0 ? Si : Si - Sj[d];
+        invd = (double)Si / (double)N;
+        diag = (double)N / (double)Si;
+      }
+      const int c = colour_of(i, j, k);
+      const long long at = g.at(i >> 1, j, k);
+      L.code[c][at] = code;
+      L.invd[c][at] = invd;
+      L.diag[c][at] = diag;
+    }
+    count_add(&counts2[0], a2);
+    count_add(&counts2[1], a1);
+  }
+}
+
+__global__ void natural_to_split_kernel(Geom g, const double* __restrict__ nat, double* dst0, double* dst1,
+                                        double scale, const uint8_t* code0, const uint8_t* code1,
+                                        uint8_t mask_bit) {
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const int c = colour_of(i, j, k);
+    const long long at = g.at(i >> 1, j, k);
+    bool keep = true;
+    if (mask_bit) keep = ((c ? code1 : code0)[at] & mask_bit) != 0;
+    (c ? dst1 : dst0)[at] = keep ? scale * nat[idx] : 0.0;
+  }
+}
+
+__global__ void split_to_natural_kernel(Geom g, const double* __restrict__ s0, const double* __restrict__ s1,
+                                        double* __restrict__ nat) {
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    nat[idx] = (colour_of(i, j, k) ? s1 : s0)[g.at(i >> 1, j, k)];
+  }
+}
+
+__global__ void code_bits_to_natural_kernel(Geom g, const uint8_t* c0, const uint8_t* c1, int32_t* nat,
+                                            uint8_t bit) {
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    nat[idx] = ((colour_of(i, j, k) ? c1 : c0)[g.at(i >> 1, j, k)] & bit) ? 1 : -1;
+  }
+}
+
+// K3 (face form): bc = 2 * sum of Phi_b over the ghost faces of each active
+// fine cell (theta = 1/2 at level 0, so Phi_b/theta = 2 Phi_b).
+__global__ void fold_faces_kernel(LevelDev L, FineExtra F, const double* __restrict__ bx,
+                                  const double* __restrict__ by, const double* __restrict__ bz) {
+  const Geom g = L.g;
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const int c = colour_of(i, j, k);
+    const long long at = g.at(i >> 1, j, k);
+    const uint8_t code = L.code[c][at];
+    double acc = 0.0;
+    if (code & kActive2) {
+      const int gh = code >> kGhostShift;
+      const long long fx = ((long long)k * g.ny + j) * (g.nx + 1) + i;
+      const long long fy = ((long long)k * (g.ny + 1) + j) * g.nx + i;
+      const long long fz = ((long long)k * g.ny + j) * g.nx + i;
+      const long long nxy = (long long)g.nx * g.ny;
+      if ((gh & 1) && bx) acc += bx[fx];
+      if ((gh & 2) && bx) acc += bx[fx + 1];
+      if ((gh & 4) && by) acc += by[fy];
+      if ((gh & 8) && by) acc += by[fy + g.nx];
+      if ((gh & 16) && bz) acc += bz[fz];
+      if ((gh & 32) && bz) acc += bz[fz + nxy];
+    }
+    F.bc[c][at] = 2.0 * acc;
+  }
+}
+
+// Trilinear interpolation of the coarse AMR potential at a point given in
+// fine-cell units; coarse cell (I,J,K) is centred at o + 2I + 1.
+__device__ __forceinline__ bool coarse_sample(const double* __restrict__ pc, int cnx, int cny, int cnz, int ox,
+                                              int oy, int oz, double px, double py, double pz, double& out) {
+  const double u = (px - ox) * 0.5 - 0.5, v = (py - oy) * 0.5 - 0.5, w = (pz - oz) * 0.5 - 0.5;
+  const double fu = floor(u), fv = floor(v), fw = floor(w);
+  const int I = (int)fu, J = (int)fv, K = (int)fw;
+  if (I < 0 || J < 0 || K < 0 || I + 1 >= cnx || J + 1 >= cny || K + 1 >= cnz) return false;
+  const double tu = u - fu, tv = v - fv, tw = w - fw;
+  const long long sy = cnx, sz = (long long)cnx * cny;
+  const double* p = pc + K * sz + (long long)J * sy + I;
+  const double c00 = (1.0 - tu) * p[0] + tu * p[1];
+  const double c10 = (1.0 - tu) * p[sy] + tu * p[sy + 1];
+  const double c01 = (1.0 - tu) * p[sz] + tu * p[sz + 1];
+  const double c11 = (1.0 - tu) * p[sz + sy] + tu * p[sz + sy + 1];
+  const double c0 = (1.0 - tv) * c00 + tv * c10;
+  const double c1 = (1.0 - tv) * c01 + tv * c11;
+  out = (1.0 - tw) * c0 + tw * c1;
+  return true;
+}
+
+// K7 + K3: Dirichlet values interpolated from the coarser AMR level at the
+// centre of each ghost face, folded into bc.
+__global__ void fold_coarse_kernel(LevelDev L, FineExtra F, const double* __restrict__ pc, int cnx, int cny,
+                                   int cnz, int ox, int oy, int oz, int* err_flag) {
+  const Geom g = L.g;
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const int c = colour_of(i, j, k);
+    const long long at = g.at(i >> 1, j, k);
+    const uint8_t code = L.code[c][at];
+    double acc = 0.0;
+    if (code & kActive2) {
+      const int gh = code >> kGhostShift;
+      const double x = i + 0.5, y = j + 0.5, z = k + 0.5;
+      const double fx[6] = {(double)i, (double)(i + 1), x, x, x, x};
+      const double fy[6] = {y, y, (double)j, (double)(j + 1), y, y};
+      const double fz[6] = {z, z, z, z, (double)k, (double)(k + 1)};
+      for (int d = 0; d < 6; ++d) {
+        if (!(gh & (1 << d))) continue;
+        double v;
+        if (coarse_sample(pc, cnx, cny, cnz, ox, oy, oz, fx[d], fy[d], fz[d], v))
+          acc += v;
+        else
+          atomicExch(err_flag, 1);
+      }
+    }
+    F.bc[c][at] = 2.0 * acc;
+  }
+}
+
+// b = h^2 rho - bc over whole colour arrays (halo and padding stay 0).
+__global__ void combine_rhs_kernel(long long total, const double* __restrict__ r0, const double* __restrict__ r1,
+                                   const double* __restrict__ b0, const double* __restrict__ b1, double* __restrict__ o0,
+                                   double* __restrict__ o1) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    o0[e] = r0[e] - b0[e];
+    o1[e] = r1[e] - b1[e];
+  }
+}
+
+int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_build_fine(const LevelDev& L0, const int8_t* mask, unsigned long long* counts2,
+                              cudaStream_t s) {
+  count_launch();
+  build_fine_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0, mask, counts2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_coarsen(const LevelDev& Lf, const int8_t* mask_if_fine, const LevelDev& Lc,
+                                cudaStream_t s) {
+  count_launch();
+  mask_coarsen_kernel<<<grid_for(Lc.g.ncells()), kThreads, 0, s>>>(Lf.g, Lf.level, mask_if_fine, Lf.S, Lc.g,
+                                                                    Lc.S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2, cudaStream_t s) {
+  count_launch();
+  coarse_coeffs_kernel<<<grid_for(Lc.g.ncells()), kThreads, 0, s>>>(Lc, counts2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_natural_to_split(const Geom& g, const double* nat, double* dst0, double* dst1, double scale,
+                                    uint8_t* const* code, uint8_t mask_bit, cudaStream_t s) {
+  count_launch();
+  natural_to_split_kernel<<<grid_for(g.ncells()), kThreads, 0, s>>>(g, nat, dst0, dst1, scale, code[0], code[1],
+                                                                     mask_bit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_to_natural(const Geom& g, double* const* src, double* nat, cudaStream_t s) {
+  count_launch();
+  split_to_natural_kernel<<<grid_for(g.ncells()), kThreads, 0, s>>>(g, src[0], src[1], nat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u8_split_to_natural_bits(const Geom& g, uint8_t* const* code, int32_t* nat, uint8_t bit,
+                                            cudaStream_t s) {
+  count_launch();
+  code_bits_to_natural_kernel<<<grid_for(g.ncells()), kThreads, 0, s>>>(g, code[0], code[1], nat, bit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_faces(const LevelDev& L0, const FineExtra& F, const double* bx, const double* by,
+                              const double* bz, cudaStream_t s) {
+  count_launch();
+  fold_faces_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0, F, bx, by, bz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_coarse(const LevelDev& L0, const FineExtra& F, const double* pc, int cnx, int cny,
+                               int cnz, int ox, int oy, int oz, int* err_flag, cudaStream_t s) {
+  count_launch();
+  fold_coarse_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0, F, pc, cnx, cny, cnz, ox, oy, oz,
+                                                                   err_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStream_t s) {
+  count_launch();
+  combine_rhs_kernel<<<grid_for(L0.g.total), kThreads, 0, s>>>(L0.g.total, F.rhoh2[0], F.rhoh2[1], F.bc[0],
+                                                                F.bc[1], L0.rhs[0], L0.rhs[1]);
+  return cudaGetLastError();
+}
+
+}  // namespace gbmg

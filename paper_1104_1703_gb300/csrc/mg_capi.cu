@@ -1,0 +1,850 @@
+// Host driver and C ABI of the masked-domain multigrid solver (Guillet &
+// Teyssier, arXiv:1104.1703).  Builds the per-level geometry and the device
+// arena, issues the kernels of kernels_build.cu / kernels_cycle.cu in the
+// order of the Section 2 recipe, and runs the solve loop with the run-time
+// reconstruction-order switch of Section 4.
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+
+namespace gbmg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace gbmg
+
+using namespace gbmg;
+
+namespace {
+
+thread_local std::string t_last_error = "no error";
+
+struct Arena {
+  size_t used = 0;
+  size_t reserve(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    return off;
+  }
+};
+
+struct TimedPair {
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mg_hierarchy {
+  mg_options opt;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int nlev = 0;
+  double h = 0;
+  LevelDev L[kMaxLevels];
+  FineExtra F;
+  long long active[3][kMaxLevels];
+  int deepest[3];
+  int hold = 0;
+  char* arena = nullptr;
+  int8_t* mask_dev = nullptr;
+  double* partials = nullptr;
+  int max_partials = 0;
+  double* dscal = nullptr;             // device scalars
+  int* err_flag = nullptr;
+  unsigned long long* counts = nullptr;  // [kMaxLevels][2]
+  double* hscal = nullptr;               // pinned host scalars
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  double r_zero = 0;
+  bool r_zero_valid = false;
+  std::string last_error = "no error";
+  bool timing = false;
+  std::vector<TimedPair> events;
+  size_t events_used = 0;
+  long long timed_launches = 0;
+  double timed_ms = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+mg_status fail(mg_hierarchy* H, mg_status st, const std::string& msg) {
+  if (H) H->last_error = msg;
+  t_last_error = msg;
+  return st;
+}
+
+mg_status cuda_fail(mg_hierarchy* H, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(H, e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA, msg);
+}
+
+#define CK(H, call)                                         \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((H), e_, #call); \
+  } while (0)
+
+#define CKS(call)                              \
+  do {                                         \
+    mg_status s_ = (call);                     \
+    if (s_ != MG_OK) return s_;                \
+  } while (0)
+
+Geom make_geom(int nx, int ny, int nz) {
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.hx = (nx + 1) / 2;
+  g.P = ((g.hx + 1) + 7) & ~7;
+  g.sz = (long long)(ny + 2) * g.P;
+  g.off0 = g.sz + g.P;
+  g.total = (long long)(nz + 2) * g.sz;
+  return g;
+}
+
+bool valid_options(const mg_options& o) {
+  return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
+         o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2);
+}
+
+// Number of levels: halve (ceil) until every dimension is at most 2.
+int plan_levels(int nx, int ny, int nz, int dims[][3]) {
+  int n = 0;
+  for (;;) {
+    dims[n][0] = nx;
+    dims[n][1] = ny;
+    dims[n][2] = nz;
+    ++n;
+    if ((nx <= 2 && ny <= 2 && nz <= 2) || n >= kMaxLevels) break;
+    nx = (nx + 1) / 2;
+    ny = (ny + 1) / 2;
+    nz = (nz + 1) / 2;
+  }
+  return n;
+}
+
+mg_status ensure_staging(mg_hierarchy* H, size_t bytes) {
+  if (H->staging_bytes >= bytes) return MG_OK;
+  if (H->staging) cudaFree(H->staging);
+  H->staging = nullptr;
+  H->staging_bytes = 0;
+  CK(H, cudaMalloc(&H->staging, bytes));
+  H->staging_bytes = bytes;
+  return MG_OK;
+}
+
+// Returns a device pointer holding `bytes` of the caller's data.  Host data
+// is copied into the staging buffer at `offset` and the stream synchronised
+// so the caller may reuse its buffer on return.
+mg_status device_view(mg_hierarchy* H, const void* src, mg_mem where, size_t bytes, size_t offset,
+                      const void** out) {
+  if (where == MG_MEM_DEVICE) {
+    *out = src;
+    return MG_OK;
+  }
+  char* dst = (char*)H->staging + offset;
+  CK(H, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, H->stream));
+  *out = dst;
+  return MG_OK;
+}
+
+int kind_order(const mg_hierarchy* H) {
+  // order for a bare V-cycle or the start of a solve
+  if (H->opt.order == 1 || H->opt.order == 2) return H->opt.order;
+  return H->hold > 0 ? 1 : 2;
+}
+
+mg_status launch_ok(mg_hierarchy* H, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return cuda_fail(H, e, what);
+  return MG_OK;
+}
+
+mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour) {
+  if (l == 0 && H->timing) {
+    if (H->events_used == H->events.size()) {
+      TimedPair p;
+      CK(H, cudaEventCreate(&p.a));
+      CK(H, cudaEventCreate(&p.b));
+      H->events.push_back(p);
+    }
+    TimedPair& p = H->events[H->events_used++];
+    CK(H, cudaEventRecord(p.a, H->stream));
+    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->stream), "half-sweep"));
+    CK(H, cudaEventRecord(p.b, H->stream));
+    return MG_OK;
+  }
+  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->stream), "half-sweep");
+}
+
+mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps) {
+  if (sweeps <= 0) return MG_OK;
+  if (small_level(H->L[l].g))
+    return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, H->stream), "small-level smoother");
+  for (int s = 0; s < sweeps; ++s) {
+    CKS(half_sweep(H, l, order, 0));
+    CKS(half_sweep(H, l, order, 1));
+  }
+  return MG_OK;
+}
+
+// Section 2 recipe at level l, recursing N_cycles times into level l+1.
+mg_status iteration(mg_hierarchy* H, int l, int order) {
+  const mg_options& o = H->opt;
+  if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps);
+  CKS(smooth(H, l, order, o.n_pre));                                        // step 1
+  CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, H->stream),
+                "residual/restriction"));                                    // steps 2-5
+  for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order));      // step 5
+  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, H->stream), "prolongation"));  // 6-7
+  return smooth(H, l, order, o.n_post);                                     // step 8
+}
+
+// Gauss-Seidel updates of active cells in one iteration starting at level l.
+long long updates(const mg_hierarchy* H, int l, int order) {
+  const mg_options& o = H->opt;
+  const long long act = l == 0 ? H->active[2][0] : H->active[order][l];
+  if (l == H->deepest[order]) return (long long)o.coarse_sweeps * act;
+  return (long long)(o.n_pre + o.n_post) * act + (long long)o.n_cycles * updates(H, l + 1, order);
+}
+
+// True when the last operation of an iteration on level 0 was a complete
+// red-black sweep (then only red cells carry a residual).
+bool ends_with_sweep(const mg_hierarchy* H, int order) {
+  return H->deepest[order] == 0 ? H->opt.coarse_sweeps >= 1 : H->opt.n_post >= 1;
+}
+
+mg_status norm2(mg_hierarchy* H, bool red_only, bool with_phi, double* out) {
+  CKS(launch_ok(H, launch_residual_norm2(H->L[0], red_only, with_phi, H->partials, H->max_partials, H->dscal,
+                                        H->stream),
+                "residual norm"));
+  CK(H, cudaMemcpyAsync(H->hscal, H->dscal, sizeof(double), cudaMemcpyDeviceToHost, H->stream));
+  CK(H, cudaStreamSynchronize(H->stream));
+  *out = H->hscal[0];
+  return MG_OK;
+}
+
+mg_status residual(mg_hierarchy* H, bool red_only, double* out) {
+  double s2;
+  CKS(norm2(H, red_only, true, &s2));
+  *out = std::sqrt(s2) / (H->h * H->h);
+  return MG_OK;
+}
+
+mg_status residual_zero(mg_hierarchy* H, double* out) {
+  if (!H->r_zero_valid) {
+    double s2;
+    CKS(norm2(H, false, false, &s2));
+    H->r_zero = std::sqrt(s2) / (H->h * H->h);
+    H->r_zero_valid = true;
+  }
+  *out = H->r_zero;
+  return MG_OK;
+}
+
+mg_status zero_split(mg_hierarchy* H, const Geom& g, double* const* a) {
+  for (int c = 0; c < 2; ++c) CK(H, cudaMemsetAsync(a[c], 0, sizeof(double) * g.total, H->stream));
+  return MG_OK;
+}
+
+// Hierarchy build (mask sums, codes, diagonals, counts) from H->mask_dev.
+mg_status build_levels(mg_hierarchy* H) {
+  cudaStream_t s = H->stream;
+  CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2 * kMaxLevels, s));
+  CKS(launch_ok(H, launch_build_fine(H->L[0], H->mask_dev, H->counts, s), "fine build"));
+  for (int l = 0; l + 1 < H->nlev; ++l) {
+    CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? H->mask_dev : nullptr, H->L[l + 1], s), "mask R1"));
+    CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
+  }
+  unsigned long long hc[2 * kMaxLevels];
+  CK(H, cudaMemcpyAsync(hc, H->counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(H, cudaStreamSynchronize(s));
+  for (int l = 0; l < H->nlev; ++l) {
+    H->active[2][l] = (long long)hc[2 * l];
+    H->active[1][l] = l == 0 ? (long long)hc[0] : (long long)hc[2 * l + 1];
+  }
+  for (int o = 1; o <= 2; ++o) {
+    H->deepest[o] = -1;
+    for (int l = 0; l < H->nlev && H->active[o][l] > 0; ++l) H->deepest[o] = l;
+  }
+  return MG_OK;
+}
+
+mg_status reset_fields(mg_hierarchy* H) {
+  for (int l = 0; l < H->nlev; ++l) {
+    CKS(zero_split(H, H->L[l].g, H->L[l].phi));
+    CKS(zero_split(H, H->L[l].g, H->L[l].rhs));
+  }
+  CKS(zero_split(H, H->L[0].g, H->F.rhoh2));
+  CKS(zero_split(H, H->L[0].g, H->F.bc));
+  H->r_zero_valid = false;
+  return MG_OK;
+}
+
+void destroy(mg_hierarchy* H) {
+  if (!H) return;
+  DeviceGuard guard(H->device);
+  if (H->stream) cudaStreamSynchronize(H->stream);
+  for (auto& p : H->events) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  if (H->staging) cudaFree(H->staging);
+  if (H->arena) cudaFree(H->arena);
+  if (H->hscal) cudaFreeHost(H->hscal);
+  if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
+  delete H;
+}
+
+mg_status check_level(mg_hierarchy* H, int level) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  if (level < 0 || level >= H->nlev) return fail(H, MG_ERR_INVALID_ARG, "level out of range");
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_options(mg_options* opt) {
+  if (!opt) return;
+  opt->n_pre = 2;
+  opt->n_post = 2;
+  opt->n_cycles = 1;
+  opt->coarse_sweeps = 50;
+  opt->hold_solves = 10;
+  opt->eta = 0.5;
+  opt->order = 0;
+  opt->use_graphs = 1;
+}
+
+const char* mg_status_string(mg_status st) {
+  switch (st) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_EMPTY_DOMAIN: return "empty domain";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_DIVERGED: return "diverged";
+    case MG_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* mg_last_error(const mg_hierarchy* H) { return H ? H->last_error.c_str() : t_last_error.c_str(); }
+
+unsigned long long mg_launch_count(void) { return g_launches.load(); }
+
+mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, int nz, double h,
+                              const mg_options* opt, void* cuda_stream, mg_hierarchy** out) {
+  if (out) *out = nullptr;
+  if (!out || !mask) return fail(nullptr, MG_ERR_INVALID_ARG, "null mask or output pointer");
+  if (where != MG_MEM_HOST && where != MG_MEM_DEVICE) return fail(nullptr, MG_ERR_INVALID_ARG, "bad mg_mem");
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 2048 || ny > 2048 || nz > 2048)
+    return fail(nullptr, MG_ERR_INVALID_ARG, "dimensions must be in 1..2048");
+  if (!(h > 0) || !std::isfinite(h)) return fail(nullptr, MG_ERR_INVALID_ARG, "h must be finite and > 0");
+  mg_options o;
+  mg_default_options(&o);
+  if (opt) o = *opt;
+  if (!valid_options(o)) return fail(nullptr, MG_ERR_INVALID_ARG, "invalid options");
+
+  mg_hierarchy* H = new mg_hierarchy();
+  H->opt = o;
+  H->h = h;
+  if (cudaGetDevice(&H->device) != cudaSuccess) {
+    delete H;
+    return fail(nullptr, MG_ERR_CUDA, "no CUDA device");
+  }
+  if (cuda_stream) {
+    H->stream = (cudaStream_t)cuda_stream;
+  } else {
+    // a blocking stream: it orders with the legacy default stream, which
+    // callers that pass no stream are most likely using
+    cudaError_t e = cudaStreamCreate(&H->stream);
+    if (e != cudaSuccess) {
+      mg_status st = cuda_fail(nullptr, e, "cudaStreamCreate");
+      delete H;
+      return st;
+    }
+    H->own_stream = true;
+  }
+  int dims[kMaxLevels][3];
+  H->nlev = plan_levels(nx, ny, nz, dims);
+
+  // one arena for every level array
+  Arena A;
+  struct Off {
+    size_t phi[2], rhs[2], invd[2], diag[2], code[2], S;
+  } off[kMaxLevels];
+  for (int l = 0; l < H->nlev; ++l) {
+    Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
+    H->L[l].g = g;
+    H->L[l].level = l;
+    for (int c = 0; c < 2; ++c) {
+      off[l].phi[c] = A.reserve(sizeof(double) * g.total);
+      off[l].rhs[c] = A.reserve(sizeof(double) * g.total);
+      off[l].code[c] = A.reserve(g.total);
+      if (l > 0) {
+        off[l].invd[c] = A.reserve(sizeof(double) * g.total);
+        off[l].diag[c] = A.reserve(sizeof(double) * g.total);
+      }
+    }
+    if (l > 0) off[l].S = A.reserve(sizeof(int32_t) * g.ncells());
+  }
+  const Geom& g0 = H->L[0].g;
+  size_t o_rhoh2[2], o_bc[2], o_save[2];
+  for (int c = 0; c < 2; ++c) {
+    o_rhoh2[c] = A.reserve(sizeof(double) * g0.total);
+    o_bc[c] = A.reserve(sizeof(double) * g0.total);
+    o_save[c] = A.reserve(sizeof(double) * g0.total);
+  }
+  size_t o_mask = A.reserve(g0.ncells());
+  H->max_partials = residual_norm_blocks(g0);
+  size_t o_part = A.reserve(sizeof(double) * H->max_partials);
+  size_t o_scal = A.reserve(sizeof(double) * 8);
+  size_t o_err = A.reserve(sizeof(int) * 4);
+  size_t o_cnt = A.reserve(sizeof(unsigned long long) * 2 * kMaxLevels);
+
+  cudaError_t e = cudaMalloc(&H->arena, A.used);
+  if (e != cudaSuccess) {
+    mg_status st = cuda_fail(nullptr, e, "cudaMalloc(arena)");
+    H->arena = nullptr;
+    destroy(H);
+    return st;
+  }
+  e = cudaMallocHost(&H->hscal, sizeof(double) * 8);
+  if (e != cudaSuccess) {
+    H->hscal = nullptr;
+    mg_status st = cuda_fail(nullptr, e, "cudaMallocHost");
+    destroy(H);
+    return st;
+  }
+  char* base = H->arena;
+  for (int l = 0; l < H->nlev; ++l) {
+    for (int c = 0; c < 2; ++c) {
+      H->L[l].phi[c] = (double*)(base + off[l].phi[c]);
+      H->L[l].rhs[c] = (double*)(base + off[l].rhs[c]);
+      H->L[l].code[c] = (uint8_t*)(base + off[l].code[c]);
+      H->L[l].invd[c] = l > 0 ? (double*)(base + off[l].invd[c]) : nullptr;
+      H->L[l].diag[c] = l > 0 ? (double*)(base + off[l].diag[c]) : nullptr;
+    }
+    H->L[l].S = l > 0 ? (int32_t*)(base + off[l].S) : nullptr;
+  }
+  for (int c = 0; c < 2; ++c) {
+    H->F.rhoh2[c] = (double*)(base + o_rhoh2[c]);
+    H->F.bc[c] = (double*)(base + o_bc[c]);
+    H->F.save[c] = (double*)(base + o_save[c]);
+  }
+  H->mask_dev = (int8_t*)(base + o_mask);
+  H->F.mask = H->mask_dev;
+  H->partials = (double*)(base + o_part);
+  H->dscal = (double*)(base + o_scal);
+  H->err_flag = (int*)(base + o_err);
+  H->counts = (unsigned long long*)(base + o_cnt);
+
+  mg_status st = MG_OK;
+  e = cudaMemsetAsync(H->arena, 0, A.used, H->stream);
+  if (e != cudaSuccess) st = cuda_fail(H, e, "cudaMemset(arena)");
+  if (st == MG_OK) {
+    e = cudaMemcpyAsync(H->mask_dev, mask, g0.ncells(),
+                        where == MG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, H->stream);
+    if (e != cudaSuccess) st = cuda_fail(H, e, "mask copy");
+  }
+  if (st == MG_OK) st = build_levels(H);
+  if (st == MG_OK && H->deepest[2] < 0) st = fail(H, MG_ERR_EMPTY_DOMAIN, "the mask has no active cell");
+  if (st != MG_OK) {
+    t_last_error = H->last_error;
+    destroy(H);
+    return st;
+  }
+  *out = H;
+  return MG_OK;
+}
+
+mg_status mg_destroy_hierarchy(mg_hierarchy* H) {
+  destroy(H);
+  return MG_OK;
+}
+
+mg_status mg_update_mask(mg_hierarchy* H, const int8_t* mask, mg_mem where) {
+  if (!H || !mask) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy or mask");
+  DeviceGuard guard(H->device);
+  const Geom& g0 = H->L[0].g;
+  // validate on a copy first so that an empty mask leaves the old one in force
+  CKS(ensure_staging(H, g0.ncells()));
+  CK(H, cudaMemcpyAsync(H->staging, mask, g0.ncells(),
+                        where == MG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, H->stream));
+  CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2, H->stream));
+  CKS(launch_ok(H, launch_build_fine(H->L[0], (const int8_t*)H->staging, H->counts, H->stream), "fine build"));
+  unsigned long long n_act = 0;
+  CK(H, cudaMemcpyAsync(&n_act, H->counts, sizeof(n_act), cudaMemcpyDeviceToHost, H->stream));
+  CK(H, cudaStreamSynchronize(H->stream));
+  if (n_act == 0) {
+    CKS(build_levels(H));  // restore the level-0 codes of the old mask
+    return fail(H, MG_ERR_EMPTY_DOMAIN, "the mask has no active cell");
+  }
+  CK(H, cudaMemcpyAsync(H->mask_dev, H->staging, g0.ncells(), cudaMemcpyDeviceToDevice, H->stream));
+  CKS(build_levels(H));
+  return reset_fields(H);
+}
+
+mg_status mg_set_rhs(mg_hierarchy* H, const double* rho, mg_mem where) {
+  if (!H || !rho) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy or rho");
+  DeviceGuard guard(H->device);
+  const Geom& g0 = H->L[0].g;
+  const size_t bytes = sizeof(double) * g0.ncells();
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
+  const void* src;
+  CKS(device_view(H, rho, where, bytes, 0, &src));
+  CKS(launch_ok(H, launch_natural_to_split(g0, (const double*)src, H->F.rhoh2[0], H->F.rhoh2[1], H->h * H->h,
+                                          H->L[0].code, kActive2, H->stream),
+                "rho layout"));
+  CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+  if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
+  H->r_zero_valid = false;
+  return MG_OK;
+}
+
+mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, const double* bz, mg_mem where) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  DeviceGuard guard(H->device);
+  const Geom& g = H->L[0].g;
+  const size_t nfx = (size_t)(g.nx + 1) * g.ny * g.nz, nfy = (size_t)g.nx * (g.ny + 1) * g.nz,
+               nfz = (size_t)g.nx * g.ny * (g.nz + 1);
+  const void *dx = nullptr, *dy = nullptr, *dz = nullptr;
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, sizeof(double) * (nfx + nfy + nfz) + 512));
+  size_t o2 = ((sizeof(double) * nfx + 255) & ~(size_t)255);
+  size_t o3 = o2 + ((sizeof(double) * nfy + 255) & ~(size_t)255);
+  if (bx) CKS(device_view(H, bx, where, sizeof(double) * nfx, 0, &dx));
+  if (by) CKS(device_view(H, by, where, sizeof(double) * nfy, o2, &dy));
+  if (bz) CKS(device_view(H, bz, where, sizeof(double) * nfz, o3, &dz));
+  CKS(launch_ok(H, launch_fold_faces(H->L[0], H->F, (const double*)dx, (const double*)dy, (const double*)dz,
+                                    H->stream),
+                "face fold"));
+  CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+  if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
+  H->r_zero_valid = false;
+  return MG_OK;
+}
+
+mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_mem where, int cnx, int cny,
+                                       int cnz, int ox, int oy, int oz) {
+  if (!H || !phi_c) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy or coarse potential");
+  if (cnx < 2 || cny < 2 || cnz < 2 || cnx > 4096 || cny > 4096 || cnz > 4096)
+    return fail(H, MG_ERR_INVALID_ARG, "coarse dimensions must be in 2..4096");
+  DeviceGuard guard(H->device);
+  const size_t bytes = sizeof(double) * (size_t)cnx * cny * cnz;
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
+  const void* src;
+  CKS(device_view(H, phi_c, where, bytes, 0, &src));
+  CK(H, cudaMemsetAsync(H->err_flag, 0, sizeof(int), H->stream));
+  CKS(launch_ok(H, launch_fold_coarse(H->L[0], H->F, (const double*)src, cnx, cny, cnz, ox, oy, oz, H->err_flag,
+                                     H->stream),
+                "coarse interpolation"));
+  int err = 0;
+  CK(H, cudaMemcpyAsync(H->hscal, H->err_flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  CK(H, cudaStreamSynchronize(H->stream));
+  std::memcpy(&err, H->hscal, sizeof(int));
+  if (err) {
+    CKS(zero_split(H, H->L[0].g, H->F.bc));
+    CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+    H->r_zero_valid = false;
+    return fail(H, MG_ERR_INVALID_ARG,
+                "a boundary face lies outside the coarse cell centres; Dirichlet values reset to 0");
+  }
+  CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+  H->r_zero_valid = false;
+  return MG_OK;
+}
+
+mg_status mg_set_solution(mg_hierarchy* H, const double* phi, mg_mem where) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  DeviceGuard guard(H->device);
+  const Geom& g0 = H->L[0].g;
+  if (!phi) return zero_split(H, g0, H->L[0].phi);
+  const size_t bytes = sizeof(double) * g0.ncells();
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
+  const void* src;
+  CKS(device_view(H, phi, where, bytes, 0, &src));
+  CKS(launch_ok(H, launch_natural_to_split(g0, (const double*)src, H->L[0].phi[0], H->L[0].phi[1], 1.0,
+                                          H->L[0].code, kActive2, H->stream),
+                "phi layout"));
+  if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
+  return MG_OK;
+}
+
+mg_status mg_get_solution(mg_hierarchy* H, double* phi, mg_mem where) {
+  return mg_level_get(H, 0, MG_FIELD_PHI, phi, where);
+}
+
+mg_status mg_residual_norm(mg_hierarchy* H, double* norm_out, double* norm_zero_out) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  DeviceGuard guard(H->device);
+  if (norm_out) CKS(residual(H, false, norm_out));
+  if (norm_zero_out) CKS(residual_zero(H, norm_zero_out));
+  return MG_OK;
+}
+
+mg_status mg_vcycle(mg_hierarchy* H, double* rel_out) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  DeviceGuard guard(H->device);
+  const int order = kind_order(H);
+  CKS(iteration(H, 0, order));
+  if (!rel_out) return MG_OK;
+  double r, r0;
+  CKS(residual(H, ends_with_sweep(H, order), &r));
+  CKS(residual_zero(H, &r0));
+  *rel_out = r0 > 0 ? r / r0 : 0.0;
+  if (!std::isfinite(r)) return fail(H, MG_ERR_DIVERGED, "non-finite residual");
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* info) {
+  if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
+  if (!(tol > 0) || max_cycles < 0) return fail(H, MG_ERR_INVALID_ARG, "tol must be > 0 and max_cycles >= 0");
+  DeviceGuard guard(H->device);
+  const mg_options& o = H->opt;
+  // Section 4: choose the order for this solve
+  int order = 2;
+  bool auto_switch = false, switched = false;
+  if (o.order == 1 || o.order == 2) {
+    order = o.order;
+  } else if (H->hold > 0) {
+    order = 1;
+    H->hold -= 1;
+  } else {
+    auto_switch = true;
+  }
+  if (H->deepest[order] < 0) order = 2;
+  const Geom& g0 = H->L[0].g;
+  double r_zero, r_init;
+  CKS(residual_zero(H, &r_zero));
+  CKS(residual(H, false, &r_init));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->r_zero = r_zero;
+    info->r_init = r_init;
+    info->hist[0] = r_init;
+  }
+  int cycles = 0;
+  long long n_updates = 0;
+  double r_n = r_init, rel = r_zero > 0 ? r_init / r_zero : 0.0;
+  mg_status st = MG_ERR_NOT_CONVERGED;
+  if (!std::isfinite(r_zero) || !std::isfinite(r_init)) {
+    st = MG_ERR_DIVERGED;  // non-finite data: nothing to iterate on
+    r_n = r_init;
+    rel = r_init / r_zero;
+  } else if (r_zero == 0.0) {
+    CKS(zero_split(H, g0, H->L[0].phi));
+    r_n = 0.0;
+    rel = 0.0;
+    st = MG_OK;
+  } else if (rel < tol) {
+    st = MG_OK;
+  } else {
+    if (auto_switch)
+      for (int c = 0; c < 2; ++c)
+        CK(H, cudaMemcpyAsync(H->F.save[c], H->L[0].phi[c], sizeof(double) * g0.total, cudaMemcpyDeviceToDevice,
+                              H->stream));
+    double r_prev = r_init;
+    for (cycles = 1; cycles <= max_cycles; ++cycles) {
+      CKS(iteration(H, 0, order));
+      n_updates += updates(H, 0, order);
+      CKS(residual(H, ends_with_sweep(H, order), &r_n));
+      if (info && cycles <= MG_HIST_MAX) info->hist[cycles] = r_n;
+      if (!std::isfinite(r_n)) {
+        st = MG_ERR_DIVERGED;
+        break;
+      }
+      rel = r_n / r_zero;
+      if (rel < tol) {
+        st = MG_OK;
+        break;
+      }
+      if (auto_switch && !switched && order == 2 && r_n >= 100.0 * DBL_EPSILON * r_zero && r_n / r_prev > o.eta) {
+        order = 1;
+        switched = true;
+        H->hold = o.hold_solves;
+        if (r_n > r_init) {
+          for (int c = 0; c < 2; ++c)
+            CK(H, cudaMemcpyAsync(H->L[0].phi[c], H->F.save[c], sizeof(double) * g0.total,
+                                  cudaMemcpyDeviceToDevice, H->stream));
+          r_n = r_init;
+        }
+      }
+      r_prev = r_n;
+    }
+    if (cycles > max_cycles) cycles = max_cycles;
+  }
+  if (info) {
+    info->cycles = cycles;
+    info->order_used = order;
+    info->switched = switched ? 1 : 0;
+    info->cell_updates = n_updates;
+    info->r_final = r_n;
+    info->rel = rel;
+    info->status = st;
+  }
+  if (st == MG_ERR_NOT_CONVERGED) return fail(H, st, "tolerance not reached within max_cycles");
+  if (st == MG_ERR_DIVERGED) return fail(H, st, "non-finite residual norm");
+  return st;
+}
+
+mg_status mg_get_hold(const mg_hierarchy* H, int* hold) {
+  if (!H || !hold) return fail(nullptr, MG_ERR_INVALID_ARG, "null argument");
+  *hold = H->hold;
+  return MG_OK;
+}
+
+mg_status mg_set_hold(mg_hierarchy* H, int hold) {
+  if (!H || hold < 0) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy or negative hold");
+  H->hold = hold;
+  return MG_OK;
+}
+
+mg_status mg_num_levels(const mg_hierarchy* H, int* nlev, int* d2, int* d1) {
+  if (!H) return fail(nullptr, MG_ERR_INVALID_ARG, "null hierarchy");
+  if (nlev) *nlev = H->nlev;
+  if (d2) *d2 = H->deepest[2];
+  if (d1) *d1 = H->deepest[1];
+  return MG_OK;
+}
+
+mg_status mg_level_info(const mg_hierarchy* H, int level, int* dims3, long long* a2, long long* a1) {
+  if (!H || level < 0 || level >= H->nlev) return fail(nullptr, MG_ERR_INVALID_ARG, "bad hierarchy or level");
+  const Geom& g = H->L[level].g;
+  if (dims3) {
+    dims3[0] = g.nx;
+    dims3[1] = g.ny;
+    dims3[2] = g.nz;
+  }
+  if (a2) *a2 = H->active[2][level];
+  if (a1) *a1 = H->active[1][level];
+  return MG_OK;
+}
+
+mg_status mg_level_get(mg_hierarchy* H, int level, int field, void* out, mg_mem where) {
+  CKS(check_level(H, level));
+  if (!out) return fail(H, MG_ERR_INVALID_ARG, "null output");
+  DeviceGuard guard(H->device);
+  const LevelDev& L = H->L[level];
+  const Geom& g = L.g;
+  const size_t n = (size_t)g.ncells();
+  const size_t elem = field == MG_FIELD_MASKSUM ? sizeof(int32_t) : sizeof(double);
+  if (field == MG_FIELD_INVDIAG && level == 0) return fail(H, MG_ERR_INVALID_ARG, "level 0 has no stored 1/D");
+  if (field < 0 || field > 3) return fail(H, MG_ERR_INVALID_ARG, "unknown field");
+  void* dst = out;
+  if (where == MG_MEM_HOST) {
+    CKS(ensure_staging(H, n * elem));
+    dst = H->staging;
+  }
+  if (field == MG_FIELD_PHI) {
+    CKS(launch_ok(H, launch_split_to_natural(g, L.phi, (double*)dst, H->stream), "layout"));
+  } else if (field == MG_FIELD_RHS) {
+    CKS(launch_ok(H, launch_split_to_natural(g, L.rhs, (double*)dst, H->stream), "layout"));
+  } else if (field == MG_FIELD_INVDIAG) {
+    CKS(launch_ok(H, launch_split_to_natural(g, L.invd, (double*)dst, H->stream), "layout"));
+  } else if (level == 0) {
+    CKS(launch_ok(H, launch_u8_split_to_natural_bits(g, L.code, (int32_t*)dst, kActive2, H->stream), "layout"));
+  } else {
+    CK(H, cudaMemcpyAsync(dst, L.S, n * elem, cudaMemcpyDeviceToDevice, H->stream));
+  }
+  if (where == MG_MEM_HOST) {
+    CK(H, cudaMemcpyAsync(out, dst, n * elem, cudaMemcpyDeviceToHost, H->stream));
+    CK(H, cudaStreamSynchronize(H->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_level_set(mg_hierarchy* H, int level, int field, const void* in, mg_mem where) {
+  CKS(check_level(H, level));
+  if (!in) return fail(H, MG_ERR_INVALID_ARG, "null input");
+  if (field != MG_FIELD_PHI && field != MG_FIELD_RHS)
+    return fail(H, MG_ERR_INVALID_ARG, "only MG_FIELD_PHI and MG_FIELD_RHS can be set");
+  DeviceGuard guard(H->device);
+  LevelDev& L = H->L[level];
+  const size_t bytes = sizeof(double) * (size_t)L.g.ncells();
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
+  const void* src;
+  CKS(device_view(H, in, where, bytes, 0, &src));
+  double** dst = field == MG_FIELD_PHI ? L.phi : L.rhs;
+  // values of cells inactive in second order are dropped (they are 0 in every mode)
+  CKS(launch_ok(H, launch_natural_to_split(L.g, (const double*)src, dst[0], dst[1], 1.0, L.code, kActive2,
+                                          H->stream),
+                "layout"));
+  if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
+  if (level == 0 && field == MG_FIELD_RHS) H->r_zero_valid = false;
+  return MG_OK;
+}
+
+mg_status mg_level_smooth(mg_hierarchy* H, int level, int order, int sweeps) {
+  CKS(check_level(H, level));
+  if ((order != 1 && order != 2) || sweeps < 0) return fail(H, MG_ERR_INVALID_ARG, "bad order or sweeps");
+  DeviceGuard guard(H->device);
+  CKS(smooth(H, level, order, sweeps));
+  CK(H, cudaStreamSynchronize(H->stream));
+  return MG_OK;
+}
+
+mg_status mg_level_restrict(mg_hierarchy* H, int level, int order) {
+  CKS(check_level(H, level));
+  if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
+  DeviceGuard guard(H->device);
+  CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, H->stream), "restriction"));
+  CK(H, cudaStreamSynchronize(H->stream));
+  return MG_OK;
+}
+
+mg_status mg_level_prolong(mg_hierarchy* H, int level, int order) {
+  CKS(check_level(H, level));
+  if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
+  DeviceGuard guard(H->device);
+  CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, H->stream), "prolongation"));
+  CK(H, cudaStreamSynchronize(H->stream));
+  return MG_OK;
+}
+
+mg_status mg_timing_enable(mg_hierarchy* H, int enable) {
+  if (!H) return fail(nullptr, MG_ERR_INVALID_ARG, "null hierarchy");
+  H->timing = enable != 0;
+  return MG_OK;
+}
+
+mg_status mg_timing_read(mg_hierarchy* H, long long* launches, double* total_ms) {
+  if (!H) return fail(nullptr, MG_ERR_INVALID_ARG, "null hierarchy");
+  DeviceGuard guard(H->device);
+  CK(H, cudaStreamSynchronize(H->stream));
+  double sum = 0;
+  for (size_t i = 0; i < H->events_used; ++i) {
+    float ms = 0;
+    CK(H, cudaEventElapsedTime(&ms, H->events[i].a, H->events[i].b));
+    sum += ms;
+  }
+  if (launches) *launches = (long long)H->events_used;
+  if (total_ms) *total_ms = sum;
+  H->events_used = 0;
+  return MG_OK;
+}
+
+}  // extern "C"

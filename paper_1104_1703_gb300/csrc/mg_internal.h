@@ -1,0 +1,108 @@
+// Internal declarations shared by the CUDA kernels and the host driver of
+// the masked-domain multigrid solver (Guillet & Teyssier, arXiv:1104.1703).
+//
+// Device layout ("red/black split"): every cell-centred field of a level is
+// stored as two arrays, one per Gauss-Seidel colour (red: (i+j+k) even).
+// Cell (i, j, k) has colour c = (i+j+k) & 1 and lives at slot q = i >> 1 of
+// row (j, k) of array c.  With this layout a half-sweep of one colour reads
+// only the other colour's array plus its own right-hand side and writes its
+// own array, every access is unit-stride in q, and no thread idles on a cell
+// of the wrong colour.  In row (j, k) the colour-c cells sit at
+// i = 2q + (c ^ ((j+k) & 1)), so their x-neighbours of the other colour are
+// at slots {q-1, q} when that parity bit is 0 and {q, q+1} when it is 1;
+// their y and z neighbours are at slot q of the adjacent rows.
+//
+// Each colour array has a zero halo: one row above and below in y, one plane
+// before and after in z, and in x a row pitch P >= hx + 1 so that slot -1
+// of a row is the last (padding) slot of the previous row and slot hx is
+// padding.  Halo and padding hold 0 forever, so the stencil needs no bounds
+// tests: inactive and out-of-box cells contribute the value 0, which is what
+// the folded operators below expect.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace gbmg {
+
+constexpr int kMaxLevels = 12;
+
+// Bits of the per-cell code byte.
+constexpr uint8_t kActive2 = 1;  // active in second order (S > 0)
+constexpr uint8_t kActive1 = 2;  // active in first order (S == 8^l); level 0: same as kActive2
+constexpr int kGhostShift = 2;   // level 0: bits 2..7 flag the faces -x,+x,-y,+y,-z,+z whose
+                                 // neighbour is inactive or outside the box (ghost faces)
+
+struct Geom {
+  int nx, ny, nz;      // cells per axis
+  int hx;              // slots per half-row: (nx + 1) / 2
+  int P;               // row pitch in elements (>= hx + 1)
+  long long sz;        // plane stride: (ny + 2) * P
+  long long off0;      // element offset of slot (0, 0, 0): sz + P
+  long long total;     // elements per colour array: (nz + 2) * sz
+  __host__ __device__ long long at(int q, int j, int k) const { return off0 + k * sz + (long long)j * P + q; }
+  __host__ __device__ long long ncells() const { return (long long)nx * ny * nz; }
+};
+
+struct LevelDev {
+  Geom g;
+  int level;
+  double* phi[2];    // level 0: Phi; level >= 1: dPhi
+  double* rhs[2];    // b = h_l^2 * (right-hand side), Dirichlet terms folded in at level 0
+  double* invd[2];   // level >= 1: 1/D of the second-order operator (0 if inactive)
+  double* diag[2];   // level >= 1: D of the second-order operator (0 if inactive)
+  uint8_t* code[2];  // kActive2 | kActive1 | ghost-face bits
+  int32_t* S;        // level >= 1: mask sums, natural layout nx*ny*nz
+};
+
+struct FineExtra {
+  double* rhoh2[2];  // h^2 rho, split layout
+  double* bc[2];     // 2 * sum of Phi_b over the ghost faces, split layout
+  double* save[2];   // backup of the initial guess for the order switch
+  const int8_t* mask;  // natural-layout mask (device)
+};
+
+// Launch-count instrumentation.
+void count_launch(unsigned long long n = 1);
+
+// ---- hierarchy build (kernels_build.cu) ----
+cudaError_t launch_build_fine(const LevelDev& L0, const int8_t* mask, unsigned long long* counts2,
+                              cudaStream_t s);
+cudaError_t launch_mask_coarsen(const LevelDev& Lf, const int8_t* mask_if_fine, const LevelDev& Lc,
+                                cudaStream_t s);
+cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2, cudaStream_t s);
+
+// ---- data movement and boundary data (kernels_build.cu) ----
+// natural (nx*ny*nz) <-> split; `scale` multiplies, `mask_bit` zeroes cells
+// whose code lacks the bit (0: keep all).
+cudaError_t launch_natural_to_split(const Geom& g, const double* nat, double* dst0, double* dst1, double scale,
+                                    uint8_t* const* code, uint8_t mask_bit, cudaStream_t s);
+cudaError_t launch_split_to_natural(const Geom& g, double* const* src, double* nat, cudaStream_t s);
+cudaError_t launch_u8_split_to_natural_bits(const Geom& g, uint8_t* const* code, int32_t* nat, uint8_t bit,
+                                            cudaStream_t s);
+cudaError_t launch_fold_faces(const LevelDev& L0, const FineExtra& F, const double* bx, const double* by,
+                              const double* bz, cudaStream_t s);
+cudaError_t launch_fold_coarse(const LevelDev& L0, const FineExtra& F, const double* pc, int cnx, int cny,
+                               int cnz, int ox, int oy, int oz, int* err_flag, cudaStream_t s);
+cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStream_t s);
+
+// ---- V-cycle kernels (kernels_cycle.cu) ----
+// order: 1 or 2; the level's active bit and diagonal follow from it.
+cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, cudaStream_t s);
+cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, cudaStream_t s);
+bool small_level(const Geom& g);
+// Residual of level Lf restricted into the rhs of Lc as -R1(r) (scaled), dPhi_c = 0.
+// black_zero: the last operation on Lf was a complete red-black sweep, so
+// the black residual vanishes and only red cells are evaluated.
+cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, cudaStream_t s);
+cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, cudaStream_t s);
+// Sum of squares of the scaled residual of level 0 into partials[0..nblocks),
+// then a fixed-order reduction into out[0].  red_only as black_zero above.
+// with_phi = false evaluates the residual of Phi = 0 (i.e. of the rhs alone).
+cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_phi, double* partials,
+                                  int max_partials, double* out, cudaStream_t s);
+int residual_norm_blocks(const Geom& g);
+
+}  // namespace gbmg

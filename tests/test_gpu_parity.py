@@ -1,0 +1,392 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the FP64 path must agree with the FP64 oracle to 1e-12 relative
+(max abs difference over the compared cells divided by the max abs value of
+the oracle's array).  Integer work (mask sums, active counts, level depths,
+cycle counts, order decisions) must agree exactly.  Residual histories agree
+to 1e-10 relative above an absolute floor of 1e-13 ||r(0)||: below that the
+norms are rounding noise of two different (equally valid) summation orders.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1104_1703_gb300 import binding as B  # noqa: E402
+from paper_1104_1703_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+HIST_REL, HIST_FLOOR = 1e-10, 1e-13
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
+
+
+def relerr(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(np.asarray(a, np.float64) - b).max() / scale
+
+
+def cases():
+    out = {}
+    out["ball32"] = W.ball(32)
+    out["ball64"] = W.ball(64)
+    m = W.random_mask((10, 12, 17), seed=101, p_active=0.7)
+    out["random17x12x10"] = {"mask": m, "rho": W.random_field(m.shape, 102), "h": 0.07,
+                             "faces": W.random_faces(m.shape, 103)}
+    out["holes32"] = W.holes(32)
+    out["blob48x32x40"] = W.blob_patch((40, 32, 48), seed=104)
+    return out
+
+
+CASES = cases()
+
+
+def faces_of(w):
+    if "faces" in w:
+        return w["faces"]
+    return w.get("bx"), w.get("by"), w.get("bz")
+
+
+def make_pair(w, dev, **opts):
+    from oracle import oracle as O
+    H = B.Hierarchy(torch.from_numpy(w["mask"]).to(dev), w["h"], **opts)
+    R = O.Hierarchy(w["mask"], w["h"])
+    rho = w["rho"]
+    H.set_rhs(torch.from_numpy(rho).to(dev))
+    R.set_rhs(rho)
+    if "phi_c" in w:
+        H.set_dirichlet_from_coarse(torch.from_numpy(w["phi_c"]).to(dev), w["origin"])
+        R.set_faces(*O.dirichlet_from_coarse(w["mask"], w["phi_c"], w["origin"]))
+    else:
+        f = faces_of(w)
+        if f[0] is not None:
+            H.set_dirichlet(*(torch.from_numpy(a).to(dev) for a in f))
+            R.set_faces(*f)
+    return H, R
+
+
+def active_of(S, level, order):
+    return S > 0 if (level == 0 or order == 2) else S == 8 ** level
+
+
+# ---------------------------------------------------------------------------
+# K1/K2: hierarchy construction
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mask_hierarchy_exact(dev, name):
+    w = CASES[name]
+    H, R = make_pair(w, dev)
+    nlev, d2, d1 = H.levels()
+    assert nlev == R.num_levels and d2 == R.deepest(2) and d1 == R.deepest(1)
+    for l in range(nlev):
+        shape, a2, a1 = H.level_info(l)
+        assert shape == R.level_shape(l)
+        assert (a2, a1) == (R.level_active(l, 2), R.level_active(l, 1))
+        S = H.level_get(l, B.MG_FIELD_MASKSUM)
+        assert np.array_equal(S.astype(np.int64), R.S(l)), "level %d" % l
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 2, 3), (3, 1, 5), (2, 2, 2)])
+def test_tiny_grids(dev, shape):
+    from oracle import oracle as O
+    mask = np.ones(shape, np.int8)
+    rho = W.random_field(shape, 7)
+    faces = W.random_faces(shape, 8)
+    H = B.Hierarchy(mask, 0.5)
+    H.set_rhs(rho)
+    H.set_dirichlet(*faces)
+    R = O.Hierarchy(mask, 0.5)
+    R.set_rhs(rho)
+    R.set_faces(*faces)
+    st, info = H.solve(1e-12, 30)
+    st_o, info_o = R.solve(1e-12, 30)
+    assert st == st_o == 0 and info["cycles"] == info_o["cycles"]
+    assert relerr(H.get_solution(), R.get_phi()) < TOL
+
+
+# ---------------------------------------------------------------------------
+# K4 smoother, K5 residual + R1, K6 P2: per level and order
+# ---------------------------------------------------------------------------
+
+LEVEL_CASES = [("ball64", 0, 2), ("ball64", 1, 2), ("ball64", 1, 1), ("ball64", 2, 2), ("ball64", 2, 1),
+               ("ball64", 3, 2), ("random17x12x10", 0, 2), ("random17x12x10", 1, 2), ("holes32", 1, 1),
+               ("holes32", 1, 2), ("blob48x32x40", 0, 2), ("blob48x32x40", 1, 2), ("blob48x32x40", 2, 1)]
+
+
+def _level_state(w, H, R, level, order, seed):
+    """Random Phi (zero off the active set) and right-hand side on `level`,
+    loaded into both implementations."""
+    S = R.S(level)
+    act = active_of(S, level, order)
+    phi = np.where(act, W.random_field(S.shape, seed), 0.0)
+    if level == 0:
+        H.level_set(0, B.MG_FIELD_PHI, phi)
+        R.set_phi(phi)
+        f = None
+    else:
+        f = W.random_field(S.shape, seed + 1)
+        hl = w["h"] * 2 ** level
+        H.level_set(level, B.MG_FIELD_PHI, phi)
+        H.level_set(level, B.MG_FIELD_RHS, f * hl * hl)
+        R.set_level_phi(level, phi)
+        R.set_level_rhs(level, f)
+    return S, act, phi, f
+
+
+@pytest.mark.parametrize("name,level,order", LEVEL_CASES)
+def test_smoother_parity(dev, name, level, order):
+    w = CASES[name]
+    H, R = make_pair(w, dev)
+    if level >= H.levels()[0]:
+        pytest.skip("level not built")
+    _level_state(w, H, R, level, order, seed=200 + level)
+    for sweeps in (1, 2):
+        H.smooth(level, order, sweeps)
+        R.smooth(level, order, sweeps)
+        got = H.level_get(level, B.MG_FIELD_PHI)
+        assert relerr(got, R.phi(level)) < TOL
+
+
+@pytest.mark.parametrize("name,level,order", LEVEL_CASES)
+def test_restriction_parity(dev, name, level, order):
+    w = CASES[name]
+    H, R = make_pair(w, dev)
+    if level + 1 >= H.levels()[0]:
+        pytest.skip("no coarser level")
+    _level_state(w, H, R, level, order, seed=300 + level)
+    H.restrict_to(level, order)
+    R.restrict_to(level, order)
+    hc = w["h"] * 2 ** (level + 1)
+    assert relerr(H.level_get(level + 1, B.MG_FIELD_RHS), R.rhs(level + 1) * hc * hc) < TOL
+    assert not H.level_get(level + 1, B.MG_FIELD_PHI).any()
+
+
+@pytest.mark.parametrize("name,level,order", LEVEL_CASES)
+def test_prolongation_parity(dev, name, level, order):
+    w = CASES[name]
+    H, R = make_pair(w, dev)
+    if level + 1 >= H.levels()[0]:
+        pytest.skip("no coarser level")
+    _level_state(w, H, R, level, order, seed=400 + level)
+    Sc = R.S(level + 1)
+    ec = np.where(active_of(Sc, level + 1, order), W.random_field(Sc.shape, 401 + level), 0.0)
+    H.level_set(level + 1, B.MG_FIELD_PHI, ec)
+    R.set_level_phi(level + 1, ec)
+    H.prolong_from(level, order)
+    R.prolong_from(level, order)
+    assert relerr(H.level_get(level, B.MG_FIELD_PHI), R.phi(level)) < TOL
+
+
+# ---------------------------------------------------------------------------
+# Whole V-cycles and solves
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("order", [1, 2])
+def test_vcycle_parity(dev, name, order):
+    w = CASES[name]
+    H, R = make_pair(w, dev, order=order)
+    r0 = R.residual_norm_zero()
+    for k in range(4):
+        rel = H.vcycle()
+        R.vcycle(order=order)
+        assert relerr(H.get_solution(), R.get_phi()) < TOL, "cycle %d" % (k + 1)
+        rel_o = R.residual_norm() / r0
+        assert abs(rel - rel_o) <= HIST_REL * rel_o + HIST_FLOOR
+
+
+@pytest.mark.parametrize("order_opt", [0, 1, 2])
+@pytest.mark.parametrize("name", ["ball32", "random17x12x10", "holes32", "blob48x32x40"])
+def test_solve_parity(dev, name, order_opt):
+    w = CASES[name]
+    tol = w.get("tol", 1e-9)
+    H, R = make_pair(w, dev, order=order_opt)
+    st, info = H.solve(tol, 80)
+    st_o, info_o = R.solve(tol, 80, order=order_opt)
+    assert st == st_o
+    for key in ("cycles", "order", "switched"):
+        assert info[key] == info_o[key], key
+    assert info["r_zero"] == pytest.approx(info_o["r_zero"], rel=1e-13)
+    ho, hg = info_o["hist"], info["hist"]
+    assert hg.shape == ho.shape
+    assert (np.abs(hg - ho) <= HIST_REL * ho + HIST_FLOOR * info_o["r_zero"]).all()
+    assert relerr(H.get_solution(), R.get_phi()) < TOL
+    assert H.hold == R.hold
+
+
+def test_small_islands_switch_and_hold(dev):
+    """The 64^3 cube with holes: second order stalls, the switch picks first
+    order within a few cycles and holds it for the next 10 solves."""
+    w = W.holes(64)
+    H, R = make_pair(w, dev)
+    for s in range(12):
+        H.set_solution(None)
+        R.set_phi(None)
+        st, info = H.solve(1e-8, 80)
+        st_o, info_o = R.solve(1e-8, 80)
+        assert st == st_o == 0
+        assert (info["cycles"], info["order"], info["switched"]) == (info_o["cycles"], info_o["order"],
+                                                                    info_o["switched"])
+        assert H.hold == R.hold
+        assert relerr(H.get_solution(), R.get_phi()) < TOL
+    assert info["switched"] == 1  # solve 12 is back in second order and trips again
+
+
+def test_dirichlet_from_coarse(dev):
+    w = CASES["blob48x32x40"]
+    H, R = make_pair(w, dev)
+    assert H.residual_norm()[1] == pytest.approx(R.residual_norm_zero(), rel=1e-13)
+    with pytest.raises(B.MGError) as e:
+        H.set_dirichlet_from_coarse(w["phi_c"][1:, 1:, 1:].copy(), (0, 0, 0))
+    assert e.value.status == B.MG_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# API behaviour and edge cases
+# ---------------------------------------------------------------------------
+
+def test_host_and_device_inputs_agree(dev):
+    w = CASES["random17x12x10"]
+    out = []
+    for to in (lambda a: a, lambda a: torch.from_numpy(a).to(dev)):
+        H = B.Hierarchy(to(w["mask"]), w["h"])
+        H.set_rhs(to(w["rho"]))
+        H.set_dirichlet(*(to(a) for a in w["faces"]))
+        H.solve(1e-10, 40)
+        out.append(H.get_solution())
+        tgt = torch.zeros(w["mask"].shape, dtype=torch.float64, device=dev)
+        H.get_solution(tgt)
+        torch.cuda.synchronize()
+        assert np.array_equal(tgt.cpu().numpy(), out[-1])
+    assert np.array_equal(out[0], out[1])
+
+
+def test_deterministic(dev):
+    w = CASES["holes32"]
+    sols = []
+    for _ in range(2):
+        H, _ = make_pair(w, dev)
+        H.solve(1e-9, 60)
+        sols.append(H.get_solution())
+    assert np.array_equal(sols[0], sols[1])
+
+
+def test_update_mask_matches_fresh(dev):
+    a, b = CASES["ball32"], W.ball(32, radius=0.3)
+    H = B.Hierarchy(a["mask"], a["h"])
+    H.update_mask(b["mask"])
+    H.set_rhs(b["rho"])
+    H.set_dirichlet(b["bx"], b["by"], b["bz"])
+    st, info = H.solve(1e-10, 40)
+    F = B.Hierarchy(b["mask"], b["h"])
+    F.set_rhs(b["rho"])
+    F.set_dirichlet(b["bx"], b["by"], b["bz"])
+    st2, info2 = F.solve(1e-10, 40)
+    assert st == st2 == 0 and info["cycles"] == info2["cycles"]
+    assert np.array_equal(H.get_solution(), F.get_solution())
+    with pytest.raises(B.MGError) as e:
+        H.update_mask(np.zeros_like(b["mask"]))
+    assert e.value.status == B.MG_ERR_EMPTY_DOMAIN
+    H.set_solution(None)
+    H.set_rhs(b["rho"])
+    H.set_dirichlet(b["bx"], b["by"], b["bz"])
+    assert H.solve(1e-10, 40)[0] == 0  # the previous mask is still in force
+
+
+def test_errors(dev):
+    with pytest.raises(B.MGError) as e:
+        B.Hierarchy(np.zeros((4, 4, 4), np.int8), 0.25)
+    assert e.value.status == B.MG_ERR_EMPTY_DOMAIN
+    w = CASES["ball32"]
+    H = B.Hierarchy(w["mask"], w["h"])
+    H.set_rhs(w["rho"])
+    st, info = H.solve(1e-14, 2)
+    assert st == B.MG_ERR_NOT_CONVERGED and info["cycles"] == 2
+    st, info = H.solve(1e-10, 40)  # still usable afterwards
+    assert st == 0
+    bad = w["rho"].copy()
+    bad[16, 16, 16] = np.nan
+    H.set_rhs(bad)
+    H.set_solution(None)
+    st, info = H.solve(1e-10, 5)
+    assert st == B.MG_ERR_DIVERGED
+    H.set_rhs(np.zeros_like(w["rho"]))
+    H.set_solution(np.ones_like(w["rho"]))
+    st, info = H.solve(1e-10, 5)
+    assert st == 0 and info["cycles"] == 0 and not H.get_solution().any()
+
+
+def test_launch_counter_and_timing(dev):
+    w = CASES["ball64"]
+    H, _ = make_pair(w, dev)
+    n0 = B.mg_launch_count()
+    B.mg_timing_enable(H.handle, True)
+    H.vcycle(want_rel=False)
+    n, ms = B.mg_timing_read(H.handle)
+    assert B.mg_launch_count() > n0
+    assert n == 8 and ms > 0  # 2 pre + 2 post sweeps of 2 half-sweeps on level 0
+
+
+# ---------------------------------------------------------------------------
+# Full-size checks at the benchmark workload (256^3 union of spheres)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_full_size_sphere_union_256(dev):
+    from oracle import oracle as O
+    w = W.sphere_union(256)
+    H, R = make_pair(w, dev)
+    # two V-cycles from zero: every cell against the oracle
+    H2 = B.Hierarchy(torch.from_numpy(w["mask"]).to(dev), w["h"], order=1)
+    H2.set_rhs(torch.from_numpy(w["rho"]).to(dev))
+    for _ in range(2):
+        H2.vcycle(want_rel=False)
+        R.vcycle(order=1)
+    assert relerr(H2.get_solution(), R.get_phi()) < TOL
+    # the full solve: its residual re-evaluated by the oracle's operator
+    st, info = H.solve(1e-8, 100)
+    assert st == 0 and info["rel"] < 1e-8
+    phi = H.get_solution()
+    S0 = np.where(w["mask"] > 0, 1, -1).astype(np.int64)
+    r = O.residual(S0, 0, 2, w["h"], phi, w["rho"])
+    rel_o = np.sqrt((r ** 2).sum()) / R.residual_norm_zero()
+    assert rel_o < 1e-8 * (1 + 1e-6)
+    assert rel_o == pytest.approx(info["rel"], rel=1e-5)
+
+
+def _host_mem_gb():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError):
+        return 0
+
+
+@pytest.mark.slow
+def test_full_size_holes_512_residual_property(dev):
+    """512^3 cube with 20000 sub-cell holes: the solve reaches 1e-8 (it needs
+    the first-order fix) and the oracle's operator confirms the residual."""
+    if _host_mem_gb() < 48:
+        pytest.skip("needs ~8 GB of host memory for the oracle residual")
+    from oracle import oracle as O
+    w = W.holes(512)
+    H = B.Hierarchy(torch.from_numpy(w["mask"]).to(dev), w["h"])
+    H.set_rhs(torch.from_numpy(w["rho"]).to(dev))
+    st, info = H.solve(1e-8, 200)
+    assert st == 0 and info["order"] == 1
+    phi = H.get_solution()
+    S0 = np.where(w["mask"] > 0, 1, -1).astype(np.int64)
+    act = w["mask"] > 0
+    r = O.residual(S0, 0, 2, w["h"], phi, w["rho"])
+    r0 = np.sqrt((w["rho"][act] ** 2).sum())
+    rel_o = np.sqrt((r ** 2).sum()) / r0
+    assert rel_o == pytest.approx(info["rel"], rel=1e-5)
