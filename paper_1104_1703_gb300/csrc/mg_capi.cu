@@ -533,7 +533,7 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
   const size_t nfx = (size_t)(g.nx + 1) * g.ny * g.nz, nfy = (size_t)g.nx * (g.ny + 1) * g.nz,
                nfz = (size_t)g.nx * g.ny * (g.nz + 1);
   const void *dx = nullptr, *dy = nullptr, *dz = nullptr;
-  if (where == MG_MEM_HOST) CKS(ensure_staging(H, sizeof(double) * (nfx + nfy + nfz) + 512));
+  if (where == MG_MEM_HOST && (bx || by || bz)) CKS(ensure_staging(H, sizeof(double) * (nfx + nfy + nfz) + 512));
   size_t o2 = ((sizeof(double) * nfx + 255) & ~(size_t)255);
   size_t o3 = o2 + ((sizeof(double) * nfy + 255) & ~(size_t)255);
   if (bx) CKS(device_view(H, bx, where, sizeof(double) * nfx, 0, &dx));
