@@ -241,6 +241,41 @@ mg_status mg_level_restrict(mg_hierarchy* hier, int level, int order);
 mg_status mg_level_prolong(mg_hierarchy* hier, int level, int order);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free residual norm
+ * ------------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory.  Examples are AMR codes and frameworks
+ * that reserve the GPU's memory up front in their own pool, where a
+ * cudaMalloc outside the pool can fail, and host code that must not block
+ * on the allocator.  It computes ||r|| = ||Laplacian(Phi) - rho||_2 over the
+ * active cells of a fine level (the operator of mg_residual_norm: Section 2
+ * stencil with the Section 3 ghost faces at theta = 1/2 through the face
+ * values) directly from the caller's device buffers, with no hierarchy and
+ * no allocation of any kind (no cudaMalloc, cudaFree or allocating library
+ * call).
+ *  mask, phi, rho   device, nx*ny*nz, natural layout (as mg_create_hierarchy,
+ *                   mg_set_solution and mg_set_rhs); values of phi and rho on
+ *                   inactive cells are ignored.
+ *  bx, by, bz       device face arrays as in mg_set_dirichlet; NULL = 0.
+ *  nx, ny, nz       1..2048 each; larger sizes return MG_ERR_INVALID_ARG.
+ *  h                fine cell size, > 0.
+ *  norm_out         device pointer to one double that receives ||r||.
+ *  cuda_stream      stream of the current device (NULL: legacy default).
+ * The work is enqueued on the stream and the call returns without waiting;
+ * norm_out is valid once the stream reaches that point.  Scratch: 4096
+ * doubles (32 KB) of static device memory in the library, which every GPU
+ * that loads the library holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device before any stream capture.  All calls on
+ * a device share the array: calls that can overlap on the GPU (different
+ * streams, no ordering between them) race on it and must be serialised by
+ * the caller.  Errors (mg_last_error(NULL)): INVALID_ARG, CUDA. */
+mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* phi, const double* rho, const double* bx,
+                                   const double* by, const double* bz, int nx, int ny, int nz, double h,
+                                   double* norm_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation
  * ------------------------------------------------------------------------- */
 

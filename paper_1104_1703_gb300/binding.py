@@ -69,6 +69,7 @@ SIGNATURES = {
     "mg_level_smooth": (_i, [_vp, _i, _i, _i]),
     "mg_level_restrict": (_i, [_vp, _i, _i]),
     "mg_level_prolong": (_i, [_vp, _i, _i]),
+    "mg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp]),
     "mg_launch_count": (ctypes.c_ulonglong, []),
     "mg_timing_enable": (_i, [_vp, _i]),
     "mg_timing_read": (_i, [_vp, _vp, _vp]),
@@ -292,6 +293,28 @@ def mg_level_restrict(h, level, order):
 
 def mg_level_prolong(h, level, order):
     _check(lib().mg_level_prolong(h, level, order), h)
+
+
+def mg_residual_norm_noalloc(mask, phi, rho, h, norm_out, bx=None, by=None, bz=None, stream=None):
+    """Enqueues ||Laplacian(Phi) - rho|| of the fine level into norm_out (a
+    one-element float64 CUDA tensor) from CUDA tensors, allocating nothing."""
+    nz, ny, nx = mask.shape
+    args = []
+    for name, a, dt, shape in (("mask", mask, np.int8, (nz, ny, nx)), ("phi", phi, np.float64, (nz, ny, nx)),
+                               ("rho", rho, np.float64, (nz, ny, nx)), ("bx", bx, np.float64, (nz, ny, nx + 1)),
+                               ("by", by, np.float64, (nz, ny + 1, nx)), ("bz", bz, np.float64, (nz + 1, ny, nx))):
+        if a is None:
+            args.append(None)
+            continue
+        p, where, keep = _in(a, dt, shape, name)
+        if where != MG_MEM_DEVICE:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        args.append(p)
+    p_out, where, keep = _in(norm_out, np.float64, (1,), "norm_out")
+    if where != MG_MEM_DEVICE:
+        raise ValueError("norm_out must be a CUDA tensor")
+    _check(lib().mg_residual_norm_noalloc(args[0], args[1], args[2], args[3], args[4], args[5], nx, ny, nz,
+                                          float(h), p_out, stream))
 
 
 def mg_launch_count() -> int:

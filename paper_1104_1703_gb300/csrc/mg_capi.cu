@@ -21,11 +21,18 @@ void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_or
 
 }  // namespace gbmg
 
+namespace {
+thread_local std::string t_last_error = "no error";
+}  // namespace
+
+namespace gbmg {
+// Sets the message mg_last_error(NULL) returns on this thread.
+void set_thread_error(const char* msg) { t_last_error = msg; }
+}  // namespace gbmg
+
 using namespace gbmg;
 
 namespace {
-
-thread_local std::string t_last_error = "no error";
 
 struct Arena {
   size_t used = 0;

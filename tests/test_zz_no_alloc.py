@@ -1,0 +1,71 @@
+"""The allocation-free residual norm (mg_residual_norm_noalloc) against the
+hierarchy's mg_residual_norm on the same data, two calls in a row.
+
+This entry point exists for callers that cannot allocate device memory
+(frameworks that keep the GPU's memory in their own pool, host code that
+must not block on the allocator); its scratch is a fixed static device
+array, so consecutive calls reuse it and must each see their own data only.
+The file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1104_1703_gb300 import binding as B  # noqa: E402
+from paper_1104_1703_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _case(kind):
+    if kind == "random":
+        shape = (10, 12, 17)
+        mask = W.random_mask(shape, seed=901, p_active=0.7)
+        return mask, W.random_field(shape, 902), W.random_faces(shape, 903), 0.07
+    if kind == "ball":
+        w = W.ball(64)
+        return w["mask"], w["rho"], (w["bx"], w["by"], w["bz"]), w["h"]
+    w = W.sphere_union(256)  # needs more blocks than the scratch holds: grid-stride path
+    return w["mask"], w["rho"], (None, None, None), w["h"]
+
+
+@pytest.mark.parametrize("kinds", [("random", "ball"), ("ball", "union")])
+def test_noalloc_norm_matches_hierarchy_norm_twice(kinds):
+    assert torch.cuda.is_available()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    out = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
+    for call, kind in enumerate(kinds):
+        mask, rho, faces, h = _case(kind)
+        phi = W.random_field(mask.shape, 904 + call)
+        H = B.Hierarchy(mask, h)
+        H.set_rhs(rho)
+        if faces[0] is not None:
+            H.set_dirichlet(*faces)
+        H.set_solution(phi)
+        H.vcycle(want_rel=False)          # a solution the smoother produced
+        phi_now = H.get_solution()
+        ref, _ = H.residual_norm()
+        to = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        B.mg_residual_norm_noalloc(to(mask), to(phi_now), to(rho), h, out, *(to(f) for f in faces))
+        torch.cuda.synchronize()
+        got = float(out.item())
+        assert abs(got - ref) <= TOL * ref, (call, kind, got, ref)
+        H.close()
+
+
+def test_noalloc_rejects_bad_sizes():
+    dev = torch.device("cuda:0")
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    m = torch.ones((2, 2, 2), dtype=torch.int8, device=dev)
+    f = torch.zeros((2, 2, 2), dtype=torch.float64, device=dev)
+    lib = B.lib()
+    st = lib.mg_residual_norm_noalloc(m.data_ptr(), f.data_ptr(), f.data_ptr(), None, None, None, 4096, 2, 2,
+                                      0.5, out.data_ptr(), None)
+    assert st == B.MG_ERR_INVALID_ARG and "1..2048" in B.mg_last_error()
+    st = lib.mg_residual_norm_noalloc(m.data_ptr(), f.data_ptr(), f.data_ptr(), None, None, None, 2, 2, 2,
+                                      -1.0, out.data_ptr(), None)
+    assert st == B.MG_ERR_INVALID_ARG
