@@ -284,10 +284,12 @@ mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* phi, const 
 unsigned long long mg_launch_count(void);
 
 /* Kernel timing: when enabled, every launch of the fine-level (level 0)
- * Gauss-Seidel half-sweep kernel issued outside a graph is bracketed by CUDA
- * events on the hierarchy's stream.  mg_timing_read synchronises the stream
- * and returns the number of timed launches and their total time in ms, then
- * resets the accumulators.  Errors: CUDA. */
+ * Gauss-Seidel half-sweep kernel is bracketed by CUDA events on the stream
+ * it runs on (inside the replayed graph when use_graphs is set; those are
+ * accumulated each time mg_solve or mg_vcycle with a non-null output waits
+ * for a cycle).  mg_timing_read synchronises the stream and returns the
+ * number of timed launches and their total time in ms, then resets the
+ * accumulators.  Errors: CUDA. */
 mg_status mg_timing_enable(mg_hierarchy* hier, int enable);
 mg_status mg_timing_read(mg_hierarchy* hier, long long* launches, double* total_ms);
 

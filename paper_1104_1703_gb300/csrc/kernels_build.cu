@@ -270,6 +270,87 @@ __global__ void combine_rhs_kernel(long long total, const double* __restrict__ r
   }
 }
 
+// Stream compaction of the active cells of one colour, in slot order
+// (k, j, q), in three passes: per-block counts, one-block exclusive scan,
+// per-block ordered writes.  Slot e = (k*ny + j)*hx + q.
+constexpr int kListThreads = 256;
+
+__device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, uint8_t bit, long long e,
+                                            long long n, long long& at, int& j, int& k) {
+  if (e >= n) return false;
+  const int q = (int)(e % g.hx);
+  const long long t = e / g.hx;
+  j = (int)(t % g.ny);
+  k = (int)(t / g.ny);
+  at = g.at(q, j, k);
+  return (code[at] & bit) != 0;
+}
+
+__global__ void __launch_bounds__(kListThreads) list_count_kernel(Geom g, const uint8_t* __restrict__ code,
+                                                                  uint8_t bit, uint32_t* block_counts) {
+  const long long n = (long long)g.hx * g.ny * g.nz;
+  const long long e = blockIdx.x * (long long)kListThreads + threadIdx.x;
+  long long at;
+  int j, k;
+  const bool m = list_member(g, code, bit, e, n, at, j, k);
+  const int cnt = __syncthreads_count(m);
+  if (threadIdx.x == 0) block_counts[blockIdx.x] = (uint32_t)cnt;
+}
+
+// exclusive scan of nb block counts in place (one block of 1024 threads);
+// the total goes to *count
+__global__ void __launch_bounds__(1024) list_scan_kernel(uint32_t* block_counts, int nb, uint32_t* count) {
+  __shared__ uint32_t part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+  uint32_t sum = 0;
+  for (int b = b0; b < b1; ++b) sum += block_counts[b];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
+    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t c = block_counts[b];
+    block_counts[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) *count = part[1023];
+}
+
+__global__ void __launch_bounds__(kListThreads) list_write_kernel(Geom g, const uint8_t* __restrict__ code,
+                                                                  int colour, uint8_t bit,
+                                                                  const uint32_t* __restrict__ block_offsets,
+                                                                  uint32_t* list) {
+  __shared__ uint32_t warp_base[kListThreads / 32];
+  const long long n = (long long)g.hx * g.ny * g.nz;
+  const long long e = blockIdx.x * (long long)kListThreads + threadIdx.x;
+  long long at = 0;
+  int j = 0, k = 0;
+  const bool m = list_member(g, code, bit, e, n, at, j, k);
+  const unsigned bal = __ballot_sync(0xffffffffu, m);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_base[w] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kListThreads / 32; ++i) {
+      const uint32_t c = warp_base[i];
+      warp_base[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (m) {
+    const uint32_t pos = block_offsets[blockIdx.x] + warp_base[w] + __popc(bal & ((1u << lane) - 1u));
+    list[pos] = (uint32_t)at | (((colour ^ j ^ k) & 1) ? kListPlusX : 0u);
+  }
+}
+
 int grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -297,6 +378,21 @@ cudaError_t launch_mask_coarsen(const LevelDev& Lf, const int8_t* mask_if_fine, 
 cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2, cudaStream_t s) {
   count_launch();
   coarse_coeffs_kernel<<<grid_for(Lc.g.ncells()), kThreads, 0, s>>>(Lc, counts2);
+  return cudaGetLastError();
+}
+
+long long list_scratch_words(const Geom& g) {
+  return ((long long)g.hx * g.ny * g.nz + kListThreads - 1) / kListThreads + 1;
+}
+
+cudaError_t launch_build_list(const Geom& g, const uint8_t* code, int colour, uint8_t bit, uint32_t* list,
+                              uint32_t* count, uint32_t* block_scratch, cudaStream_t s) {
+  const long long n = (long long)g.hx * g.ny * g.nz;
+  const int nb = (int)((n + kListThreads - 1) / kListThreads);
+  count_launch(3);
+  list_count_kernel<<<nb, kListThreads, 0, s>>>(g, code, bit, block_scratch);
+  list_scan_kernel<<<1, 1024, 0, s>>>(block_scratch, nb, count);
+  list_write_kernel<<<nb, kListThreads, 0, s>>>(g, code, colour, bit, block_scratch, list);
   return cudaGetLastError();
 }
 

@@ -15,22 +15,21 @@
 // The level-0 Dirichlet terms are folded into b once, outside the cycle.
 // The coarse right-hand side is b_{l+1} = h_{l+1}^2 (-R1(r_l)) = -1/2 sum of
 // the 8 children's r^ (h_{l+1} = 2 h_l, R1 = mean of 8).
+//
+// On GB300 every one of these kernels is bound by the FP64 pipe (2 FP64
+// lane-operations per clock per SM), not by HBM, and a warp instruction
+// costs the pipe the same whether or not its lanes are predicated off.  So
+// the kernels run over compact lists of the unknowns (built once per mask),
+// where every lane holds an unknown, and issue as few FP64 instructions as
+// the operator allows.  Neighbour values come through L1/L2.
+
 #include "mg_internal.h"
 
 namespace gbmg {
 
 namespace {
 
-// P2 weights (Section 2, Fig. 3): per axis a fine cell takes 3/4 of its
-// parent and 1/4 of the coarse neighbour on its side.  kWyz[py*2+pz][b*2+e]
-// is the y-z weight of coarse rows Ya+b, Za+e for a fine cell whose y and z
-// parities are py, pz (Ya = (j-1)>>1, Za = (k-1)>>1).
-__constant__ double kWyz[4][4] = {
-    {0.0625, 0.1875, 0.1875, 0.5625},  // py=0 (0.25,0.75) x pz=0 (0.25,0.75)
-    {0.1875, 0.0625, 0.5625, 0.1875},  // py=0 x pz=1 (0.75,0.25)
-    {0.1875, 0.5625, 0.0625, 0.1875},  // py=1 x pz=0
-    {0.5625, 0.1875, 0.1875, 0.0625},  // py=1 x pz=1
-};
+constexpr int kBlockX = 32, kBlockY = 4;
 
 // KIND 0: level 0 (D from the ghost-face count); 1: coarse, second order
 // (per-cell D and 1/D); 2: coarse, first order (D = 6).
@@ -60,46 +59,80 @@ __device__ __forceinline__ void init_tab(double* tab) {
   __syncthreads();
 }
 
-struct SweepArgs {
+// x offset of the non-shared x-neighbour of a colour-c cell in row (j, k)
+__device__ __forceinline__ int x_offset(int c, int j, int k) { return ((c ^ j ^ k) & 1) ? 1 : -1; }
+
+constexpr int kListBlock = 256;
+
+struct ListArgs {
   Geom g;
-  double* self;
-  const double* other;
+  double* self;          // Phi of the listed colour
+  const double* other;   // Phi of the other colour
   const double* rhs;
   const double* invd;
+  const double* diag;
   const uint8_t* code;
-  int colour;
-  uint8_t bit;
-  int kchunk;
+  const uint32_t* list;
+  const uint32_t* count;
+  double* res;
+  double* partials;
 };
 
-// K4: one colour of a red-black Gauss-Seidel sweep (Section 2).  A thread
-// owns slot (q, j) and marches through kchunk planes keeping the z
-// neighbours in registers; the same-slot value of the other colour is one of
-// the two x-neighbours.
+// K4: one colour of a red-black Gauss-Seidel sweep (Section 2) over the
+// compact list of that colour's unknowns: every lane of every warp updates
+// an unknown, so no FP64 issue slot is spent on a predicated-off lane.
 template <int KIND>
-__global__ void __launch_bounds__(128) half_sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs a) {
   __shared__ double tab[8];
   if (KIND == 0) init_tab(tab);
   const Geom g = a.g;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k0 = blockIdx.z * a.kchunk;
-  if (q >= g.hx || j >= g.ny || k0 >= g.nz) return;
-  const int k1 = min(g.nz, k0 + a.kchunk);
-  const double* __restrict__ o = a.other;
-  long long at = g.at(q, j, k0);
-  double zm = o[at - g.sz], z0 = o[at];
-  for (int k = k0; k < k1; ++k, at += g.sz) {
-    const double zp = o[at + g.sz];
-    const uint8_t code = a.code[at];
-    if (code & a.bit) {
-      const int dx = ((a.colour ^ j ^ k) & 1) ? 1 : -1;
-      const double s = ((z0 + o[at + dx]) + (o[at - g.P] + o[at + g.P])) + (zm + zp);
-      a.self[at] = (s - a.rhs[at]) * inv_diag<KIND>(code, a.invd, at, tab);
-    }
-    zm = z0;
-    z0 = zp;
+  const uint32_t n = *a.count;
+  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
+    const uint32_t e = a.list[i];
+    const long long at = e & kListAt;
+    const double s = nbr_sum(a.other, at, (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+    const uint8_t code = KIND == 0 ? a.code[at] : 0;
+    a.self[at] = (s - a.rhs[at]) * inv_diag<KIND>(code, a.invd, at, tab);
   }
+}
+
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ void block_reduce_store(double acc, double* out) {
+  __shared__ double warp_sums[32];
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+  __syncthreads();
+  if (t < 32) {
+    double v = t < nw ? warp_sums[t] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (t == 0) *out = v;
+  }
+}
+
+// Scaled residual r^ = sum_nbr Phi_j - D Phi_i - b of the listed unknowns
+// (Section 2, recipe step 2).  NORM = false stores it for the restriction;
+// NORM = true sums r^2 per block into partials[blockIdx.x] (K9, first pass;
+// the grid is fixed per level, so the partials do not depend on scheduling).
+template <int KIND, bool NORM>
+__global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs a) {
+  const Geom g = a.g;
+  const uint32_t n = *a.count;
+  double acc = 0.0;
+  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
+    const uint32_t e = a.list[i];
+    const long long at = e & kListAt;
+    const double s = nbr_sum(a.other, at, (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+    const uint8_t code = KIND == 0 ? a.code[at] : 0;
+    const double r = fma(-diag_of<KIND>(code, a.diag, at), a.self[at], s) - a.rhs[at];
+    if (NORM)
+      acc = fma(r, r, acc);
+    else
+      a.res[at] = r;
+  }
+  if (NORM) block_reduce_store(acc, a.partials + blockIdx.x);
 }
 
 struct SmallArgs {
@@ -116,18 +149,35 @@ struct SmallArgs {
   int sweeps;
 };
 
+constexpr int kSmallThreads = 512;
+constexpr int kSmallSmemBytes = 96 * 1024;
+
 // Several full sweeps of a small level inside one CTA (no launch per
-// half-sweep); __syncthreads separates the colours.
-template <int KIND>
-__global__ void __launch_bounds__(512) smooth_small_kernel(SmallArgs a) {
+// half-sweep); __syncthreads separates the colours.  With SMEM the two
+// colour arrays of Phi (halo included) are staged in shared memory for the
+// whole call, so every neighbour read is an on-chip load.
+template <int KIND, bool SMEM>
+__global__ void __launch_bounds__(kSmallThreads) smooth_small_kernel(SmallArgs a) {
+  extern __shared__ double sm[];
   __shared__ double tab[8];
   if (KIND == 0) init_tab(tab);
   const Geom g = a.g;
+  double* p0 = a.phi0;
+  double* p1 = a.phi1;
+  if (SMEM) {
+    p0 = sm;
+    p1 = sm + g.total;
+    for (long long e = threadIdx.x; e < g.total; e += blockDim.x) {
+      p0[e] = a.phi0[e];
+      p1[e] = a.phi1[e];
+    }
+    __syncthreads();
+  }
   const int n = g.hx * g.ny * g.nz;
   for (int s = 0; s < a.sweeps; ++s) {
     for (int c = 0; c < 2; ++c) {
-      double* self = c ? a.phi1 : a.phi0;
-      const double* o = c ? a.phi0 : a.phi1;
+      double* self = c ? p1 : p0;
+      const double* o = c ? p0 : p1;
       const double* rhs = c ? a.rhs1 : a.rhs0;
       const double* invd = c ? a.invd1 : a.invd0;
       const uint8_t* code = c ? a.code1 : a.code0;
@@ -136,162 +186,130 @@ __global__ void __launch_bounds__(512) smooth_small_kernel(SmallArgs a) {
         const long long at = g.at(q, j, k);
         const uint8_t cd = code[at];
         if (!(cd & a.bit)) continue;
-        const int dx = ((c ^ j ^ k) & 1) ? 1 : -1;
-        self[at] = (nbr_sum(o, at, dx, g.P, g.sz) - rhs[at]) * inv_diag<KIND>(cd, invd, at, tab);
+        self[at] = (nbr_sum(o, at, x_offset(c, j, k), g.P, g.sz) - rhs[at]) * inv_diag<KIND>(cd, invd, at, tab);
       }
       __syncthreads();
+    }
+  }
+  if (SMEM) {
+    for (long long e = threadIdx.x; e < g.total; e += blockDim.x) {
+      a.phi0[e] = p0[e];
+      a.phi1[e] = p1[e];
     }
   }
 }
 
 struct RestrictArgs {
   Geom gf, gc;
-  const double* phi[2];
-  const double* rhs[2];
-  const double* diag[2];
+  const double* res[2];
   const uint8_t* code[2];
   uint8_t bit;
   double* crhs[2];
   double* cphi[2];
 };
 
-// K5: scaled residual of the fine level, R1 into the coarse right-hand side
-// (b_c = -1/2 sum of the children's r^), dPhi_c = 0 (Section 2, recipe steps
-// 2-5).  One thread per coarse cell; its children in x are both at slot I of
-// the four child rows.  With BLACK_ZERO the last fine operation was a full
-// red-black sweep, after which every black cell satisfies its own equation,
-// so only the red children are evaluated.
-template <int KIND, bool BLACK_ZERO>
-__global__ void restrict_kernel(RestrictArgs a) {
+// K5 (second half): R1 of the stored fine residuals into the coarse
+// right-hand side, b_c = -1/2 sum of the children's r^ (Section 2, recipe
+// steps 3-5; Fig. 3), and dPhi_c = 0.  Thread (I, J) of coarse plane K; the
+// two x-children of coarse cell I are both at fine slot I of the child rows.
+// With BLACK_ZERO the last fine operation was a full red-black sweep, after
+// which every black cell satisfies its own equation, so only red children
+// carry a residual.  Children outside the active set (of this order) count 0.
+template <bool BLACK_ZERO>
+__global__ void __launch_bounds__(kBlockX * kBlockY) restrict_sum_kernel(RestrictArgs a) {
   const Geom gf = a.gf, gc = a.gc;
-  const long long n = gc.ncells();
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(idx % gc.nx);
-    const long long t = idx / gc.nx;
-    const int J = (int)(t % gc.ny), K = (int)(t / gc.ny);
-    double sum = 0.0;
+  const int I = blockIdx.x * kBlockX + threadIdx.x;
+  const int J = blockIdx.y * kBlockY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= gc.nx || J >= gc.ny) return;
+  double sum = 0.0;
 #pragma unroll
-    for (int dk = 0; dk < 2; ++dk) {
-      const int k = 2 * K + dk;
-      if (k >= gf.nz) break;
+  for (int dk = 0; dk < 2; ++dk) {
+    const int k = 2 * K + dk;
+    if (k >= gf.nz) break;
 #pragma unroll
-      for (int dj = 0; dj < 2; ++dj) {
-        const int j = 2 * J + dj;
-        if (j >= gf.ny) break;
-        const long long at = gf.at(I, j, k);
+    for (int dj = 0; dj < 2; ++dj) {
+      const int j = 2 * J + dj;
+      if (j >= gf.ny) break;
+      const long long at = gf.at(I, j, k);
 #pragma unroll
-        for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c) {
-          const uint8_t code = a.code[c][at];
-          if (!(code & a.bit)) continue;
-          const int dx = ((c ^ j ^ k) & 1) ? 1 : -1;
-          const double s = nbr_sum(a.phi[1 - c], at, dx, gf.P, gf.sz);
-          const double D = diag_of<KIND>(code, a.diag[c], at);
-          sum += fma(-D, a.phi[c][at], s) - a.rhs[c][at];
-        }
-      }
+      for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c)
+        if (a.code[c][at] & a.bit) sum += a.res[c][at];
     }
-    const int C = (I + J + K) & 1;
-    const long long atc = gc.at(I >> 1, J, K);
-    a.crhs[C][atc] = -0.5 * sum;
-    a.cphi[C][atc] = 0.0;
   }
+  const int C = (I + J + K) & 1;
+  const long long atc = gc.at(I >> 1, J, K);
+  a.crhs[C][atc] = -0.5 * sum;
+  a.cphi[C][atc] = 0.0;
 }
 
 struct ProlongArgs {
   Geom gf, gc;
   double* phi[2];
-  const uint8_t* code[2];
+  const uint32_t* list[2];
+  const uint32_t* count[2];
   const double* cphi[2];
-  uint8_t bit;
 };
 
 __device__ __forceinline__ double coarse_at(const ProlongArgs& a, int X, int Y, int Z) {
   return a.cphi[(X + Y + Z) & 1][a.gc.at(X >> 1, Y, Z)];
 }
 
-// K6: Phi_f += P2(dPhi_c) on active fine cells (Section 2, recipe steps 6-7;
-// Fig. 3).  A thread owns fine slot (q, j, k), i.e. the two x-children
-// i = 2q and 2q+1 of coarse column q, which share the coarse planes
-// Ya..Ya+1, Za..Za+1 and the coarse columns q-1..q+1.  Coarse cells outside
-// Omega_c hold 0 and out-of-box coarse indices read the zero halo.
-__global__ void __launch_bounds__(128) prolong_kernel(ProlongArgs a) {
+// K6: Phi_f += P2(dPhi_c) on the unknowns of the fine level (Section 2,
+// recipe steps 6-7; Fig. 3).  Per axis a fine cell lies 1/4 of a coarse cell
+// from its parent ("near") and 3/4 from the coarse neighbour on its side
+// ("far"); P2 weighs them 3/4 and 1/4, so the 8 corner weights are 27, 9, 3
+// and 1 (/64) for 0, 1, 2 and 3 far axes.  Grouping the corners by weight
+// costs 9 FP64 instructions per fine cell.  Coarse cells outside Omega_c
+// hold 0 and out-of-box coarse indices read the zero halo.
+__global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs a) {
   const Geom gf = a.gf;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (q >= gf.hx || j >= gf.ny || k >= gf.nz) return;
-  const long long at = gf.at(q, j, k);
-  const int c0 = (j + k) & 1;  // colour of i = 2q
-  const bool act0 = a.code[c0][at] & a.bit;
-  const bool act1 = a.code[c0 ^ 1][at] & a.bit;
-  if (!act0 && !act1) return;
-  const int Ya = (j - 1) >> 1, Za = (k - 1) >> 1;
-  const double* w = kWyz[((j & 1) << 1) | (k & 1)];
-  double t[3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    const int X = q - 1 + x;
-    t[x] = w[0] * coarse_at(a, X, Ya, Za);
-    t[x] = fma(w[1], coarse_at(a, X, Ya, Za + 1), t[x]);
-    t[x] = fma(w[2], coarse_at(a, X, Ya + 1, Za), t[x]);
-    t[x] = fma(w[3], coarse_at(a, X, Ya + 1, Za + 1), t[x]);
+  const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
+  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
+    const int c = i >= n0;
+    const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
+    const long long at = e & kListAt;
+    const int rel = (int)(at - gf.off0);
+    const int k = rel / (int)gf.sz;
+    const int rem = rel - k * (int)gf.sz;
+    const int j = rem / gf.P;
+    const int q = rem - j * gf.P;
+    const int ix = 2 * q + ((c ^ j ^ k) & 1);
+    const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+    const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
+    const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
+    const double e0 = coarse_at(a, Xn, Yn, Zn);
+    const double e1 = (coarse_at(a, Xf, Yn, Zn) + coarse_at(a, Xn, Yf, Zn)) + coarse_at(a, Xn, Yn, Zf);
+    const double e2 = (coarse_at(a, Xn, Yf, Zf) + coarse_at(a, Xf, Yn, Zf)) + coarse_at(a, Xf, Yf, Zn);
+    const double e3 = coarse_at(a, Xf, Yf, Zf);
+    const double w = fma(3.0, e2, fma(27.0, e0, 9.0 * e1)) + e3;
+    a.phi[c][at] = fma(w, 1.0 / 64.0, a.phi[c][at]);
   }
-  if (act0) a.phi[c0][at] += fma(0.25, t[0], 0.75 * t[1]);
-  if (act1) a.phi[c0 ^ 1][at] += fma(0.75, t[1], 0.25 * t[2]);
 }
 
 struct NormArgs {
   Geom g;
-  const double* phi[2];
   const double* rhs[2];
-  const double* diag[2];
   const uint8_t* code[2];
   uint8_t bit;
   double* partials;
 };
 
-constexpr int kNormThreads = 256;
-
-// K9 (first pass): per-block sums of r^2 over the active cells (only red
-// cells with RED_ONLY, see BLACK_ZERO above; WITH_PHI false gives the
-// residual of Phi = 0, i.e. -b).  Warp shuffles, then a fixed tree across
-// the block's warps, so the partial of each block is reproducible.
-template <int KIND, bool RED_ONLY, bool WITH_PHI>
-__global__ void __launch_bounds__(kNormThreads) resnorm_kernel(NormArgs a) {
+// sum of b^2 over the active cells (the residual of Phi = 0 is -b)
+__global__ void __launch_bounds__(kNormThreads) rhsnorm_kernel(NormArgs a) {
   const Geom g = a.g;
   const long long per_colour = (long long)g.hx * g.ny * g.nz;
-  const long long n = RED_ONLY ? per_colour : 2 * per_colour;
   double acc = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * per_colour;
        e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e / per_colour);
+    const int c = e >= per_colour;
     const long long r = e - c * per_colour;
     const int q = (int)(r % g.hx);
     const long long t = r / g.hx;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
-    const long long at = g.at(q, j, k);
-    const uint8_t code = a.code[c][at];
-    if (!(code & a.bit)) continue;
-    double res;
-    if (WITH_PHI) {
-      const int dx = ((c ^ j ^ k) & 1) ? 1 : -1;
-      const double s = nbr_sum(a.phi[1 - c], at, dx, g.P, g.sz);
-      res = fma(-diag_of<KIND>(code, a.diag[c], at), a.phi[c][at], s) - a.rhs[c][at];
-    } else {
-      res = a.rhs[c][at];
-    }
-    acc = fma(res, res, acc);
+    const long long at = g.at(q, (int)(t % g.ny), (int)(t / g.ny));
+    if (a.code[c][at] & a.bit) acc = fma(a.rhs[c][at], a.rhs[c][at], acc);
   }
-  __shared__ double warp_sums[kNormThreads / 32];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < kNormThreads / 32 ? warp_sums[threadIdx.x] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = v;
-  }
+  block_reduce_store(acc, a.partials + blockIdx.x);
 }
 
 // K9 (second pass): one CTA sums the partials in a fixed order.
@@ -312,37 +330,62 @@ __global__ void __launch_bounds__(kNormThreads) finalize_kernel(const double* __
 int kind_of(int level, int order) { return level == 0 ? 0 : (order == 1 ? 2 : 1); }
 uint8_t bit_of(int level, int order) { return (level >= 1 && order == 1) ? kActive1 : kActive2; }
 
-int kchunk_for(const Geom& g) {
-  const long long cols = (long long)g.hx * g.ny;
-  const long long target = 152LL * 2048 * 2;  // resident threads x 2
-  long long chunk = (cols * g.nz + target - 1) / target;
-  if (chunk < 1) chunk = 1;
-  if (chunk > g.nz) chunk = g.nz;
-  return (int)chunk;
+// fixed grid of the list kernels of a level: enough blocks for every slot of
+// one colour, at most 16 per SM (grid-stride beyond that)
+int list_grid(const Geom& g) {
+  const long long n = (long long)g.hx * g.ny * g.nz;
+  long long b = (n + kListBlock - 1) / kListBlock;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+bool small_smem(const Geom& g) { return 2 * g.total * (long long)sizeof(double) <= kSmallSmemBytes; }
+
+// level 0 has a single active set, stored under order 2
+int list_order(const LevelDev& L, int order) { return L.level == 0 ? 2 : order; }
+
+ListArgs list_args(const LevelDev& L, int order, int colour) {
+  ListArgs a;
+  a.g = L.g;
+  a.self = L.phi[colour];
+  a.other = L.phi[colour ^ 1];
+  a.rhs = L.rhs[colour];
+  a.invd = L.level ? L.invd[colour] : nullptr;
+  a.diag = L.level ? L.diag[colour] : nullptr;
+  a.code = L.code[colour];
+  a.list = L.list[list_order(L, order)][colour];
+  a.count = L.count + list_order(L, order) * 2 + colour;
+  a.res = L.res[colour];
+  a.partials = nullptr;
+  return a;
 }
 
 }  // namespace
 
 bool small_level(const Geom& g) { return (long long)g.hx * g.ny * g.nz <= 4096; }
 
+cudaError_t init_cycle_kernels() {
+  cudaError_t e = cudaSuccess;
+#define GBMG_SMEM_ATTR(K)                                                                                \
+  if (e == cudaSuccess)                                                                                  \
+    e = cudaFuncSetAttribute(smooth_small_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             kSmallSmemBytes);
+  GBMG_SMEM_ATTR(0)
+  GBMG_SMEM_ATTR(1)
+  GBMG_SMEM_ATTR(2)
+#undef GBMG_SMEM_ATTR
+  return e;
+}
+
 cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, cudaStream_t s) {
-  SweepArgs a;
-  a.g = L.g;
-  a.self = L.phi[colour];
-  a.other = L.phi[colour ^ 1];
-  a.rhs = L.rhs[colour];
-  a.invd = L.level ? L.invd[colour] : nullptr;
-  a.code = L.code[colour];
-  a.colour = colour;
-  a.bit = bit_of(L.level, order);
-  a.kchunk = kchunk_for(L.g);
-  dim3 block(32, 4);
-  dim3 grid((L.g.hx + 31) / 32, (L.g.ny + 3) / 4, (L.g.nz + a.kchunk - 1) / a.kchunk);
+  const ListArgs a = list_args(L, order, colour);
+  const int grid = list_grid(L.g);
   count_launch();
   switch (kind_of(L.level, order)) {
-    case 0: half_sweep_kernel<0><<<grid, block, 0, s>>>(a); break;
-    case 1: half_sweep_kernel<1><<<grid, block, 0, s>>>(a); break;
-    default: half_sweep_kernel<2><<<grid, block, 0, s>>>(a); break;
+    case 0: gs_list_kernel<0><<<grid, kListBlock, 0, s>>>(a); break;
+    case 1: gs_list_kernel<1><<<grid, kListBlock, 0, s>>>(a); break;
+    default: gs_list_kernel<2><<<grid, kListBlock, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -360,41 +403,55 @@ cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, cudaSt
   a.code1 = L.code[1];
   a.bit = bit_of(L.level, order);
   a.sweeps = sweeps;
+  const bool sm = small_smem(L.g);
+  const size_t bytes = sm ? 2 * L.g.total * sizeof(double) : 0;
+  count_launch();
+#define GBMG_SMALL(K)                                                      \
+  if (sm) smooth_small_kernel<K, true><<<1, kSmallThreads, bytes, s>>>(a); \
+  else smooth_small_kernel<K, false><<<1, kSmallThreads, 0, s>>>(a);
+  switch (kind_of(L.level, order)) {
+    case 0: GBMG_SMALL(0) break;
+    case 1: GBMG_SMALL(1) break;
+    default: GBMG_SMALL(2) break;
+  }
+#undef GBMG_SMALL
+  return cudaGetLastError();
+}
+
+// residual of the listed unknowns of one colour into L.res (NORM = false)
+static cudaError_t launch_residual(const LevelDev& L, int order, int colour, cudaStream_t s) {
+  const ListArgs a = list_args(L, order, colour);
+  const int grid = list_grid(L.g);
   count_launch();
   switch (kind_of(L.level, order)) {
-    case 0: smooth_small_kernel<0><<<1, 512, 0, s>>>(a); break;
-    case 1: smooth_small_kernel<1><<<1, 512, 0, s>>>(a); break;
-    default: smooth_small_kernel<2><<<1, 512, 0, s>>>(a); break;
+    case 0: res_list_kernel<0, false><<<grid, kListBlock, 0, s>>>(a); break;
+    case 1: res_list_kernel<1, false><<<grid, kListBlock, 0, s>>>(a); break;
+    default: res_list_kernel<2, false><<<grid, kListBlock, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, cudaStream_t s) {
+  cudaError_t e = launch_residual(Lf, order, 0, s);
+  if (e == cudaSuccess && !black_zero) e = launch_residual(Lf, order, 1, s);
+  if (e != cudaSuccess) return e;
   RestrictArgs a;
   a.gf = Lf.g;
   a.gc = Lc.g;
   for (int c = 0; c < 2; ++c) {
-    a.phi[c] = Lf.phi[c];
-    a.rhs[c] = Lf.rhs[c];
-    a.diag[c] = Lf.level ? Lf.diag[c] : nullptr;
+    a.res[c] = Lf.res[c];
     a.code[c] = Lf.code[c];
     a.crhs[c] = Lc.rhs[c];
     a.cphi[c] = Lc.phi[c];
   }
   a.bit = bit_of(Lf.level, order);
-  long long n = Lc.g.ncells();
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
+  const dim3 grid((Lc.g.nx + kBlockX - 1) / kBlockX, (Lc.g.ny + kBlockY - 1) / kBlockY, Lc.g.nz);
+  const dim3 block(kBlockX, kBlockY);
   count_launch();
-  const int kind = kind_of(Lf.level, order);
-#define GBMG_RESTRICT(K)                                                    \
-  if (black_zero) restrict_kernel<K, true><<<blocks, 256, 0, s>>>(a);       \
-  else restrict_kernel<K, false><<<blocks, 256, 0, s>>>(a);
-  if (kind == 0) { GBMG_RESTRICT(0) }
-  else if (kind == 1) { GBMG_RESTRICT(1) }
-  else { GBMG_RESTRICT(2) }
-#undef GBMG_RESTRICT
+  if (black_zero)
+    restrict_sum_kernel<true><<<grid, block, 0, s>>>(a);
+  else
+    restrict_sum_kernel<false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -404,43 +461,48 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, cu
   a.gc = Lc.g;
   for (int c = 0; c < 2; ++c) {
     a.phi[c] = Lf.phi[c];
-    a.code[c] = Lf.code[c];
+    a.list[c] = Lf.list[list_order(Lf, order)][c];
+    a.count[c] = Lf.count + list_order(Lf, order) * 2 + c;
     a.cphi[c] = Lc.phi[c];
   }
-  a.bit = bit_of(Lf.level, order);
-  dim3 block(32, 4);
-  dim3 grid((Lf.g.hx + 31) / 32, (Lf.g.ny + 3) / 4, Lf.g.nz);
   count_launch();
-  prolong_kernel<<<grid, block, 0, s>>>(a);
+  prolong_list_kernel<<<list_grid(Lf.g), kListBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 int residual_norm_blocks(const Geom& g) {
-  long long n = 2LL * g.hx * g.ny * g.nz;
-  long long b = (n + kNormThreads - 1) / kNormThreads;
-  if (b > 152 * 8) b = 152 * 8;
-  if (b < 1) b = 1;
-  return (int)b;
+  const int plain = 152 * 8;
+  const int lists = 2 * list_grid(g);
+  return lists > plain ? lists : plain;
 }
 
 cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_phi, double* partials,
                                   int max_partials, double* out, cudaStream_t s) {
-  NormArgs a;
-  a.g = L0.g;
-  for (int c = 0; c < 2; ++c) {
-    a.phi[c] = L0.phi[c];
-    a.rhs[c] = L0.rhs[c];
-    a.diag[c] = L0.level ? L0.diag[c] : nullptr;
-    a.code[c] = L0.code[c];
+  int blocks;
+  if (!with_phi) {
+    NormArgs a;
+    a.g = L0.g;
+    for (int c = 0; c < 2; ++c) {
+      a.rhs[c] = L0.rhs[c];
+      a.code[c] = L0.code[c];
+    }
+    a.bit = kActive2;
+    a.partials = partials;
+    blocks = 152 * 8;
+    count_launch();
+    rhsnorm_kernel<<<blocks, kNormThreads, 0, s>>>(a);
+  } else {
+    const int grid = list_grid(L0.g);
+    blocks = red_only ? grid : 2 * grid;
+    if (blocks > max_partials) return cudaErrorInvalidValue;
+    for (int c = 0; c < (red_only ? 1 : 2); ++c) {
+      ListArgs a = list_args(L0, 2, c);
+      a.partials = partials + c * grid;
+      count_launch();
+      res_list_kernel<0, true><<<grid, kListBlock, 0, s>>>(a);
+    }
   }
-  a.bit = kActive2;
-  a.partials = partials;
-  int blocks = residual_norm_blocks(L0.g);
-  if (blocks > max_partials) return cudaErrorInvalidValue;
-  count_launch(2);
-  if (!with_phi) resnorm_kernel<0, false, false><<<blocks, kNormThreads, 0, s>>>(a);
-  else if (red_only) resnorm_kernel<0, true, true><<<blocks, kNormThreads, 0, s>>>(a);
-  else resnorm_kernel<0, false, true><<<blocks, kNormThreads, 0, s>>>(a);
+  count_launch();
   finalize_kernel<<<1, kNormThreads, 0, s>>>(partials, blocks, out);
   return cudaGetLastError();
 }

@@ -17,7 +17,14 @@
 namespace gbmg {
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// While a graph is being captured on this thread, launches are counted into
+// the graph's node count instead (they run only when the graph is replayed).
+static thread_local bool t_capturing = false;
+static thread_local unsigned long long t_captured = 0;
+void count_launch(unsigned long long n) {
+  if (t_capturing) t_captured += n;
+  else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 
 }  // namespace gbmg
 
@@ -47,11 +54,25 @@ struct TimedPair {
   cudaEvent_t a, b;
 };
 
+// A captured multigrid iteration (plus the residual norm and its copy to the
+// pinned host scalar) for one order; replayed once per cycle.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  int deepest = -2;                // deepest level at capture time
+  unsigned long long nodes = 0;    // kernel launches per replay
+  std::vector<TimedPair> events;   // level-0 half-sweep event pairs (timing graphs)
+};
+
 }  // namespace
 
 struct mg_hierarchy {
   mg_options opt;
   cudaStream_t stream = nullptr;
+  cudaStream_t cur = nullptr;          // stream the emitters launch on (stream, or cap_stream while capturing)
+  cudaStream_t cap_stream = nullptr;
+  GraphSlot graphs[3][2];              // [order][timing]
+  std::vector<TimedPair>* cap_events = nullptr;
+  size_t cap_events_used = 0;
   bool own_stream = false;
   int device = 0;
   int nlev = 0;
@@ -63,6 +84,7 @@ struct mg_hierarchy {
   int hold = 0;
   char* arena = nullptr;
   int8_t* mask_dev = nullptr;
+  uint32_t* list_scratch = nullptr;
   double* partials = nullptr;
   int max_partials = 0;
   double* dscal = nullptr;             // device scalars
@@ -77,7 +99,7 @@ struct mg_hierarchy {
   bool timing = false;
   std::vector<TimedPair> events;
   size_t events_used = 0;
-  long long timed_launches = 0;
+  long long timed_launches = 0;   // accumulated from graph replays
   double timed_ms = 0;
 };
 
@@ -189,25 +211,29 @@ mg_status launch_ok(mg_hierarchy* H, cudaError_t e, const char* what) {
 
 mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour) {
   if (l == 0 && H->timing) {
-    if (H->events_used == H->events.size()) {
+    std::vector<TimedPair>& pool = H->cap_events ? *H->cap_events : H->events;
+    size_t& used = H->cap_events ? H->cap_events_used : H->events_used;
+    if (used == pool.size()) {
       TimedPair p;
       CK(H, cudaEventCreate(&p.a));
       CK(H, cudaEventCreate(&p.b));
-      H->events.push_back(p);
+      pool.push_back(p);
     }
-    TimedPair& p = H->events[H->events_used++];
-    CK(H, cudaEventRecord(p.a, H->stream));
-    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->stream), "half-sweep"));
-    CK(H, cudaEventRecord(p.b, H->stream));
+    TimedPair& p = pool[used++];
+    // inside a capture the records become event nodes of the graph
+    const unsigned flags = H->cap_events ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(H, cudaEventRecordWithFlags(p.a, H->cur, flags));
+    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->cur), "half-sweep"));
+    CK(H, cudaEventRecordWithFlags(p.b, H->cur, flags));
     return MG_OK;
   }
-  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->stream), "half-sweep");
+  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->cur), "half-sweep");
 }
 
 mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps) {
   if (sweeps <= 0) return MG_OK;
   if (small_level(H->L[l].g))
-    return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, H->stream), "small-level smoother");
+    return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, H->cur), "small-level smoother");
   for (int s = 0; s < sweeps; ++s) {
     CKS(half_sweep(H, l, order, 0));
     CKS(half_sweep(H, l, order, 1));
@@ -220,10 +246,10 @@ mg_status iteration(mg_hierarchy* H, int l, int order) {
   const mg_options& o = H->opt;
   if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps);
   CKS(smooth(H, l, order, o.n_pre));                                        // step 1
-  CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, H->stream),
+  CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, H->cur),
                 "residual/restriction"));                                    // steps 2-5
   for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order));      // step 5
-  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, H->stream), "prolongation"));  // 6-7
+  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, H->cur), "prolongation"));  // 6-7
   return smooth(H, l, order, o.n_post);                                     // step 8
 }
 
@@ -241,13 +267,89 @@ bool ends_with_sweep(const mg_hierarchy* H, int order) {
   return H->deepest[order] == 0 ? H->opt.coarse_sweeps >= 1 : H->opt.n_post >= 1;
 }
 
-mg_status norm2(mg_hierarchy* H, bool red_only, bool with_phi, double* out) {
+// Enqueues the residual norm (squared, scaled) and its copy to the pinned
+// host scalar on H->cur.
+mg_status emit_norm2(mg_hierarchy* H, bool red_only, bool with_phi) {
   CKS(launch_ok(H, launch_residual_norm2(H->L[0], red_only, with_phi, H->partials, H->max_partials, H->dscal,
-                                        H->stream),
+                                        H->cur),
                 "residual norm"));
-  CK(H, cudaMemcpyAsync(H->hscal, H->dscal, sizeof(double), cudaMemcpyDeviceToHost, H->stream));
+  CK(H, cudaMemcpyAsync(H->hscal, H->dscal, sizeof(double), cudaMemcpyDeviceToHost, H->cur));
+  return MG_OK;
+}
+
+mg_status norm2(mg_hierarchy* H, bool red_only, bool with_phi, double* out) {
+  CKS(emit_norm2(H, red_only, with_phi));
   CK(H, cudaStreamSynchronize(H->stream));
   *out = H->hscal[0];
+  return MG_OK;
+}
+
+void drop_graph(GraphSlot& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.deepest = -2;
+}
+
+// Captures one multigrid iteration of `order` followed by the end-of-cycle
+// residual norm and its copy to the host scalar.
+mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
+  drop_graph(gs);
+  if (!H->cap_stream) CK(H, cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+  H->cur = H->cap_stream;
+  H->cap_events = H->timing ? &gs.events : nullptr;
+  H->cap_events_used = 0;
+  t_capturing = true;
+  t_captured = 0;
+  mg_status st = MG_OK;
+  cudaError_t e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = iteration(H, 0, order);
+    if (st == MG_OK) st = emit_norm2(H, ends_with_sweep(H, order), true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(H->cap_stream, &graph);
+    if (st == MG_OK && e2 == cudaSuccess) {
+      e = cudaGraphInstantiate(&gs.exec, graph, 0);
+      if (e != cudaSuccess) gs.exec = nullptr;
+    } else if (e2 != cudaSuccess) {
+      e = e2;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  t_capturing = false;
+  H->cur = H->stream;
+  H->cap_events = nullptr;
+  if (st != MG_OK) return st;
+  if (e != cudaSuccess || !gs.exec) return cuda_fail(H, e, "graph capture");
+  gs.deepest = H->deepest[order];
+  gs.nodes = t_captured;
+  return MG_OK;
+}
+
+// One multigrid iteration of `order` followed by the end-of-cycle residual
+// norm, replayed from a CUDA graph when use_graphs is set.  If r_out is
+// non-null the stream is synchronised and ||r|| is returned.
+mg_status run_cycle(mg_hierarchy* H, int order, double* r_out) {
+  const bool red_only = ends_with_sweep(H, order);
+  if (!H->opt.use_graphs) {
+    CKS(iteration(H, 0, order));
+    CKS(emit_norm2(H, red_only, true));
+  } else {
+    GraphSlot& gs = H->graphs[order][H->timing ? 1 : 0];
+    if (!gs.exec || gs.deepest != H->deepest[order]) CKS(capture_cycle(H, order, gs));
+    CK(H, cudaGraphLaunch(gs.exec, H->stream));
+    count_launch(gs.nodes);
+  }
+  if (!r_out) return MG_OK;
+  CK(H, cudaStreamSynchronize(H->stream));
+  *r_out = std::sqrt(H->hscal[0]) / (H->h * H->h);
+  if (H->opt.use_graphs && H->timing) {
+    for (auto& p : H->graphs[order][1].events) {
+      float ms = 0;
+      CK(H, cudaEventElapsedTime(&ms, p.a, p.b));
+      H->timed_ms += ms;
+      H->timed_launches += 1;
+    }
+  }
   return MG_OK;
 }
 
@@ -283,6 +385,15 @@ mg_status build_levels(mg_hierarchy* H) {
     CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? H->mask_dev : nullptr, H->L[l + 1], s), "mask R1"));
     CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
   }
+  // compact lists of the unknowns, per order and colour (level 0: one set)
+  for (int l = 0; l < H->nlev; ++l) {
+    LevelDev& L = H->L[l];
+    for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+      for (int c = 0; c < 2; ++c)
+        CKS(launch_ok(H, launch_build_list(L.g, L.code[c], c, o == 2 ? kActive2 : kActive1, L.list[o][c],
+                                           L.count + o * 2 + c, H->list_scratch, s),
+                      "active lists"));
+  }
   unsigned long long hc[2 * kMaxLevels];
   CK(H, cudaMemcpyAsync(hc, H->counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CK(H, cudaStreamSynchronize(s));
@@ -316,6 +427,15 @@ void destroy(mg_hierarchy* H) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
   }
+  for (auto& row : H->graphs)
+    for (auto& g : row) {
+      drop_graph(g);
+      for (auto& p : g.events) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+      }
+    }
+  if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   if (H->staging) cudaFree(H->staging);
   if (H->arena) cudaFree(H->arena);
   if (H->hscal) cudaFreeHost(H->hscal);
@@ -396,13 +516,26 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     }
     H->own_stream = true;
   }
+  H->cur = H->stream;
+  {
+    cudaError_t e0 = init_cycle_kernels();
+    if (e0 != cudaSuccess) {
+      mg_status st = cuda_fail(nullptr, e0, "kernel attributes");
+      destroy(H);
+      return st;
+    }
+  }
   int dims[kMaxLevels][3];
   H->nlev = plan_levels(nx, ny, nz, dims);
+  if (make_geom(nx, ny, nz).total >= (1LL << 31)) {
+    destroy(H);
+    return fail(nullptr, MG_ERR_INVALID_ARG, "grid too large: padded colour arrays must hold < 2^31 elements");
+  }
 
   // one arena for every level array
   Arena A;
   struct Off {
-    size_t phi[2], rhs[2], invd[2], diag[2], code[2], S;
+    size_t phi[2], rhs[2], invd[2], diag[2], code[2], res[2], list[3][2], count, S;
   } off[kMaxLevels];
   for (int l = 0; l < H->nlev; ++l) {
     Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
@@ -412,13 +545,18 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       off[l].phi[c] = A.reserve(sizeof(double) * g.total);
       off[l].rhs[c] = A.reserve(sizeof(double) * g.total);
       off[l].code[c] = A.reserve(g.total);
+      off[l].res[c] = A.reserve(sizeof(double) * g.total);
+      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+        off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)g.hx * g.ny * g.nz);
       if (l > 0) {
         off[l].invd[c] = A.reserve(sizeof(double) * g.total);
         off[l].diag[c] = A.reserve(sizeof(double) * g.total);
       }
     }
     if (l > 0) off[l].S = A.reserve(sizeof(int32_t) * g.ncells());
+    off[l].count = A.reserve(sizeof(uint32_t) * 6);
   }
+  const size_t o_lscr = A.reserve(sizeof(uint32_t) * list_scratch_words(H->L[0].g));
   const Geom& g0 = H->L[0].g;
   size_t o_rhoh2[2], o_bc[2], o_save[2];
   for (int c = 0; c < 2; ++c) {
@@ -453,11 +591,17 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       H->L[l].phi[c] = (double*)(base + off[l].phi[c]);
       H->L[l].rhs[c] = (double*)(base + off[l].rhs[c]);
       H->L[l].code[c] = (uint8_t*)(base + off[l].code[c]);
+      H->L[l].res[c] = (double*)(base + off[l].res[c]);
+      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o) H->L[l].list[o][c] = (uint32_t*)(base + off[l].list[o][c]);
+      if (l == 0) H->L[l].list[1][c] = H->L[l].list[2][c];
+      H->L[l].list[0][c] = nullptr;
       H->L[l].invd[c] = l > 0 ? (double*)(base + off[l].invd[c]) : nullptr;
       H->L[l].diag[c] = l > 0 ? (double*)(base + off[l].diag[c]) : nullptr;
     }
     H->L[l].S = l > 0 ? (int32_t*)(base + off[l].S) : nullptr;
+    H->L[l].count = (uint32_t*)(base + off[l].count);
   }
+  H->list_scratch = (uint32_t*)(base + o_lscr);
   for (int c = 0; c < 2; ++c) {
     H->F.rhoh2[c] = (double*)(base + o_rhoh2[c]);
     H->F.bc[c] = (double*)(base + o_bc[c]);
@@ -617,10 +761,9 @@ mg_status mg_vcycle(mg_hierarchy* H, double* rel_out) {
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   DeviceGuard guard(H->device);
   const int order = kind_order(H);
-  CKS(iteration(H, 0, order));
-  if (!rel_out) return MG_OK;
+  if (!rel_out) return run_cycle(H, order, nullptr);
   double r, r0;
-  CKS(residual(H, ends_with_sweep(H, order), &r));
+  CKS(run_cycle(H, order, &r));
   CKS(residual_zero(H, &r0));
   *rel_out = r0 > 0 ? r / r0 : 0.0;
   if (!std::isfinite(r)) return fail(H, MG_ERR_DIVERGED, "non-finite residual");
@@ -676,9 +819,8 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
                               H->stream));
     double r_prev = r_init;
     for (cycles = 1; cycles <= max_cycles; ++cycles) {
-      CKS(iteration(H, 0, order));
+      CKS(run_cycle(H, order, &r_n));
       n_updates += updates(H, 0, order);
-      CKS(residual(H, ends_with_sweep(H, order), &r_n));
       if (info && cycles <= MG_HIST_MAX) info->hist[cycles] = r_n;
       if (!std::isfinite(r_n)) {
         st = MG_ERR_DIVERGED;
@@ -848,9 +990,11 @@ mg_status mg_timing_read(mg_hierarchy* H, long long* launches, double* total_ms)
     CK(H, cudaEventElapsedTime(&ms, H->events[i].a, H->events[i].b));
     sum += ms;
   }
-  if (launches) *launches = (long long)H->events_used;
-  if (total_ms) *total_ms = sum;
+  if (launches) *launches = (long long)H->events_used + H->timed_launches;
+  if (total_ms) *total_ms = sum + H->timed_ms;
   H->events_used = 0;
+  H->timed_launches = 0;
+  H->timed_ms = 0;
   return MG_OK;
 }
 

@@ -55,7 +55,19 @@ struct LevelDev {
   double* diag[2];   // level >= 1: D of the second-order operator (0 if inactive)
   uint8_t* code[2];  // kActive2 | kActive1 | ghost-face bits
   int32_t* S;        // level >= 1: mask sums, natural layout nx*ny*nz
+  // Compact lists of the unknowns: list[order][colour] holds, in slot order,
+  // the element offset of every active cell of that colour (bits 0..30) and
+  // in bit 31 whether its non-shared x-neighbour is at +1 (else -1).  Level 0
+  // has one active set: list[1] == list[2].  count[order*2 + colour] is the
+  // list length (device memory, so captured graphs stay valid when the mask
+  // changes).
+  uint32_t* list[3][2];
+  uint32_t* count;
+  double* res[2];    // scaled residual r^ of the active cells (restriction input)
 };
+
+constexpr uint32_t kListAt = 0x7fffffffu;
+constexpr uint32_t kListPlusX = 0x80000000u;
 
 struct FineExtra {
   double* rhoh2[2];  // h^2 rho, split layout
@@ -73,6 +85,11 @@ cudaError_t launch_build_fine(const LevelDev& L0, const int8_t* mask, unsigned l
 cudaError_t launch_mask_coarsen(const LevelDev& Lf, const int8_t* mask_if_fine, const LevelDev& Lc,
                                 cudaStream_t s);
 cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2, cudaStream_t s);
+// Compact list of the cells of colour c whose code has `bit`, in slot order;
+// block_scratch holds (slots/256 + 1) uint32.  count receives the length.
+cudaError_t launch_build_list(const Geom& g, const uint8_t* code, int colour, uint8_t bit, uint32_t* list,
+                              uint32_t* count, uint32_t* block_scratch, cudaStream_t s);
+long long list_scratch_words(const Geom& g);
 
 // ---- data movement and boundary data (kernels_build.cu) ----
 // natural (nx*ny*nz) <-> split; `scale` multiplies, `mask_bit` zeroes cells
@@ -93,6 +110,8 @@ cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStrea
 cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, cudaStream_t s);
 cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, cudaStream_t s);
 bool small_level(const Geom& g);
+// One-time kernel attributes (shared-memory opt-in) for the current device.
+cudaError_t init_cycle_kernels();
 // Residual of level Lf restricted into the rhs of Lc as -R1(r) (scaled), dPhi_c = 0.
 // black_zero: the last operation on Lf was a complete red-black sweep, so
 // the black residual vanishes and only red cells are evaluated.

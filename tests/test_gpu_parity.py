@@ -118,7 +118,7 @@ def test_tiny_grids(dev, shape):
 # K4 smoother, K5 residual + R1, K6 P2: per level and order
 # ---------------------------------------------------------------------------
 
-LEVEL_CASES = [("ball64", 0, 2), ("ball64", 1, 2), ("ball64", 1, 1), ("ball64", 2, 2), ("ball64", 2, 1),
+LEVEL_CASES = [("ball64", 0, 2), ("ball64", 0, 1), ("ball64", 1, 2), ("ball64", 1, 1), ("ball64", 2, 2), ("ball64", 2, 1),
                ("ball64", 3, 2), ("random17x12x10", 0, 2), ("random17x12x10", 1, 2), ("holes32", 1, 1),
                ("holes32", 1, 2), ("blob48x32x40", 0, 2), ("blob48x32x40", 1, 2), ("blob48x32x40", 2, 1)]
 
@@ -205,12 +205,13 @@ def test_vcycle_parity(dev, name, order):
         assert abs(rel - rel_o) <= HIST_REL * rel_o + HIST_FLOOR
 
 
+@pytest.mark.parametrize("graphs", [1, 0])
 @pytest.mark.parametrize("order_opt", [0, 1, 2])
 @pytest.mark.parametrize("name", ["ball32", "random17x12x10", "holes32", "blob48x32x40"])
-def test_solve_parity(dev, name, order_opt):
+def test_solve_parity(dev, name, order_opt, graphs):
     w = CASES[name]
     tol = w.get("tol", 1e-9)
-    H, R = make_pair(w, dev, order=order_opt)
+    H, R = make_pair(w, dev, order=order_opt, use_graphs=graphs)
     st, info = H.solve(tol, 80)
     st_o, info_o = R.solve(tol, 80, order=order_opt)
     assert st == st_o
@@ -331,7 +332,7 @@ def test_launch_counter_and_timing(dev):
     H, _ = make_pair(w, dev)
     n0 = B.mg_launch_count()
     B.mg_timing_enable(H.handle, True)
-    H.vcycle(want_rel=False)
+    H.vcycle()
     n, ms = B.mg_timing_read(H.handle)
     assert B.mg_launch_count() > n0
     assert n == 8 and ms > 0  # 2 pre + 2 post sweeps of 2 half-sweeps on level 0
