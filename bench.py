@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 
 from paper_1104_1703_gb300 import workloads as W  # noqa: E402
 
-METRIC = "GS cell-updates/s, FP64 multigrid solve to rel. residual 1e-8"
+METRIC = "GS cell-updates/s of the multigrid solve to rel. residual 1e-8 (time to tolerance in ms_per_step)"
 UNIT = "cell-updates/s"
 TOL = 1e-8
 N = 256
@@ -50,7 +50,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=N)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    p.add_argument("--profile", action="store_true",
+                   help="profiling runs: time the headline form only (no second form, e2e or CPU leg)")
+    p.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                   help="form timed for the headline: 1 = FP32 V-cycles in FP64 refinement, 0 = FP64")
     return p.parse_args()
 
 
@@ -221,6 +224,94 @@ def cpu_baseline(size):
 # our arm
 # --------------------------------------------------------------------------
 
+FORMS = {0: "fp64", 1: "mixed"}
+
+
+class Form:
+    """One solver form (precision 0 = FP64 method, 1 = FP32 V-cycles inside
+    FP64 iterative refinement) on the resident workload."""
+
+    def __init__(self, B, precision, mask_d, rho_d, h, stream):
+        self.B = B
+        self.precision = precision
+        self.H = B.Hierarchy(mask_d, h, stream=stream, precision=precision)
+        self.n_active = self.H.level_info(0)[1]
+
+    def step(self, mask, rho, out=None):
+        H = self.H
+        H.update_mask(mask)
+        H.set_rhs(rho)
+        H.set_dirichlet(None, None, None)
+        H.set_solution(None)
+        st, info = H.solve(TOL, 200)
+        if st != 0:
+            raise RuntimeError("solve failed: status %d rel %.3e" % (st, info["rel"]))
+        if out is not None:
+            H.get_solution(out)
+        return info
+
+
+def time_form(f, args, mask, rho, stream, world, device, out=None, timing=False):
+    """W untimed warm-up steps, then K steps between CUDA events on the
+    library's stream; returns elapsed seconds (max over ranks) and stats."""
+    import torch
+    B = f.B
+    for _ in range(max(3, args.warmup)):
+        f.step(mask, rho, out)
+    torch.cuda.synchronize()
+    barrier(world)
+    if timing:
+        B.mg_timing_enable(f.H.handle, True)
+        B.mg_timing_read(f.H.handle)
+    l0 = B.mg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    updates, cycles, orders = 0, 0, set()
+    for _ in range(args.steps):
+        info = f.step(mask, rho, out)
+        updates += info["cell_updates"]
+        cycles += info["cycles"]
+        orders.add(info["order"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    st = {"launches": B.mg_launch_count() - l0, "cycles": cycles / args.steps, "orders": sorted(orders)}
+    if timing:
+        st["gs_n"], st["gs_ms"] = B.mg_timing_read(f.H.handle)
+        B.mg_timing_enable(f.H.handle, False)
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, device)
+    st["elapsed"] = elapsed
+    st["updates"] = sum_over_ranks(updates, world, device)
+    barrier(world)
+    return st
+
+
+def roofline(st, n_active, precision, peaks):
+    """Roofline of the dominant kernel, the level-0 Gauss-Seidel half-sweep,
+    from its CUDA-event-timed launches inside the timed region.  One launch
+    updates one colour of the unknowns (n_active / 2 on average)."""
+    gs_s = st["gs_ms"] / 1e3 / max(st["gs_n"], 1)
+    half = n_active / 2.0
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    if precision == 0:
+        # 7 FP64 instructions per update; 25 B per update over the red+black sweep
+        fp64_peak = 2 * 152 * 2.07e9 / 1e12
+        ach = 7.0 * half / gs_s / 1e12
+        return {"bound": "alu", "kernel": "gs_list_kernel<0,double> (level-0 red/black Gauss-Seidel, FP64)",
+                "achieved": ach, "peak": fp64_peak, "unit": "T FP64 instr/s", "frac": ach / fp64_peak,
+                "traffic": None, "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6,
+                "peak_source": "nominal FP64 rate: 2 FP64 lane-ops/clk/SM x 152 SMs x 2.07 GHz "
+                               "(1.25 TFLOP/s counting an FMA as 2)",
+                "hbm_view": {"achieved_gbs": 25.0 * half / gs_s / 1e9, "peak_gbs": hbm_peak,
+                             "frac": 25.0 * half / gs_s / 1e9 / hbm_peak, "peak_source": src}}
+    # FP32: read the other colour 4 + b 4 + code 1, write 4 = 13 B per update
+    ach = 13.0 * half / gs_s / 1e9
+    return {"bound": "hbm", "kernel": "gs_list_kernel<0,float> (level-0 red/black Gauss-Seidel, FP32 inner cycle)",
+            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+            "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -238,112 +329,60 @@ def run_ours(args):
     rho_d = torch.from_numpy(w["rho"]).to(device)
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=device)
-    H = B.Hierarchy(mask_d, w["h"], stream=stream.cuda_stream)
-    n_active = H.level_info(0)[1]
+    main = Form(B, args.precision, mask_d, rho_d, w["h"], stream.cuda_stream)
+    n_active = main.n_active
 
-    def step(mask, rho, out=None):
-        H.update_mask(mask)
-        H.set_rhs(rho)
-        H.set_dirichlet(None, None, None)
-        H.set_solution(None)
-        st, info = H.solve(TOL, 200)
-        if st != 0:
-            raise RuntimeError("solve failed: status %d rel %.3e" % (st, info["rel"]))
-        if out is not None:
-            H.get_solution(out)
-        return info
-
-    # ---- device-resident timing ----
-    for _ in range(max(3, args.warmup)):
-        step(mask_d, rho_d)
-    torch.cuda.synchronize()
-    barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
-    B.mg_timing_enable(H.handle, True)
-    B.mg_timing_read(H.handle)  # reset accumulators
-    l0 = B.mg_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    updates, cycles, orders = 0, 0, []
-    for _ in range(args.steps):
-        info = step(mask_d, rho_d)
-        updates += info["cell_updates"]
-        cycles += info["cycles"]
-        orders.append(info["order"])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    launches = B.mg_launch_count() - l0
-    n_gs, gs_ms = B.mg_timing_read(H.handle)
-    B.mg_timing_enable(H.handle, False)
+    st_main = time_form(main, args, mask_d, rho_d, stream, world, device, timing=True)
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    elapsed = max_over_ranks(elapsed, world, device)
-    total_updates = sum_over_ranks(updates, world, device)
-    barrier(world)
 
-    # ---- end to end through the C ABI with host buffers ----
-    if args.no_e2e:
+    if args.profile:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": total_updates / elapsed, "unit": UNIT,
-                              "ms_per_step": 1e3 * elapsed / args.steps, "gpu_launches": launches,
-                              "note": "profiling run without the e2e pass"}), flush=True)
+            print(json.dumps({"metric": METRIC, "form": FORMS[args.precision],
+                              "value": st_main["updates"] / st_main["elapsed"], "unit": UNIT,
+                              "ms_per_step": 1e3 * st_main["elapsed"] / args.steps,
+                              "gpu_launches": st_main["launches"], "note": "profiling run without the e2e pass"}),
+                  flush=True)
         return
+
+    other = Form(B, 1 - args.precision, mask_d, rho_d, w["h"], stream.cuda_stream)
+    st_other = time_form(other, args, mask_d, rho_d, stream, world, device, timing=True)
+
+    # end to end through the C ABI with host buffers: mask and rho copied from
+    # pinned host memory and the solution read back every step
     mask_h = torch.from_numpy(w["mask"]).pin_memory()
     rho_h = torch.from_numpy(w["rho"]).pin_memory()
     out_h = torch.empty(w["rho"].shape, dtype=torch.float64).pin_memory()
-    step(mask_h, rho_h, out_h)
-    torch.cuda.synchronize()
-    barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    e2e_updates = 0
-    for _ in range(args.steps):
-        e2e_updates += step(mask_h, rho_h, out_h)["cell_updates"]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device)
-    e2e_total = sum_over_ranks(e2e_updates, world, device)
+    st_e2e = time_form(main, args, mask_h, rho_h, stream, world, device, out=out_h)
     h2d = w["mask"].nbytes + w["rho"].nbytes
     d2h = w["rho"].nbytes
 
     if rank != 0:
         return
-    gs_avg_s = gs_ms / 1e3 / max(n_gs, 1)
-    # algorithmic content of one level-0 half-sweep (one colour of the active
-    # cells): 7 FP64 instructions and 12.5 bytes per active cell on average
-    # (25 B per cell-update over the full red+black sweep)
-    half_cells = n_active / 2.0
-    fp64_instr = 7.0 * half_cells
-    alg_bytes = 25.0 * half_cells
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak = 2 * 152 * 2.07e9 / 1e12  # T FP64 instructions/s: 2 per clock per SM at 2070 MHz
+    ms = lambda st: 1e3 * st["elapsed"] / args.steps  # noqa: E731
     line = {
-        "metric": METRIC, "value": total_updates / elapsed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config(args.size),
-        "time_to_tol_ms": 1e3 * elapsed / args.steps,
-        "cycles_per_solve": cycles / args.steps, "orders": sorted(set(orders)),
-        "roofline": {"bound": "alu", "kernel": "half_sweep_kernel<0> (level-0 red/black Gauss-Seidel)",
-                     "achieved": fp64_instr / gs_avg_s / 1e12, "peak": fp64_peak,
-                     "unit": "T FP64 instr/s", "frac": fp64_instr / gs_avg_s / 1e12 / fp64_peak,
-                     "traffic": None, "launches": n_gs, "avg_launch_us": gs_avg_s * 1e6,
-                     "peak_source": "nominal FP64 rate (1.25 TFLOP/s = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
-                     "hbm_view": {"achieved_gbs": alg_bytes / gs_avg_s / 1e9, "peak_gbs": hbm_peak,
-                                  "frac": alg_bytes / gs_avg_s / 1e9 / hbm_peak,
-                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks
-                                  else "fallback 6.8 TB/s"}},
-        "e2e": {"value": e2e_total / e2e_elapsed, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "metric": METRIC, "value": st_main["updates"] / st_main["elapsed"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms(st_main), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 in f64 refinement" if args.precision == 1 else "f64",
+        "data": "synthetic", "config": config(args.size),
+        "form": FORMS[args.precision],
+        "time_to_tol_ms": ms(st_main), "cycles_per_solve": st_main["cycles"], "orders": st_main["orders"],
+        "roofline": roofline(st_main, n_active, args.precision, peaks),
+        FORMS[1 - args.precision]: {"time_to_tol_ms": ms(st_other),
+                                     "value": st_other["updates"] / st_other["elapsed"],
+                                     "cycles_per_solve": st_other["cycles"],
+                                     "roofline": roofline(st_other, n_active, 1 - args.precision, peaks)},
+        "e2e": {"value": st_e2e["updates"] / st_e2e["elapsed"], "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms(st_e2e)},
         "clocks": clk,
-        "gpu_launches": launches,
+        "gpu_launches": st_main["launches"],
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.size)

@@ -68,12 +68,22 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *  eta             switch threshold on ||r_{n+1}|| / ||r_n|| (Section 4; 0.5).
  *  hold_solves     solves that stay in first order after a switch
  *                  (Section 4: "for the next 10 solves").
- *  use_graphs      1 = replay each V-cycle from a captured CUDA graph. */
+ *  use_graphs      1 = replay each V-cycle from a captured CUDA graph.
+ *  precision       0 = the method in FP64 throughout; 1 = mixed: each
+ *                  multigrid iteration is the paper's V-cycle run in FP32 on
+ *                  the error equation A e = b - A Phi, inside FP64 iterative
+ *                  refinement (the residual, its norm, the update Phi += e
+ *                  and the folded boundary data stay FP64).  The paper has
+ *                  no counterpart; the stopping test and the order switch
+ *                  act on the FP64 residual norms as in FP64 mode.
+ *  inner_cycles    FP32 V-cycles per refinement step (precision 1), >= 1. */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
   int order;
   int use_graphs;
+  int precision;
+  int inner_cycles;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -93,7 +103,8 @@ typedef struct {
 } mg_solve_info;
 
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
- * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1. */
+ * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
+ * precision = 0 (FP64), inner_cycles = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

@@ -59,6 +59,7 @@ struct TimedPair {
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int deepest = -2;                // deepest level at capture time
+  unsigned long long lists_hash = 0;  // list lengths at capture time (they size the grids)
   unsigned long long nodes = 0;    // kernel launches per replay
   std::vector<TimedPair> events;   // level-0 half-sweep event pairs (timing graphs)
 };
@@ -95,6 +96,7 @@ struct mg_hierarchy {
   size_t staging_bytes = 0;
   double r_zero = 0;
   bool r_zero_valid = false;
+  bool prepared = false;  // mixed form: rhs32/e32 of level 0 match the current Phi and b
   std::string last_error = "no error";
   bool timing = false;
   std::vector<TimedPair> events;
@@ -154,7 +156,8 @@ Geom make_geom(int nx, int ny, int nz) {
 
 bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
-         o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2);
+         o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
+         (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8;
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -209,7 +212,7 @@ mg_status launch_ok(mg_hierarchy* H, cudaError_t e, const char* what) {
   return MG_OK;
 }
 
-mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour) {
+mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec) {
   if (l == 0 && H->timing) {
     std::vector<TimedPair>& pool = H->cap_events ? *H->cap_events : H->events;
     size_t& used = H->cap_events ? H->cap_events_used : H->events_used;
@@ -223,34 +226,35 @@ mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour) {
     // inside a capture the records become event nodes of the graph
     const unsigned flags = H->cap_events ? cudaEventRecordExternal : cudaEventRecordDefault;
     CK(H, cudaEventRecordWithFlags(p.a, H->cur, flags));
-    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->cur), "half-sweep"));
+    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, H->cur), "half-sweep"));
     CK(H, cudaEventRecordWithFlags(p.b, H->cur, flags));
     return MG_OK;
   }
-  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, H->cur), "half-sweep");
+  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, H->cur), "half-sweep");
 }
 
-mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps) {
+mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps, int prec = kFP64) {
   if (sweeps <= 0) return MG_OK;
   if (small_level(H->L[l].g))
-    return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, H->cur), "small-level smoother");
+    return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, prec, H->cur), "small-level smoother");
   for (int s = 0; s < sweeps; ++s) {
-    CKS(half_sweep(H, l, order, 0));
-    CKS(half_sweep(H, l, order, 1));
+    CKS(half_sweep(H, l, order, 0, prec));
+    CKS(half_sweep(H, l, order, 1, prec));
   }
   return MG_OK;
 }
 
-// Section 2 recipe at level l, recursing N_cycles times into level l+1.
-mg_status iteration(mg_hierarchy* H, int l, int order) {
+// Section 2 recipe at level l, recursing N_cycles times into level l+1, in
+// FP64 or (inner cycles of the mixed form) FP32.
+mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64) {
   const mg_options& o = H->opt;
-  if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps);
-  CKS(smooth(H, l, order, o.n_pre));                                        // step 1
-  CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, H->cur),
+  if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec);
+  CKS(smooth(H, l, order, o.n_pre, prec));                                  // step 1
+  CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, prec, H->cur),
                 "residual/restriction"));                                    // steps 2-5
-  for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order));      // step 5
-  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, H->cur), "prolongation"));  // 6-7
-  return smooth(H, l, order, o.n_post);                                     // step 8
+  for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order, prec));  // step 5
+  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, prec, H->cur), "prolongation"));  // 6-7
+  return smooth(H, l, order, o.n_post, prec);                               // step 8
 }
 
 // Gauss-Seidel updates of active cells in one iteration starting at level l.
@@ -284,14 +288,46 @@ mg_status norm2(mg_hierarchy* H, bool red_only, bool with_phi, double* out) {
   return MG_OK;
 }
 
+unsigned long long lists_hash(const mg_hierarchy* H) {
+  unsigned long long x = 1469598103934665603ULL;  // FNV-1a over every list length
+  for (int l = 0; l < H->nlev; ++l)
+    for (int i = 0; i < 6; ++i) {
+      x ^= H->L[l].hcount[i];
+      x *= 1099511628211ULL;
+    }
+  return x;
+}
+
 void drop_graph(GraphSlot& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   g.exec = nullptr;
   g.deepest = -2;
 }
 
-// Captures one multigrid iteration of `order` followed by the end-of-cycle
-// residual norm and its copy to the host scalar.
+// Enqueues the FP64 residual of the mixed form (which also writes the FP32
+// right-hand side -r^ and zeroes the FP32 correction) and its norm.
+mg_status emit_refine_residual(mg_hierarchy* H) {
+  CKS(launch_ok(H, launch_refine_residual(H->L[0], H->partials, H->max_partials, H->dscal, H->cur),
+                "refinement residual"));
+  CK(H, cudaMemcpyAsync(H->hscal, H->dscal, sizeof(double), cudaMemcpyDeviceToHost, H->cur));
+  return MG_OK;
+}
+
+// One multigrid iteration and the end-of-cycle residual norm (with its copy
+// to the host scalar).  FP64: the Section 2 recipe on Phi.  Mixed: the same
+// recipe in FP32 on the error equation (inner_cycles times), Phi += e in
+// FP64, then the FP64 residual, which also prepares the next step.
+mg_status emit_cycle(mg_hierarchy* H, int order) {
+  if (H->opt.precision == 1) {
+    for (int i = 0; i < H->opt.inner_cycles; ++i) CKS(iteration(H, 0, order, kFP32));
+    CKS(launch_ok(H, launch_refine_update(H->L[0], H->cur), "refinement update"));
+    return emit_refine_residual(H);
+  }
+  CKS(iteration(H, 0, order));
+  return emit_norm2(H, ends_with_sweep(H, order), true);
+}
+
+// Captures emit_cycle(order) into a graph.
 mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
   drop_graph(gs);
   if (!H->cap_stream) CK(H, cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
@@ -303,8 +339,7 @@ mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
   mg_status st = MG_OK;
   cudaError_t e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    st = iteration(H, 0, order);
-    if (st == MG_OK) st = emit_norm2(H, ends_with_sweep(H, order), true);
+    st = emit_cycle(H, order);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(H->cap_stream, &graph);
     if (st == MG_OK && e2 == cudaSuccess) {
@@ -321,6 +356,7 @@ mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
   if (st != MG_OK) return st;
   if (e != cudaSuccess || !gs.exec) return cuda_fail(H, e, "graph capture");
   gs.deepest = H->deepest[order];
+  gs.lists_hash = lists_hash(H);
   gs.nodes = t_captured;
   return MG_OK;
 }
@@ -329,13 +365,14 @@ mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
 // norm, replayed from a CUDA graph when use_graphs is set.  If r_out is
 // non-null the stream is synchronised and ||r|| is returned.
 mg_status run_cycle(mg_hierarchy* H, int order, double* r_out) {
-  const bool red_only = ends_with_sweep(H, order);
+  if (H->opt.precision == 1 && !H->prepared) CKS(emit_refine_residual(H));
+  H->prepared = true;
   if (!H->opt.use_graphs) {
-    CKS(iteration(H, 0, order));
-    CKS(emit_norm2(H, red_only, true));
+    CKS(emit_cycle(H, order));
   } else {
     GraphSlot& gs = H->graphs[order][H->timing ? 1 : 0];
-    if (!gs.exec || gs.deepest != H->deepest[order]) CKS(capture_cycle(H, order, gs));
+    if (!gs.exec || gs.deepest != H->deepest[order] || gs.lists_hash != lists_hash(H))
+      CKS(capture_cycle(H, order, gs));
     CK(H, cudaGraphLaunch(gs.exec, H->stream));
     count_launch(gs.nodes);
   }
@@ -385,6 +422,13 @@ mg_status build_levels(mg_hierarchy* H) {
     CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? H->mask_dev : nullptr, H->L[l + 1], s), "mask R1"));
     CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
   }
+  // FP32 copies of the coarse diagonals for the mixed form
+  for (int l = 1; l < H->nlev; ++l)
+    if (H->L[l].invd32[0])
+      for (int c = 0; c < 2; ++c) {
+        CKS(launch_ok(H, launch_to_f32(H->L[l].invd[c], H->L[l].invd32[c], H->L[l].g.total, s), "fp32 copy"));
+        CKS(launch_ok(H, launch_to_f32(H->L[l].diag[c], H->L[l].diag32[c], H->L[l].g.total, s), "fp32 copy"));
+      }
   // compact lists of the unknowns, per order and colour (level 0: one set)
   for (int l = 0; l < H->nlev; ++l) {
     LevelDev& L = H->L[l];
@@ -396,7 +440,10 @@ mg_status build_levels(mg_hierarchy* H) {
   }
   unsigned long long hc[2 * kMaxLevels];
   CK(H, cudaMemcpyAsync(hc, H->counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  for (int l = 0; l < H->nlev; ++l)
+    CK(H, cudaMemcpyAsync(H->L[l].hcount, H->L[l].count, sizeof(H->L[l].hcount), cudaMemcpyDeviceToHost, s));
   CK(H, cudaStreamSynchronize(s));
+  for (int c = 0; c < 2; ++c) H->L[0].hcount[2 + c] = H->L[0].hcount[4 + c];  // level 0: one active set
   for (int l = 0; l < H->nlev; ++l) {
     H->active[2][l] = (long long)hc[2 * l];
     H->active[1][l] = l == 0 ? (long long)hc[0] : (long long)hc[2 * l + 1];
@@ -416,6 +463,7 @@ mg_status reset_fields(mg_hierarchy* H) {
   CKS(zero_split(H, H->L[0].g, H->F.rhoh2));
   CKS(zero_split(H, H->L[0].g, H->F.bc));
   H->r_zero_valid = false;
+  H->prepared = false;
   return MG_OK;
 }
 
@@ -463,6 +511,8 @@ void mg_default_options(mg_options* opt) {
   opt->eta = 0.5;
   opt->order = 0;
   opt->use_graphs = 1;
+  opt->precision = 0;
+  opt->inner_cycles = 1;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -536,7 +586,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   Arena A;
   struct Off {
     size_t phi[2], rhs[2], invd[2], diag[2], code[2], res[2], list[3][2], count, S;
+    size_t f_phi[2], f_rhs[2], f_res[2], f_invd[2], f_diag[2];
   } off[kMaxLevels];
+  const bool mixed = o.precision == 1;
   for (int l = 0; l < H->nlev; ++l) {
     Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
     H->L[l].g = g;
@@ -548,6 +600,15 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       off[l].res[c] = A.reserve(sizeof(double) * g.total);
       for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
         off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)g.hx * g.ny * g.nz);
+      if (mixed) {
+        off[l].f_phi[c] = A.reserve(sizeof(float) * g.total);
+        off[l].f_rhs[c] = A.reserve(sizeof(float) * g.total);
+        off[l].f_res[c] = A.reserve(sizeof(float) * g.total);
+        if (l > 0) {
+          off[l].f_invd[c] = A.reserve(sizeof(float) * g.total);
+          off[l].f_diag[c] = A.reserve(sizeof(float) * g.total);
+        }
+      }
       if (l > 0) {
         off[l].invd[c] = A.reserve(sizeof(double) * g.total);
         off[l].diag[c] = A.reserve(sizeof(double) * g.total);
@@ -595,6 +656,12 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       for (int o = (l == 0 ? 2 : 1); o <= 2; ++o) H->L[l].list[o][c] = (uint32_t*)(base + off[l].list[o][c]);
       if (l == 0) H->L[l].list[1][c] = H->L[l].list[2][c];
       H->L[l].list[0][c] = nullptr;
+      LevelDev& Lm = H->L[l];
+      Lm.phi32[c] = mixed ? (float*)(base + off[l].f_phi[c]) : nullptr;
+      Lm.rhs32[c] = mixed ? (float*)(base + off[l].f_rhs[c]) : nullptr;
+      Lm.res32[c] = mixed ? (float*)(base + off[l].f_res[c]) : nullptr;
+      Lm.invd32[c] = (mixed && l > 0) ? (float*)(base + off[l].f_invd[c]) : nullptr;
+      Lm.diag32[c] = (mixed && l > 0) ? (float*)(base + off[l].f_diag[c]) : nullptr;
       H->L[l].invd[c] = l > 0 ? (double*)(base + off[l].invd[c]) : nullptr;
       H->L[l].diag[c] = l > 0 ? (double*)(base + off[l].diag[c]) : nullptr;
     }
@@ -674,6 +741,7 @@ mg_status mg_set_rhs(mg_hierarchy* H, const double* rho, mg_mem where) {
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
+  H->prepared = false;
   return MG_OK;
 }
 
@@ -696,6 +764,7 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
+  H->prepared = false;
   return MG_OK;
 }
 
@@ -721,11 +790,13 @@ mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_
     CKS(zero_split(H, H->L[0].g, H->F.bc));
     CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
     H->r_zero_valid = false;
+  H->prepared = false;
     return fail(H, MG_ERR_INVALID_ARG,
                 "a boundary face lies outside the coarse cell centres; Dirichlet values reset to 0");
   }
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   H->r_zero_valid = false;
+  H->prepared = false;
   return MG_OK;
 }
 
@@ -733,6 +804,7 @@ mg_status mg_set_solution(mg_hierarchy* H, const double* phi, mg_mem where) {
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   DeviceGuard guard(H->device);
   const Geom& g0 = H->L[0].g;
+  H->prepared = false;
   if (!phi) return zero_split(H, g0, H->L[0].phi);
   const size_t bytes = sizeof(double) * g0.ncells();
   if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
@@ -790,7 +862,15 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
   const Geom& g0 = H->L[0].g;
   double r_zero, r_init;
   CKS(residual_zero(H, &r_zero));
-  CKS(residual(H, false, &r_init));
+  if (o.precision == 1) {
+    // the FP64 residual of the initial guess also prepares the first FP32 step
+    CKS(emit_refine_residual(H));
+    CK(H, cudaStreamSynchronize(H->stream));
+    r_init = std::sqrt(H->hscal[0]) / (H->h * H->h);
+    H->prepared = true;
+  } else {
+    CKS(residual(H, false, &r_init));
+  }
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->r_zero = r_zero;
@@ -839,6 +919,7 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
           for (int c = 0; c < 2; ++c)
             CK(H, cudaMemcpyAsync(H->L[0].phi[c], H->F.save[c], sizeof(double) * g0.total,
                                   cudaMemcpyDeviceToDevice, H->stream));
+          H->prepared = false;
           r_n = r_init;
         }
       }
@@ -928,6 +1009,7 @@ mg_status mg_level_get(mg_hierarchy* H, int level, int field, void* out, mg_mem 
 
 mg_status mg_level_set(mg_hierarchy* H, int level, int field, const void* in, mg_mem where) {
   CKS(check_level(H, level));
+  H->prepared = false;
   if (!in) return fail(H, MG_ERR_INVALID_ARG, "null input");
   if (field != MG_FIELD_PHI && field != MG_FIELD_RHS)
     return fail(H, MG_ERR_INVALID_ARG, "only MG_FIELD_PHI and MG_FIELD_RHS can be set");
@@ -944,11 +1026,13 @@ mg_status mg_level_set(mg_hierarchy* H, int level, int field, const void* in, mg
                 "layout"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   if (level == 0 && field == MG_FIELD_RHS) H->r_zero_valid = false;
+  H->prepared = false;
   return MG_OK;
 }
 
 mg_status mg_level_smooth(mg_hierarchy* H, int level, int order, int sweeps) {
   CKS(check_level(H, level));
+  H->prepared = false;
   if ((order != 1 && order != 2) || sweeps < 0) return fail(H, MG_ERR_INVALID_ARG, "bad order or sweeps");
   DeviceGuard guard(H->device);
   CKS(smooth(H, level, order, sweeps));
@@ -958,18 +1042,20 @@ mg_status mg_level_smooth(mg_hierarchy* H, int level, int order, int sweeps) {
 
 mg_status mg_level_restrict(mg_hierarchy* H, int level, int order) {
   CKS(check_level(H, level));
+  H->prepared = false;
   if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
   DeviceGuard guard(H->device);
-  CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, H->stream), "restriction"));
+  CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, kFP64, H->stream), "restriction"));
   CK(H, cudaStreamSynchronize(H->stream));
   return MG_OK;
 }
 
 mg_status mg_level_prolong(mg_hierarchy* H, int level, int order) {
   CKS(check_level(H, level));
+  H->prepared = false;
   if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
   DeviceGuard guard(H->device);
-  CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, H->stream), "prolongation"));
+  CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, kFP64, H->stream), "prolongation"));
   CK(H, cudaStreamSynchronize(H->stream));
   return MG_OK;
 }

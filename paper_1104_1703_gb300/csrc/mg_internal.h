@@ -63,8 +63,19 @@ struct LevelDev {
   // changes).
   uint32_t* list[3][2];
   uint32_t* count;
+  uint32_t hcount[6];  // host copy of count (sizes the launch grids)
   double* res[2];    // scaled residual r^ of the active cells (restriction input)
+  // FP32 copies for the inner cycles of the mixed-precision form (nullptr
+  // when the hierarchy was created for FP64 only); level 0: phi32 is the
+  // correction e, rhs32 is -r^ of the FP64 residual.
+  float* phi32[2];
+  float* rhs32[2];
+  float* res32[2];
+  float* invd32[2];
+  float* diag32[2];
 };
+
+enum { kFP64 = 0, kFP32 = 1 };
 
 constexpr uint32_t kListAt = 0x7fffffffu;
 constexpr uint32_t kListPlusX = 0x80000000u;
@@ -107,21 +118,29 @@ cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStrea
 
 // ---- V-cycle kernels (kernels_cycle.cu) ----
 // order: 1 or 2; the level's active bit and diagonal follow from it.
-cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, cudaStream_t s);
-cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, cudaStream_t s);
+cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, int prec, cudaStream_t s);
+cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, int prec, cudaStream_t s);
 bool small_level(const Geom& g);
 // One-time kernel attributes (shared-memory opt-in) for the current device.
 cudaError_t init_cycle_kernels();
 // Residual of level Lf restricted into the rhs of Lc as -R1(r) (scaled), dPhi_c = 0.
 // black_zero: the last operation on Lf was a complete red-black sweep, so
 // the black residual vanishes and only red cells are evaluated.
-cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, cudaStream_t s);
-cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, cudaStream_t s);
+cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, int prec,
+                            cudaStream_t s);
+cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, cudaStream_t s);
 // Sum of squares of the scaled residual of level 0 into partials[0..nblocks),
 // then a fixed-order reduction into out[0].  red_only as black_zero above.
 // with_phi = false evaluates the residual of Phi = 0 (i.e. of the rhs alone).
 cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_phi, double* partials,
                                   int max_partials, double* out, cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
+// Mixed precision: FP64 residual of level 0 over every unknown -> FP32
+// right-hand side -r^ and zero FP32 correction, plus the norm (like
+// launch_residual_norm2); and Phi += e in FP64.
+cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max_partials, double* out,
+                                   cudaStream_t s);
+cudaError_t launch_refine_update(const LevelDev& L0, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 
 }  // namespace gbmg
