@@ -44,11 +44,39 @@ __device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, 
   return T(1) / T(6);
 }
 
+// The level-0 diagonal D = 6 + (ghost faces) comes from a table rather than
+// an int-to-double conversion, which would run on the FP64 pipe.
 template <int KIND, typename T>
-__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, long long at) {
-  if (KIND == 0) return (T)(6 + __popc((unsigned)code >> kGhostShift));
+__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, long long at, const T* tab) {
+  if (KIND == 0) return tab[8 + __popc((unsigned)code >> kGhostShift)];
   if (KIND == 1) return diag[at];
   return T(6);
+}
+
+// FP32 <-> FP64 conversions with integer operations only (the conversion
+// instructions share the FP64 pipe, the binding resource of the mixed
+// form's FP64 kernels).  Narrowing truncates the mantissa (relative error
+// below 2^-23; it only feeds the FP32 correction problem) and flushes
+// magnitudes below 2^-126 to zero; widening is exact (FP32 subnormals, far
+// below any correction, flush to zero).  Infinities and NaNs are kept.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | mant));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | mant));
 }
 
 template <typename T>
@@ -56,10 +84,13 @@ __device__ __forceinline__ T nbr_sum(const T* __restrict__ o, long long at, int 
   return ((o[at] + o[at + dx]) + (o[at - P] + o[at + P])) + (o[at - sz] + o[at + sz]);
 }
 
+// tab[0..7] = 1/(6+n), tab[8..15] = 6+n: the level-0 diagonal and its
+// inverse for n ghost faces
 template <typename T>
 __device__ __forceinline__ void init_tab(T* tab) {
   const int t = threadIdx.x + threadIdx.y * blockDim.x;
   if (t < 8) tab[t] = T(1) / (T)(6 + t);
+  else if (t < 16) tab[t] = (T)(t - 2);
   __syncthreads();
 }
 
@@ -79,42 +110,55 @@ struct ListArgs {
   const uint32_t* count;
   T* res;
   double* partials;
+  double* phi64;  // level 0 of the mixed form: Phi of the listed colour (fused update)
 };
 
-template <int KIND, typename T>
-__device__ __forceinline__ void gs_update(const ListArgs<T>& a, uint32_t e, const T* tab) {
-  const long long at = e & kListAt;
-  const T s = nbr_sum(a.other, at, (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-  const uint8_t code = KIND == 0 ? a.code[at] : 0;
-  a.self[at] = (s - a.rhs[at]) * inv_diag<KIND>(code, a.invd, at, tab);
-}
+// entries per thread of the list kernels: the FP64 kernels are bound by the
+// FP64 pipe, the FP32 ones by load latency, which more entries in flight hide
+template <typename T>
+struct PerThread {
+  static constexpr int value = 2;
+};
 
 // K4: one colour of a red-black Gauss-Seidel sweep (Section 2) over the
 // compact list of that colour's unknowns: every lane of every warp updates
-// an unknown, so no issue slot is spent on a predicated-off lane.  The grid
-// is sized from the list length so that every thread takes two entries
-// (i and i + stride), all loads of both before either store.
-template <int KIND, typename T>
+// an unknown, so no issue slot is spent on a predicated-off lane.  Each
+// thread takes PER entries (i, i + stride, ...) and issues every load of
+// all of them before any store (the compiler cannot prove that the written
+// and the read colour arrays do not alias).  With UPDATE (the last sweep of
+// the fine level in a mixed-precision step) the colour's correction e is
+// final once written, so Phi += e is applied in FP64 in the same pass.
+template <int KIND, typename T, bool UPDATE>
 __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
-  __shared__ T tab[8];
+  constexpr int PER = PerThread<T>::value;
+  __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const uint32_t n = *a.count;
   const uint32_t stride = gridDim.x * kListBlock;
-  uint32_t i = blockIdx.x * kListBlock + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    // the compiler cannot prove that the written and the read colour arrays
-    // do not alias, so both entries are loaded explicitly first
-    const uint32_t e0 = a.list[i], e1 = a.list[i + stride];
-    const long long at0 = e0 & kListAt, at1 = e1 & kListAt;
-    const T s0 = nbr_sum(a.other, at0, (e0 & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-    const T s1 = nbr_sum(a.other, at1, (e1 & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-    const T b0 = a.rhs[at0], b1 = a.rhs[at1];
-    const T d0 = inv_diag<KIND>(KIND == 0 ? a.code[at0] : 0, a.invd, at0, tab);
-    const T d1 = inv_diag<KIND>(KIND == 0 ? a.code[at1] : 0, a.invd, at1, tab);
-    a.self[at0] = (s0 - b0) * d0;
-    a.self[at1] = (s1 - b1) * d1;
+  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+    long long at[PER];
+    T s[PER], b[PER], d[PER];
+    bool ok[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * stride;
+      ok[u] = i < n;
+      const uint32_t e = ok[u] ? a.list[i] : 0u;
+      at[u] = e & kListAt;
+      if (ok[u]) {
+        s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        b[u] = a.rhs[at[u]];
+        d[u] = inv_diag<KIND>(KIND == 0 ? a.code[at[u]] : 0, a.invd, at[u], tab);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok[u]) continue;
+      const T v = (s[u] - b[u]) * d[u];
+      a.self[at[u]] = v;
+      if (UPDATE) a.phi64[at[u]] += widen_f32(v);
+    }
   }
-  if (i < n) gs_update<KIND>(a, a.list[i], tab);
 }
 
 constexpr int kNormThreads = 256;
@@ -139,19 +183,37 @@ __device__ __forceinline__ void block_reduce_store(double acc, double* out) {
 // the grid is fixed per level, so the partials do not depend on scheduling).
 template <int KIND, bool NORM, typename T>
 __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
+  constexpr int PER = PerThread<T>::value;
+  __shared__ T tab[16];
+  if (KIND == 0) init_tab(tab);
   const Geom g = a.g;
   const uint32_t n = *a.count;
+  const uint32_t stride = gridDim.x * kListBlock;
   double acc = 0.0;
-  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
-    const uint32_t e = a.list[i];
-    const long long at = e & kListAt;
-    const T s = nbr_sum(a.other, at, (e & kListPlusX) ? 1 : -1, g.P, g.sz);
-    const uint8_t code = KIND == 0 ? a.code[at] : 0;
-    const T r = fma(-diag_of<KIND>(code, a.diag, at), a.self[at], s) - a.rhs[at];
-    if (NORM)
-      acc = fma((double)r, (double)r, acc);
-    else
-      a.res[at] = r;
+  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+    long long at[PER];
+    T r[PER];
+    bool ok[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * stride;
+      ok[u] = i < n;
+      const uint32_t e = ok[u] ? a.list[i] : 0u;
+      at[u] = e & kListAt;
+      if (ok[u]) {
+        const T s = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+        const uint8_t code = KIND == 0 ? a.code[at[u]] : 0;
+        r[u] = fma(-diag_of<KIND>(code, a.diag, at[u], tab), a.self[at[u]], s) - a.rhs[at[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok[u]) continue;
+      if (NORM)
+        acc = fma((double)r[u], (double)r[u], acc);
+      else
+        a.res[at[u]] = r[u];
+    }
   }
   if (NORM) block_reduce_store(acc, a.partials + blockIdx.x);
 }
@@ -181,7 +243,7 @@ constexpr int kSmallSmemBytes = 96 * 1024;
 template <int KIND, bool SMEM, typename T>
 __global__ void __launch_bounds__(kSmallThreads) smooth_small_kernel(SmallArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T tab[8];
+  __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const Geom g = a.g;
   T* p0 = a.phi0;
@@ -290,27 +352,247 @@ __device__ __forceinline__ T coarse_at(const ProlongArgs<T>& a, int X, int Y, in
 // Omega_c hold 0 and out-of-box coarse indices read the zero halo.
 template <typename T>
 __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T> a) {
+  constexpr int PER = 2;
   const Geom gf = a.gf;
   const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
-  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
-    const int c = i >= n0;
-    const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
-    const long long at = e & kListAt;
-    const int rel = (int)(at - gf.off0);
-    const int k = rel / (int)gf.sz;
-    const int rem = rel - k * (int)gf.sz;
-    const int j = rem / gf.P;
-    const int q = rem - j * gf.P;
-    const int ix = 2 * q + ((c ^ j ^ k) & 1);
-    const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-    const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-    const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
-    const T e0 = coarse_at(a, Xn, Yn, Zn);
-    const T e1 = (coarse_at(a, Xf, Yn, Zn) + coarse_at(a, Xn, Yf, Zn)) + coarse_at(a, Xn, Yn, Zf);
-    const T e2 = (coarse_at(a, Xn, Yf, Zf) + coarse_at(a, Xf, Yn, Zf)) + coarse_at(a, Xf, Yf, Zn);
-    const T e3 = coarse_at(a, Xf, Yf, Zf);
-    const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
-    a.phi[c][at] = fma(w, T(1) / T(64), a.phi[c][at]);
+  const uint32_t stride = gridDim.x * kListBlock;
+  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+    long long at[PER];
+    int cc[PER];
+    T w[PER], old[PER];
+    bool ok[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * stride;
+      ok[u] = i < n;
+      if (!ok[u]) continue;
+      const int c = i >= n0;
+      cc[u] = c;
+      const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
+      at[u] = e & kListAt;
+      const int rel = (int)(at[u] - gf.off0);
+      const int k = rel / (int)gf.sz;
+      const int rem = rel - k * (int)gf.sz;
+      const int j = rem / gf.P;
+      const int q = rem - j * gf.P;
+      const int ix = 2 * q + ((c ^ j ^ k) & 1);
+      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
+      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
+      const T e0 = coarse_at(a, Xn, Yn, Zn);
+      const T e1 = (coarse_at(a, Xf, Yn, Zn) + coarse_at(a, Xn, Yf, Zn)) + coarse_at(a, Xn, Yn, Zf);
+      const T e2 = (coarse_at(a, Xn, Yf, Zf) + coarse_at(a, Xf, Yn, Zf)) + coarse_at(a, Xf, Yf, Zn);
+      const T e3 = coarse_at(a, Xf, Yf, Zf);
+      w[u] = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      old[u] = a.phi[c][at[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (ok[u]) a.phi[cc[u]][at[u]] = fma(w[u], T(1) / T(64), old[u]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bottom of the V-cycle in one CTA
+// ---------------------------------------------------------------------------
+
+constexpr int kBottomThreads = 1024;
+constexpr int kBottomMaxLevels = 8;
+constexpr int kBottomSmemBytes = 200 * 1024;
+
+template <typename T>
+struct BottomLevel {
+  Geom g;
+  T* phi[2];             // global copies (read at entry for level lb's b, written at exit)
+  T* rhs[2];
+  const T* invd[2];
+  const T* diag[2];
+  const uint8_t* code[2];
+  const uint32_t* list[2];   // unknowns of this order, per colour
+  const uint32_t* count;     // their numbers (device memory), [colour]
+  long long smem_off;    // element offset of this level's staged arrays (phi0, phi1, rhs0, rhs1)
+};
+
+template <typename T>
+struct BottomArgs {
+  BottomLevel<T> L[kBottomMaxLevels];
+  int nlev;  // levels lb .. deepest
+  uint8_t bit;
+  int n_pre, n_post, coarse_sweeps;
+};
+
+// a level's working arrays: staged in shared memory for the whole kernel
+template <typename T>
+struct BottomView {
+  Geom g;
+  T* phi[2];
+  T* rhs[2];
+  const T* invd[2];
+  const T* diag[2];
+  const uint8_t* code[2];
+  const uint32_t* list[2];
+  uint32_t n[2];
+};
+
+// Gauss-Seidel sweeps of one bottom level over its lists of unknowns.  A
+// level with at most 64 unknowns per colour is swept by warp 0 alone, with
+// warp-level barriers between the half-sweeps (the deepest level of a
+// complex domain often has a handful of unknowns and gets 2 * coarse_sweeps
+// half-sweeps); otherwise the whole block works and synchronises.
+template <int KIND, typename T>
+__device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
+  const Geom& g = L.g;
+  const bool one_warp = L.n[0] <= 64 && L.n[1] <= 64;
+  if (one_warp) {
+    if (threadIdx.x < 32) {
+      for (int s = 0; s < sweeps; ++s)
+        for (int c = 0; c < 2; ++c) {
+          for (uint32_t i = threadIdx.x; i < L.n[c]; i += 32) {
+            const uint32_t e = L.list[c][i];
+            const long long at = e & kListAt;
+            L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
+                           inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
+          }
+          __syncwarp();
+        }
+    }
+    __syncthreads();
+    return;
+  }
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      for (uint32_t i = threadIdx.x; i < L.n[c]; i += blockDim.x) {
+        const uint32_t e = L.list[c][i];
+        const long long at = e & kListAt;
+        L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
+                       inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
+      }
+      __syncthreads();
+    }
+}
+
+// residual of level f and R1 into level f+1 in one pass over the coarse
+// cells (each coarse cell evaluates its own children): b = -1/2 sum r^,
+// dPhi = 0.  Children of the black colour carry no residual after a full
+// sweep (black_zero).
+template <int KIND, typename T>
+__device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, bool black_zero) {
+  const Geom& g = F.g;
+  const Geom& gc = C.g;
+  const int nc = gc.nx * gc.ny * gc.nz;
+  for (int e = threadIdx.x; e < nc; e += blockDim.x) {
+    const int I = e % gc.nx, t = e / gc.nx, J = t % gc.ny, K = t / gc.ny;
+    T sum = 0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj, k = 2 * K + dk;
+        if (j >= g.ny || k >= g.nz) continue;
+        const long long at = g.at(I, j, k);
+        for (int c = 0; c < (black_zero ? 1 : 2); ++c) {
+          if (!(F.code[c][at] & bit)) continue;
+          const T nb = nbr_sum<T>(F.phi[c ^ 1], at, x_offset(c, j, k), g.P, g.sz);
+          sum += fma(-diag_of<KIND>(0, F.diag[c], at, (const T*)nullptr), F.phi[c][at], nb) - F.rhs[c][at];
+        }
+      }
+    const int Cc = (I + J + K) & 1;
+    const long long atc = gc.at(I >> 1, J, K);
+    C.rhs[Cc][atc] = T(-0.5) * sum;
+    C.phi[Cc][atc] = T(0);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ T bottom_coarse(const BottomView<T>& C, int X, int Y, int Z) {
+  return C.phi[(X + Y + Z) & 1][C.g.at(X >> 1, Y, Z)];
+}
+
+// P2 of level f+1 into the unknowns of level f
+template <typename T>
+__device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit) {
+  const Geom& g = F.g;
+  const int n = g.hx * g.ny * g.nz;
+  for (int c = 0; c < 2; ++c)
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int q = e % g.hx, t = e / g.hx, j = t % g.ny, k = t / g.ny;
+      const long long at = g.at(q, j, k);
+      if (!(F.code[c][at] & bit)) continue;
+      const int ix = 2 * q + ((c ^ j ^ k) & 1);
+      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
+      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
+      const T e0 = bottom_coarse(C, Xn, Yn, Zn);
+      const T e1 = (bottom_coarse(C, Xf, Yn, Zn) + bottom_coarse(C, Xn, Yf, Zn)) + bottom_coarse(C, Xn, Yn, Zf);
+      const T e2 = (bottom_coarse(C, Xn, Yf, Zf) + bottom_coarse(C, Xf, Yn, Zf)) + bottom_coarse(C, Xf, Yf, Zn);
+      const T e3 = bottom_coarse(C, Xf, Yf, Zf);
+      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      F.phi[c][at] = fma(w, T(1) / T(64), F.phi[c][at]);
+    }
+  __syncthreads();
+}
+
+// The Section 2 recipe (V-cycle, N_cycles = 1) on the small coarse levels
+// lb .. deepest, from the state the restriction into level lb left (its
+// right-hand side set, its correction zero), inside one CTA.  With SMEM the
+// correction and right-hand side of every level (halo included) live in
+// shared memory for the whole kernel, so the many barrier-separated steps
+// (2 * coarse_sweeps of them on the deepest level) read on-chip data that
+// the previous step wrote; the results go back to global memory at the end.
+// Each step is a block-strided loop over the level's slots closed by
+// __syncthreads.  This replaces about six launches per level and the
+// 2 * coarse_sweeps launches of the coarsest solve.
+template <int KIND, typename T, bool SMEM>
+__global__ void __launch_bounds__(kBottomThreads) bottom_kernel(BottomArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
+  if (threadIdx.x == 0)
+    for (int i = 0; i < a.nlev; ++i) {
+      const BottomLevel<T>& L = a.L[i];
+      V[i].g = L.g;
+      for (int c = 0; c < 2; ++c) {
+        V[i].phi[c] = SMEM ? sm + L.smem_off + c * L.g.total : L.phi[c];
+        V[i].rhs[c] = SMEM ? sm + L.smem_off + (2 + c) * L.g.total : L.rhs[c];
+        V[i].invd[c] = L.invd[c];
+        V[i].diag[c] = L.diag[c];
+        V[i].code[c] = L.code[c];
+        V[i].list[c] = L.list[c];
+        V[i].n[c] = L.count[c];
+      }
+    }
+  __syncthreads();
+  if (SMEM) {
+    // stage: level lb's b and dPhi (= 0 after the restriction); the deeper
+    // levels are fully written before they are read, except their zero halo
+    for (int i = 0; i < a.nlev; ++i) {
+      const long long tot = a.L[i].g.total;
+      for (int c = 0; c < 2; ++c)
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+          V[i].phi[c][e] = T(0);
+          V[i].rhs[c][e] = i == 0 ? a.L[0].rhs[c][e] : T(0);
+        }
+    }
+    __syncthreads();
+  }
+  const int last = a.nlev - 1;
+  for (int i = 0; i < last; ++i) {
+    bottom_smooth<KIND>(V[i], a.n_pre);
+    bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
+  }
+  bottom_smooth<KIND>(V[last], a.coarse_sweeps);
+  for (int i = last - 1; i >= 0; --i) {
+    bottom_prolong(V[i], V[i + 1], a.bit);
+    bottom_smooth<KIND>(V[i], a.n_post);
+  }
+  if (SMEM) {
+    for (int i = 0; i < a.nlev; ++i) {
+      const long long tot = a.L[i].g.total;
+      for (int c = 0; c < 2; ++c)
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+          a.L[i].phi[c][e] = V[i].phi[c][e];
+          a.L[i].rhs[c][e] = V[i].rhs[c][e];
+        }
+    }
   }
 }
 
@@ -339,19 +621,22 @@ __global__ void __launch_bounds__(kNormThreads) rhsnorm_kernel(NormArgs a) {
   block_reduce_store(acc, a.partials + blockIdx.x);
 }
 
-// K9 (second pass): one CTA sums the partials in a fixed order.
-__global__ void __launch_bounds__(kNormThreads) finalize_kernel(const double* __restrict__ partials, int n,
-                                                                double* out) {
-  double acc = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += partials[e];
-  __shared__ double sm[kNormThreads];
-  sm[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = kNormThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-    __syncthreads();
+// K9 (second pass): one CTA sums the partials in a fixed order (four
+// independent accumulators per thread so that the loads overlap).
+constexpr int kFinalThreads = 1024;
+
+__global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const double* __restrict__ partials, int n,
+                                                                 double* out) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int e = threadIdx.x;
+  for (; e + 3 * kFinalThreads < n; e += 4 * kFinalThreads) {
+    a0 += partials[e];
+    a1 += partials[e + kFinalThreads];
+    a2 += partials[e + 2 * kFinalThreads];
+    a3 += partials[e + 3 * kFinalThreads];
   }
-  if (threadIdx.x == 0) out[0] = sm[0];
+  for (; e < n; e += kFinalThreads) a0 += partials[e];
+  block_reduce_store((a0 + a1) + (a2 + a3), out);
 }
 
 // Mixed precision, start of a refinement step: the FP64 scaled residual of
@@ -373,19 +658,38 @@ struct RefineArgs {
 };
 
 __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs a) {
+  constexpr int PER = 2;
+  __shared__ double tab[16];
+  init_tab(tab);
   const Geom g = a.g;
   const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
+  const uint32_t stride = gridDim.x * kListBlock;
   double acc = 0.0;
-  for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
-    const int c = i >= n0;
-    const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
-    const long long at = e & kListAt;
-    const double s = nbr_sum(a.phi[1 - c], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz);
-    const double D = (double)(6 + __popc((unsigned)a.code[c][at] >> kGhostShift));
-    const double r = fma(-D, a.phi[c][at], s) - a.rhs[c][at];
-    a.rhs32[c][at] = (float)(-r);
-    a.e32[c][at] = 0.0f;
-    acc = fma(r, r, acc);
+  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+    long long at[PER];
+    int cc[PER];
+    double r[PER];
+    bool ok[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * stride;
+      ok[u] = i < n;
+      if (!ok[u]) continue;
+      const int c = i >= n0;
+      cc[u] = c;
+      const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
+      at[u] = e & kListAt;
+      const double s = nbr_sum(a.phi[1 - c], at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+      const double D = tab[8 + __popc((unsigned)a.code[c][at[u]] >> kGhostShift)];
+      r[u] = fma(-D, a.phi[c][at[u]], s) - a.rhs[c][at[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok[u]) continue;
+      a.rhs32[cc[u]][at[u]] = narrow_f64(-r[u]);
+      a.e32[cc[u]][at[u]] = 0.0f;
+      acc = fma(r[u], r[u], acc);
+    }
   }
   block_reduce_store(acc, a.partials + blockIdx.x);
 }
@@ -403,7 +707,7 @@ __global__ void __launch_bounds__(kListBlock) refine_update_kernel(UpdateArgs a)
   for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
     const int c = i >= n0;
     const long long at = (c ? a.list[1][i - n0] : a.list[0][i]) & kListAt;
-    a.phi[c][at] += (double)a.e32[c][at];
+    a.phi[c][at] += widen_f32(a.e32[c][at]);
   }
 }
 
@@ -425,8 +729,11 @@ int list_grid(const Geom& g) {
   return (int)b;
 }
 
-// exact grid for n list entries at `per` entries per thread
+// grid for n list entries: `per` entries per thread for long lists, one
+// entry per thread for short ones (so that short lists still spread over
+// all SMs); the kernels loop over their entries up to n either way
 int exact_grid(uint32_t n, int per) {
+  if ((long long)n < 4LL * 152 * kListBlock * per) per = 1;
   const long long b = ((long long)n + (long long)kListBlock * per - 1) / ((long long)kListBlock * per);
   return b < 1 ? 1 : (int)b;
 }
@@ -466,18 +773,25 @@ ListArgs<T> list_args(const LevelDev& L, int order, int colour) {
   a.count = L.count + list_order(L, order) * 2 + colour;
   a.res = f.res[colour];
   a.partials = nullptr;
+  a.phi64 = nullptr;
   return a;
 }
 
 template <typename T>
-cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, cudaStream_t s) {
-  const ListArgs<T> a = list_args<T>(L, order, colour);
-  const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], 2);
+cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, bool update, cudaStream_t s) {
+  ListArgs<T> a = list_args<T>(L, order, colour);
+  a.phi64 = L.phi[colour];
+  const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], PerThread<T>::value);
   count_launch();
+  if (update) {
+    if (L.level != 0 || sizeof(T) != 4) return cudaErrorInvalidValue;
+    gs_list_kernel<0, T, true><<<grid, kListBlock, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (kind_of(L.level, order)) {
-    case 0: gs_list_kernel<0, T><<<grid, kListBlock, 0, s>>>(a); break;
-    case 1: gs_list_kernel<1, T><<<grid, kListBlock, 0, s>>>(a); break;
-    default: gs_list_kernel<2, T><<<grid, kListBlock, 0, s>>>(a); break;
+    case 0: gs_list_kernel<0, T, false><<<grid, kListBlock, 0, s>>>(a); break;
+    case 1: gs_list_kernel<1, T, false><<<grid, kListBlock, 0, s>>>(a); break;
+    default: gs_list_kernel<2, T, false><<<grid, kListBlock, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -516,7 +830,7 @@ cudaError_t smooth_small_t(const LevelDev& L, int order, int sweeps, cudaStream_
 template <typename T>
 cudaError_t residual_t(const LevelDev& L, int order, int colour, cudaStream_t s) {
   const ListArgs<T> a = list_args<T>(L, order, colour);
-  const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], 1);
+  const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], PerThread<T>::value);
   count_launch();
   switch (kind_of(L.level, order)) {
     case 0: res_list_kernel<0, false, T><<<grid, kListBlock, 0, s>>>(a); break;
@@ -566,7 +880,7 @@ cudaError_t prolong_t(const LevelDev& Lc, const LevelDev& Lf, int order, cudaStr
     a.cphi[c] = fc.phi[c];
   }
   count_launch();
-  prolong_list_kernel<T><<<exact_grid(Lf.hcount[lo * 2] + Lf.hcount[lo * 2 + 1], 1), kListBlock, 0, s>>>(a);
+  prolong_list_kernel<T><<<exact_grid(Lf.hcount[lo * 2] + Lf.hcount[lo * 2 + 1], 2), kListBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -587,11 +901,21 @@ cudaError_t init_cycle_kernels() {
   GBMG_SMEM_ATTR(1, float)
   GBMG_SMEM_ATTR(2, float)
 #undef GBMG_SMEM_ATTR
+#define GBMG_BOTTOM_ATTR(K, T)                                                                         \
+  if (e == cudaSuccess)                                                                                \
+    e = cudaFuncSetAttribute(bottom_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             kBottomSmemBytes);
+  GBMG_BOTTOM_ATTR(1, double)
+  GBMG_BOTTOM_ATTR(2, double)
+  GBMG_BOTTOM_ATTR(1, float)
+  GBMG_BOTTOM_ATTR(2, float)
+#undef GBMG_BOTTOM_ATTR
   return e;
 }
 
-cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, int prec, cudaStream_t s) {
-  return prec == kFP32 ? half_sweep_t<float>(L, order, colour, s) : half_sweep_t<double>(L, order, colour, s);
+cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, int prec, bool update, cudaStream_t s) {
+  return prec == kFP32 ? half_sweep_t<float>(L, order, colour, update, s)
+                       : half_sweep_t<double>(L, order, colour, update, s);
 }
 
 cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, int prec, cudaStream_t s) {
@@ -606,6 +930,53 @@ cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, b
 
 cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, cudaStream_t s) {
   return prec == kFP32 ? prolong_t<float>(Lc, Lf, order, s) : prolong_t<double>(Lc, Lf, order, s);
+}
+
+
+template <typename T>
+cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
+                     cudaStream_t s) {
+  BottomArgs<T> a;
+  a.nlev = deepest - lb + 1;
+  if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return cudaErrorInvalidValue;
+  long long off = 0;
+  for (int i = 0; i < a.nlev; ++i) {
+    const LevelDev& L = levels[lb + i];
+    const Fields<T> f = fields(L, T());
+    a.L[i].g = L.g;
+    for (int c = 0; c < 2; ++c) {
+      a.L[i].phi[c] = f.phi[c];
+      a.L[i].rhs[c] = f.rhs[c];
+      a.L[i].invd[c] = f.invd[c];
+      a.L[i].diag[c] = f.diag[c];
+      a.L[i].code[c] = L.code[c];
+      a.L[i].list[c] = L.list[order][c];
+    }
+    a.L[i].count = L.count + order * 2;
+    a.L[i].smem_off = off;
+    off += 4 * L.g.total;
+  }
+  a.bit = bit_of(lb, order);
+  a.n_pre = n_pre;
+  a.n_post = n_post;
+  a.coarse_sweeps = coarse_sweeps;
+  const size_t bytes = (size_t)off * sizeof(T);
+  const bool sm = bytes <= (size_t)kBottomSmemBytes;
+  count_launch();
+  if (order == 1) {
+    if (sm) bottom_kernel<2, T, true><<<1, kBottomThreads, bytes, s>>>(a);
+    else bottom_kernel<2, T, false><<<1, kBottomThreads, 0, s>>>(a);
+  } else {
+    if (sm) bottom_kernel<1, T, true><<<1, kBottomThreads, bytes, s>>>(a);
+    else bottom_kernel<1, T, false><<<1, kBottomThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
+                          int coarse_sweeps, int prec, cudaStream_t s) {
+  return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s)
+                       : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s);
 }
 
 int residual_norm_blocks(const Geom& g) {
@@ -641,7 +1012,7 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
     }
   }
   count_launch();
-  finalize_kernel<<<1, kNormThreads, 0, s>>>(partials, blocks, out);
+  finalize_kernel<<<1, kFinalThreads, 0, s>>>(partials, blocks, out);
   return cudaGetLastError();
 }
 
@@ -663,7 +1034,7 @@ cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max
   if (blocks > max_partials) return cudaErrorInvalidValue;
   count_launch(2);
   refine_residual_kernel<<<blocks, kListBlock, 0, s>>>(a);
-  finalize_kernel<<<1, kNormThreads, 0, s>>>(partials, blocks, out);
+  finalize_kernel<<<1, kFinalThreads, 0, s>>>(partials, blocks, out);
   return cudaGetLastError();
 }
 

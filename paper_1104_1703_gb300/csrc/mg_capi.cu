@@ -212,7 +212,7 @@ mg_status launch_ok(mg_hierarchy* H, cudaError_t e, const char* what) {
   return MG_OK;
 }
 
-mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec) {
+mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec, bool update = false) {
   if (l == 0 && H->timing) {
     std::vector<TimedPair>& pool = H->cap_events ? *H->cap_events : H->events;
     size_t& used = H->cap_events ? H->cap_events_used : H->events_used;
@@ -226,35 +226,42 @@ mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec) {
     // inside a capture the records become event nodes of the graph
     const unsigned flags = H->cap_events ? cudaEventRecordExternal : cudaEventRecordDefault;
     CK(H, cudaEventRecordWithFlags(p.a, H->cur, flags));
-    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, H->cur), "half-sweep"));
+    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, update, H->cur), "half-sweep"));
     CK(H, cudaEventRecordWithFlags(p.b, H->cur, flags));
     return MG_OK;
   }
-  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, H->cur), "half-sweep");
+  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, update, H->cur), "half-sweep");
 }
 
-mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps, int prec = kFP64) {
+// update_last: the last sweep also applies Phi += e (level 0, mixed form)
+mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps, int prec = kFP64, bool update_last = false) {
   if (sweeps <= 0) return MG_OK;
   if (small_level(H->L[l].g))
     return launch_ok(H, launch_smooth_small(H->L[l], order, sweeps, prec, H->cur), "small-level smoother");
   for (int s = 0; s < sweeps; ++s) {
-    CKS(half_sweep(H, l, order, 0, prec));
-    CKS(half_sweep(H, l, order, 1, prec));
+    const bool up = update_last && s == sweeps - 1;
+    CKS(half_sweep(H, l, order, 0, prec, up));
+    CKS(half_sweep(H, l, order, 1, prec, up));
   }
   return MG_OK;
 }
 
 // Section 2 recipe at level l, recursing N_cycles times into level l+1, in
 // FP64 or (inner cycles of the mixed form) FP32.
-mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64) {
+mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool update_last = false) {
   const mg_options& o = H->opt;
-  if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec);
+  // the small coarse levels run as one single-CTA launch (V-cycles only)
+  if (l >= 1 && o.n_cycles == 1 && small_level(H->L[l].g))
+    return launch_ok(H, launch_bottom(H->L, l, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps, prec,
+                                      H->cur),
+                     "bottom cycle");
+  if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec, update_last);
   CKS(smooth(H, l, order, o.n_pre, prec));                                  // step 1
   CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, prec, H->cur),
                 "residual/restriction"));                                    // steps 2-5
   for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order, prec));  // step 5
   CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, prec, H->cur), "prolongation"));  // 6-7
-  return smooth(H, l, order, o.n_post, prec);                               // step 8
+  return smooth(H, l, order, o.n_post, prec, update_last);                  // step 8
 }
 
 // Gauss-Seidel updates of active cells in one iteration starting at level l.
@@ -319,8 +326,12 @@ mg_status emit_refine_residual(mg_hierarchy* H) {
 // FP64, then the FP64 residual, which also prepares the next step.
 mg_status emit_cycle(mg_hierarchy* H, int order) {
   if (H->opt.precision == 1) {
-    for (int i = 0; i < H->opt.inner_cycles; ++i) CKS(iteration(H, 0, order, kFP32));
-    CKS(launch_ok(H, launch_refine_update(H->L[0], H->cur), "refinement update"));
+    // Phi += e rides on the last level-0 sweep when there is one
+    const bool fused = !small_level(H->L[0].g) &&
+                       (H->deepest[order] == 0 ? H->opt.coarse_sweeps >= 1 : H->opt.n_post >= 1);
+    for (int i = 0; i < H->opt.inner_cycles; ++i)
+      CKS(iteration(H, 0, order, kFP32, fused && i == H->opt.inner_cycles - 1));
+    if (!fused) CKS(launch_ok(H, launch_refine_update(H->L[0], H->cur), "refinement update"));
     return emit_refine_residual(H);
   }
   CKS(iteration(H, 0, order));

@@ -118,7 +118,9 @@ cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStrea
 
 // ---- V-cycle kernels (kernels_cycle.cu) ----
 // order: 1 or 2; the level's active bit and diagonal follow from it.
-cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, int prec, cudaStream_t s);
+// update: level 0 of the mixed form only: also apply Phi += e (FP64) to the
+// colour just smoothed (its last sweep of the refinement step)
+cudaError_t launch_half_sweep(const LevelDev& L, int order, int colour, int prec, bool update, cudaStream_t s);
 cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, int prec, cudaStream_t s);
 bool small_level(const Geom& g);
 // One-time kernel attributes (shared-memory opt-in) for the current device.
@@ -134,6 +136,10 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, in
 // with_phi = false evaluates the residual of Phi = 0 (i.e. of the rhs alone).
 cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_phi, double* partials,
                                   int max_partials, double* out, cudaStream_t s);
+// The whole V-cycle (N_cycles = 1) on levels lb .. deepest in one CTA, for
+// small levels (every level lb..deepest satisfies small_level); lb >= 1.
+cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
+                          int coarse_sweeps, int prec, cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
 // Mixed precision: FP64 residual of level 0 over every unknown -> FP32
 // right-hand side -r^ and zero FP32 correction, plus the norm (like
