@@ -20,8 +20,10 @@ same workload per step).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -286,6 +288,25 @@ def time_form(f, args, mask, rho, stream, world, device, out=None, timing=False)
     return st
 
 
+KERNEL_SRC = os.path.join(ROOT, "paper_1104_1703_gb300", "csrc", "kernels_cycle.cu")
+
+
+def profiled_traffic(profile):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the
+    committed ncu summary `profiles/<profile>`, or None when the summary is
+    missing or the kernel source has changed since it was captured."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        src = open(KERNEL_SRC, "rb").read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not (m_hash and m_bytes) or hashlib.sha256(src).hexdigest() != m_hash.group(1):
+        return None
+    return int(m_bytes.group(1))
+
+
 def roofline(st, n_active, precision, peaks):
     """Roofline of the dominant kernel, the level-0 Gauss-Seidel half-sweep,
     from its CUDA-event-timed launches inside the timed region.  One launch
@@ -300,7 +321,8 @@ def roofline(st, n_active, precision, peaks):
         ach = 7.0 * half / gs_s / 1e12
         return {"bound": "alu", "kernel": "gs_list_kernel<0,double> (level-0 red/black Gauss-Seidel, FP64)",
                 "achieved": ach, "peak": fp64_peak, "unit": "T FP64 instr/s", "frac": ach / fp64_peak,
-                "traffic": None, "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6,
+                "traffic": profiled_traffic("gs_list_fp64_level0_sphere_union_256.md"),
+                "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6,
                 "peak_source": "nominal FP64 rate: 2 FP64 lane-ops/clk/SM x 152 SMs x 2.07 GHz "
                                "(1.25 TFLOP/s counting an FMA as 2)",
                 "hbm_view": {"achieved_gbs": 25.0 * half / gs_s / 1e9, "peak_gbs": hbm_peak,
@@ -308,7 +330,8 @@ def roofline(st, n_active, precision, peaks):
     # FP32: read the other colour 4 + b 4 + code 1, write 4 = 13 B per update
     ach = 13.0 * half / gs_s / 1e9
     return {"bound": "hbm", "kernel": "gs_list_kernel<0,float> (level-0 red/black Gauss-Seidel, FP32 inner cycle)",
-            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": profiled_traffic("gs_list_fp32_level0_sphere_union_256.md"),
             "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
 
 
