@@ -211,3 +211,61 @@ def blob_patch(shape, seed: int, corr_cells: float = 8.0):
     phi_c = coarse_potential(shape_c, seed + 1000003)
     return {"name": "blob_%dx%dx%d" % (nx, ny, nz), "mask": mask, "rho": rho, "phi_c": phi_c,
             "origin": (-2, -2, -2), "h": 1.0 / max(shape), "tol": 1e-8}
+
+
+# ---------------------------------------------------------------------------
+# Concentrated mass at a refined-level boundary (Section 5.1, last test)
+# ---------------------------------------------------------------------------
+
+def concentrated_phi(x, y, z, r0: float):
+    """The concentrated potential of Section 5.1, ln(r^2 / r0^2 + 1), with r
+    the distance to the box centre (1/2, 1/2, 1/2)."""
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2
+    return np.log(r2 / (r0 * r0) + 1.0)
+
+
+def concentrated_rho(x, y, z, r0: float):
+    """The 3D Laplacian of concentrated_phi: with f(r) = ln(r^2/r0^2 + 1),
+    f'' + 2 f'/r = (2 r^2 + 6 r0^2) / (r^2 + r0^2)^2 (the paper's 2D test has
+    4 r0^2 / (r^2 + r0^2)^2 for the same potential)."""
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2
+    return (2.0 * r2 + 6.0 * r0 * r0) / (r2 + r0 * r0) ** 2
+
+
+def concentrated_coarse(nc: int, r0: float):
+    """The coarse AMR level of the boundary-gradient test: the whole unit box
+    at spacing 1/nc, every cell active, rho = concentrated_rho and Dirichlet
+    values concentrated_phi at the box faces."""
+    h = 1.0 / nc
+    c = cell_centres(nc, h)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    fn = lambda a, b, d: concentrated_phi(a, b, d, r0)  # noqa: E731
+    bx, by, bz = faces_from_function(fn, nc, nc, nc, h)
+    return {"name": "concentrated_coarse_%d" % nc, "mask": np.ones((nc, nc, nc), np.int8),
+            "rho": concentrated_rho(x, y, z, r0), "bx": bx, "by": by, "bz": bz, "h": h,
+            "phi_exact": concentrated_phi(x, y, z, r0)}
+
+
+def concentrated_patch(nc: int, r0: float, radius: float, d: float):
+    """A refined patch at spacing 1/(2 nc) whose active cells are those with
+    centre inside a ball of the given radius; the ball is shifted along +x so
+    that its boundary passes at distance d from the mass at the box centre
+    (d = radius: centred).  The patch starts one coarse cell outside the ball's
+    bounding box, on a coarse-cell corner; ``origin`` is the corner of coarse
+    cell (0,0,0) in the patch's fine-cell units, as the one-way interface
+    (Dirichlet values from the coarse solution) takes it."""
+    hc = 1.0 / nc
+    h = hc / 2
+    cx = 0.5 + (radius - d)
+    centre = (cx, 0.5, 0.5)
+    lo = [int(math.floor((v - radius) / hc)) - 1 for v in centre]
+    hi = [int(math.ceil((v + radius) / hc)) + 1 for v in centre]
+    if min(lo) < 0 or max(hi) > nc:
+        raise ValueError("the patch must lie inside the coarse box")
+    n = [2 * (b - a) for a, b in zip(lo, hi)]
+    xs, ys, zs = [(2 * lo[a] + np.arange(n[a]) + 0.5) * h for a in range(3)]
+    z, y, x = np.meshgrid(zs, ys, xs, indexing="ij")
+    mask = (((x - cx) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2) < radius * radius).astype(np.int8)
+    return {"name": "concentrated_patch_d%.3f" % d, "mask": mask, "rho": concentrated_rho(x, y, z, r0),
+            "h": h, "origin": (-2 * lo[0], -2 * lo[1], -2 * lo[2]),
+            "phi_exact": concentrated_phi(x, y, z, r0), "corner": tuple(2 * v for v in lo)}
