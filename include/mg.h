@@ -76,7 +76,10 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  and the folded boundary data stay FP64).  The paper has
  *                  no counterpart; the stopping test and the order switch
  *                  act on the FP64 residual norms as in FP64 mode.
- *  inner_cycles    FP32 V-cycles per refinement step (precision 1), >= 1. */
+ *  inner_cycles    FP32 V-cycles per refinement step (precision 1), 1..8.
+ *                  The stopping test and the switch act once per step; the
+ *                  switch compares the step's residual ratio with
+ *                  eta^inner_cycles (eta per multigrid iteration). */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -93,7 +96,7 @@ typedef struct {
  * reference of the relative residual rel = ||r_final|| / r_zero.  Norms are
  * unscaled L2 norms of r = Laplacian(Phi) - rho over the active fine cells. */
 typedef struct {
-  int cycles;     /* multigrid iterations performed */
+  int cycles;     /* multigrid iterations performed (mixed form: refinement steps) */
   int order_used; /* coarse reconstruction order at exit (1 or 2) */
   int switched;   /* 1 if this solve switched from second to first order */
   int status;     /* the mg_status returned by mg_solve */
@@ -285,6 +288,96 @@ mg_status mg_level_prolong(mg_hierarchy* hier, int level, int order);
 mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* phi, const double* rho, const double* bx,
                                    const double* by, const double* bz, int nx, int ny, int nz, double h,
                                    double* norm_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched solve of many independent patches
+ *
+ * An AMR level is made of many patches of uneven size, each with its own
+ * mask and its own Dirichlet values from the coarser level (Section 2
+ * problem statement, one per patch; Fig. 1).  A batch owns one hierarchy per
+ * patch and runs the multigrid iteration of all of them together: one
+ * launch per step of the Section 2 recipe covers that level of every patch,
+ * the small coarse levels of each patch run as a one-CTA V-cycle (one CTA
+ * per patch, all patches in one launch), and one cycle of the whole batch is
+ * replayed from a CUDA graph.  Each patch keeps its own convergence test,
+ * order switch and hold counter (Section 4), with the same decisions as
+ * mg_solve on that patch alone.  FP64 only, V-cycles only (options
+ * precision = 0, n_cycles = 1).
+ * ------------------------------------------------------------------------- */
+
+typedef struct mg_batch mg_batch; /* opaque, library-owned */
+
+/* Launch parameters of a batch (results do not depend on them, except the
+ * smoother schedule n_pre / n_post, which is part of the method):
+ *  threads          threads per block of the chunked kernels: 128, 256 or
+ *                   512; every block takes chunks of 2 * threads unknowns
+ *  persistent_ctas  0: one block per chunk; > 0: at most this many blocks,
+ *                   each looping over chunks
+ *  bottom_slots     a patch's coarse levels with at most this many cells per
+ *                   colour (64 .. 16384) run inside the one-CTA bottom cycle
+ *  n_pre, n_post    Gauss-Seidel sweeps around the coarse correction (0..8)
+ *  ms_per_cycle     output of mg_batch_autotune: the measured time of one
+ *                   batched cycle with these parameters (0 if not measured) */
+typedef struct {
+  int threads;
+  int persistent_ctas;
+  int bottom_slots;
+  int n_pre, n_post;
+  double ms_per_cycle;
+} mg_batch_tuning;
+
+/* Creates a batch of n_patches (1 .. 4096) patches.  masks[p] points to
+ * the nx*ny*nz int8 mask of patch p (layout as mg_create_hierarchy), all in
+ * memory of kind `where`; dims[3p .. 3p+2] = nx, ny, nz of patch p; h[p] its
+ * cell size.  opt as in mg_create_hierarchy (nullable) with precision 0 and
+ * n_cycles 1.  All patches work on the batch's stream (cuda_stream, or a
+ * new stream when NULL).  Errors: INVALID_ARG (a patch's dims, h or mask is
+ * invalid; the message names the patch), EMPTY_DOMAIN (a patch has no
+ * active cell), OOM, CUDA. */
+mg_status mg_batch_create(int n_patches, const int8_t* const* masks, mg_mem where, const int* dims, const double* h,
+                          const mg_options* opt, void* cuda_stream, mg_batch** out);
+mg_status mg_batch_destroy(mg_batch* batch);
+
+/* The hierarchy of patch p, owned by the batch (do not destroy it).  Its
+ * right-hand side, Dirichlet values and initial guess are set, and its
+ * solution read, with the mg_hierarchy calls above.  Errors: INVALID_ARG. */
+mg_status mg_batch_patch(mg_batch* batch, int p, mg_hierarchy** out);
+
+/* One multigrid iteration of every patch in its current order (as
+ * mg_vcycle; no order switching).  rel_out (nullable) receives n_patches
+ * relative residuals.  Errors: CUDA, DIVERGED (a non-finite norm). */
+mg_status mg_batch_vcycle(mg_batch* batch, double* rel_out);
+
+/* Solves every patch to relative residual tol (as mg_solve on each patch,
+ * with its own order switch, hold counter and stopping test); patches that
+ * converge stop iterating while the others go on.  infos (nullable) receives
+ * n_patches results.  Returns OK when every patch converged, else
+ * NOT_CONVERGED or DIVERGED (the worst over the patches; each patch's own
+ * status is in infos[p].status).  Errors: INVALID_ARG, CUDA. */
+mg_status mg_batch_solve(mg_batch* batch, double tol, int max_cycles, mg_solve_info* infos);
+
+/* Current launch parameters; setting them validates the values and rebuilds
+ * the chunk tables and the cycle graph.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_batch_get_tuning(const mg_batch* batch, mg_batch_tuning* out);
+mg_status mg_batch_set_tuning(mg_batch* batch, const mg_batch_tuning* tuning);
+
+/* Autotuner: times candidate launch parameters (threads 128/256/512, one
+ * block per chunk or 4 / 8 resident blocks per SM, bottom_slots
+ * 1024/2048/4096) on `reps` batched cycles each (CUDA events on the batch's
+ * stream) and keeps the fastest.  With flags & MG_TUNE_SCHEDULE it then
+ * times whole solves to tol from a zero initial guess for the smoother
+ * schedules (n_pre, n_post) = (1,1), (2,1), (2,2), (3,3) and keeps the one
+ * with the shortest time to tolerance.  Each patch's solution and hold
+ * counter are restored afterwards.  best (nullable) receives the result.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+#define MG_TUNE_SCHEDULE 1
+mg_status mg_batch_autotune(mg_batch* batch, int reps, double tol, int max_cycles, int flags,
+                            mg_batch_tuning* best);
+
+/* Kernels the last batched cycle graph holds (launches per cycle). */
+mg_status mg_batch_launches_per_cycle(const mg_batch* batch, long long* launches);
+
+const char* mg_batch_last_error(const mg_batch* batch);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation

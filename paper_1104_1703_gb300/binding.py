@@ -37,6 +37,14 @@ class MGSolveInfo(ctypes.Structure):
                 ("r_init", _d), ("r_final", _d), ("rel", _d), ("hist", _d * (MG_HIST_MAX + 1))]
 
 
+class MGBatchTuning(ctypes.Structure):
+    _fields_ = [("threads", _i), ("persistent_ctas", _i), ("bottom_slots", _i), ("n_pre", _i), ("n_post", _i),
+                ("ms_per_cycle", _d)]
+
+
+MG_TUNE_SCHEDULE = 1
+
+
 class MGError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s (status %d)" % (message, status))
@@ -73,6 +81,16 @@ SIGNATURES = {
     "mg_launch_count": (ctypes.c_ulonglong, []),
     "mg_timing_enable": (_i, [_vp, _i]),
     "mg_timing_read": (_i, [_vp, _vp, _vp]),
+    "mg_batch_create": (_i, [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "mg_batch_destroy": (_i, [_vp]),
+    "mg_batch_patch": (_i, [_vp, _i, _vp]),
+    "mg_batch_vcycle": (_i, [_vp, _vp]),
+    "mg_batch_solve": (_i, [_vp, _d, _i, _vp]),
+    "mg_batch_get_tuning": (_i, [_vp, _vp]),
+    "mg_batch_set_tuning": (_i, [_vp, _vp]),
+    "mg_batch_autotune": (_i, [_vp, _i, _d, _i, _i, _vp]),
+    "mg_batch_launches_per_cycle": (_i, [_vp, _vp]),
+    "mg_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 _LIB = None
@@ -415,3 +433,161 @@ class Hierarchy:
 
     def prolong_from(self, level, order):
         mg_level_prolong(self.handle, level, order)
+
+
+# --------------------------------------------------------------------------
+# Batched solve of many patches
+# --------------------------------------------------------------------------
+
+def mg_batch_last_error(b=None) -> str:
+    return lib().mg_batch_last_error(b).decode()
+
+
+def _check_batch(st, b=None):
+    if st != MG_OK:
+        raise MGError(st, mg_batch_last_error(b))
+
+
+def _info_dict(info):
+    n = min(info.cycles, MG_HIST_MAX)
+    return {"cycles": info.cycles, "order": info.order_used, "switched": info.switched, "status": info.status,
+            "cell_updates": info.cell_updates, "r_zero": info.r_zero, "r_init": info.r_init,
+            "r_final": info.r_final, "rel": info.rel, "hist": np.array(info.hist[: n + 1])}
+
+
+def mg_batch_create(masks, hs, options=None, stream="auto"):
+    """masks: a sequence of (nz, ny, nx) int8 arrays or tensors, all on the
+    host or all on the device; hs: one cell size per patch."""
+    n = len(masks)
+    if n < 1 or len(hs) != n:
+        raise ValueError("need one h per mask and at least one patch")
+    ptrs = (_vp * n)()
+    dims = (_i * (3 * n))()
+    harr = (_d * n)(*[float(h) for h in hs])
+    keep, where = [], None
+    for p, m in enumerate(masks):
+        nz, ny, nx = m.shape
+        ptr, w, k = _in(m, np.int8, (nz, ny, nx), "mask %d" % p)
+        if where is not None and w != where:
+            raise ValueError("masks must all be host arrays or all device tensors")
+        where = w
+        ptrs[p] = ptr
+        dims[3 * p], dims[3 * p + 1], dims[3 * p + 2] = nx, ny, nz
+        keep.append(k)
+    if stream == "auto":
+        stream = _default_stream()
+    out = _vp()
+    st = lib().mg_batch_create(n, ptrs, where, dims, harr, ctypes.byref(options) if options is not None else None,
+                               stream, ctypes.byref(out))
+    _check_batch(st)
+    return out
+
+
+def mg_batch_destroy(b):
+    _check_batch(lib().mg_batch_destroy(b))
+
+
+def mg_batch_patch(b, p):
+    out = _vp()
+    _check_batch(lib().mg_batch_patch(b, int(p), ctypes.byref(out)), b)
+    return out
+
+
+def mg_batch_vcycle(b, n, want_rel=True):
+    rel = (_d * n)()
+    _check_batch(lib().mg_batch_vcycle(b, rel if want_rel else None), b)
+    return np.array(rel[:]) if want_rel else None
+
+
+def mg_batch_solve(b, n, tol, max_cycles=100):
+    """Returns (status, list of per-patch info dicts); raises MGError for
+    argument and CUDA errors."""
+    infos = (MGSolveInfo * n)()
+    st = lib().mg_batch_solve(b, float(tol), int(max_cycles), infos)
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED):
+        _check_batch(st, b)
+    return st, [_info_dict(infos[p]) for p in range(n)]
+
+
+def mg_batch_get_tuning(b):
+    t = MGBatchTuning()
+    _check_batch(lib().mg_batch_get_tuning(b, ctypes.byref(t)), b)
+    return t
+
+
+def mg_batch_set_tuning(b, t):
+    _check_batch(lib().mg_batch_set_tuning(b, ctypes.byref(t)), b)
+
+
+def mg_batch_autotune(b, reps=5, tol=1e-8, max_cycles=100, flags=0):
+    t = MGBatchTuning()
+    _check_batch(lib().mg_batch_autotune(b, int(reps), float(tol), int(max_cycles), int(flags), ctypes.byref(t)), b)
+    return t
+
+
+def mg_batch_launches_per_cycle(b):
+    v = ctypes.c_longlong()
+    _check_batch(lib().mg_batch_launches_per_cycle(b, ctypes.byref(v)), b)
+    return v.value
+
+
+class _Patch(Hierarchy):
+    """A patch of a Batch: the batch owns the handle."""
+
+    def __init__(self, batch, p, shape, h):
+        self._batch = batch
+        self.shape = tuple(shape)
+        self.h = float(h)
+        self.handle = mg_batch_patch(batch.handle, p)
+
+    def close(self):
+        self.handle = None
+
+
+class Batch:
+    """Owns one batch handle; patch(p) gives the hierarchy of patch p."""
+
+    def __init__(self, masks, hs, options=None, stream="auto", **opts):
+        if options is None and opts:
+            options = mg_default_options()
+            for k, v in opts.items():
+                setattr(options, k, v)
+        self.n = len(masks)
+        self.handle = mg_batch_create(masks, hs, options, stream)
+        self._patches = [_Patch(self, p, masks[p].shape, hs[p]) for p in range(self.n)]
+
+    def patch(self, p):
+        return self._patches[p]
+
+    def close(self):
+        if self.handle:
+            for q in self._patches:
+                q.close()
+            mg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vcycle(self, want_rel=True):
+        return mg_batch_vcycle(self.handle, self.n, want_rel)
+
+    def solve(self, tol, max_cycles=100):
+        return mg_batch_solve(self.handle, self.n, tol, max_cycles)
+
+    @property
+    def tuning(self):
+        return mg_batch_get_tuning(self.handle)
+
+    @tuning.setter
+    def tuning(self, t):
+        mg_batch_set_tuning(self.handle, t)
+
+    def autotune(self, reps=5, tol=1e-8, max_cycles=100, flags=0):
+        return mg_batch_autotune(self.handle, reps, tol, max_cycles, flags)
+
+    def launches_per_cycle(self):
+        return mg_batch_launches_per_cycle(self.handle)

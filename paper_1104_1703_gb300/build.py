@@ -33,8 +33,8 @@ def sources():
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [
-        os.path.abspath(__file__)]
+    headers = [os.path.join(CSRC, "*.h"), os.path.join(CSRC, "*.cuh"), os.path.join(INCLUDE, "*.h")]
+    return sources() + [f for pat in headers for f in glob.glob(pat)] + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

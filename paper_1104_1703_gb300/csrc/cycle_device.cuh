@@ -1,0 +1,297 @@
+// Device-side building blocks shared by the single-hierarchy cycle kernels
+// (kernels_cycle.cu) and the batched multi-patch kernels (kernels_batch.cu):
+// the scaled operator of the Section 2 recipe in the red/black split layout
+// of mg_internal.h, and the one-CTA V-cycle on small coarse levels.
+#pragma once
+
+#include "mg_internal.h"
+
+namespace gbmg {
+namespace {
+
+constexpr int kBlockX = 32, kBlockY = 4;
+constexpr int kListBlock = 256;
+
+// KIND 0: level 0 (D from the ghost-face count); 1: coarse, second order
+// (per-cell D and 1/D); 2: coarse, first order (D = 6).
+template <int KIND, typename T>
+__device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, long long at, const T* tab) {
+  if (KIND == 0) return tab[__popc((unsigned)code >> kGhostShift)];
+  if (KIND == 1) return invd[at];
+  return T(1) / T(6);
+}
+
+// The level-0 diagonal D = 6 + (ghost faces) comes from a table rather than
+// an int-to-double conversion, which would run on the FP64 pipe.
+template <int KIND, typename T>
+__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, long long at, const T* tab) {
+  if (KIND == 0) return tab[8 + __popc((unsigned)code >> kGhostShift)];
+  if (KIND == 1) return diag[at];
+  return T(6);
+}
+
+// FP32 <-> FP64 conversions with integer operations only (the conversion
+// instructions share the FP64 pipe, the binding resource of the mixed
+// form's FP64 kernels).  Narrowing truncates the mantissa (relative error
+// below 2^-23; it only feeds the FP32 correction problem) and flushes
+// magnitudes below 2^-126 to zero; widening is exact (FP32 subnormals, far
+// below any correction, flush to zero).  Infinities and NaNs are kept.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | mant));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | mant));
+}
+
+template <typename T>
+__device__ __forceinline__ T nbr_sum(const T* __restrict__ o, long long at, int dx, int P, long long sz) {
+  return ((o[at] + o[at + dx]) + (o[at - P] + o[at + P])) + (o[at - sz] + o[at + sz]);
+}
+
+// tab[0..7] = 1/(6+n), tab[8..15] = 6+n: the level-0 diagonal and its
+// inverse for n ghost faces
+template <typename T>
+__device__ __forceinline__ void init_tab(T* tab) {
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  if (t < 8) tab[t] = T(1) / (T)(6 + t);
+  else if (t < 16) tab[t] = (T)(t - 2);
+  __syncthreads();
+}
+
+// x offset of the non-shared x-neighbour of a colour-c cell in row (j, k)
+__device__ __forceinline__ int x_offset(int c, int j, int k) { return ((c ^ j ^ k) & 1) ? 1 : -1; }
+
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ void block_reduce_store(double acc, double* out) {
+  __shared__ double warp_sums[32];
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+  __syncthreads();
+  if (t < 32) {
+    double v = t < nw ? warp_sums[t] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (t == 0) *out = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bottom of the V-cycle in one CTA
+// ---------------------------------------------------------------------------
+
+constexpr int kBottomThreads = 1024;
+constexpr int kBottomMaxLevels = 8;
+constexpr int kBottomSmemBytes = 200 * 1024;
+
+template <typename T>
+struct BottomLevel {
+  Geom g;
+  T* phi[2];             // global copies (read at entry for level lb's b, written at exit)
+  T* rhs[2];
+  const T* invd[2];
+  const T* diag[2];
+  const uint8_t* code[2];
+  const uint32_t* list[2];   // unknowns of this order, per colour
+  const uint32_t* count;     // their numbers (device memory), [colour]
+  long long smem_off;    // element offset of this level's staged arrays (phi0, phi1, rhs0, rhs1)
+};
+
+template <typename T>
+struct BottomArgs {
+  BottomLevel<T> L[kBottomMaxLevels];
+  int nlev;  // levels lb .. deepest
+  uint8_t bit;
+  int n_pre, n_post, coarse_sweeps;
+};
+
+// a level's working arrays: staged in shared memory for the whole kernel
+template <typename T>
+struct BottomView {
+  Geom g;
+  T* phi[2];
+  T* rhs[2];
+  const T* invd[2];
+  const T* diag[2];
+  const uint8_t* code[2];
+  const uint32_t* list[2];
+  uint32_t n[2];
+};
+
+// Gauss-Seidel sweeps of one bottom level over its lists of unknowns.  A
+// level with at most 64 unknowns per colour is swept by warp 0 alone, with
+// warp-level barriers between the half-sweeps (the deepest level of a
+// complex domain often has a handful of unknowns and gets 2 * coarse_sweeps
+// half-sweeps); otherwise the whole block works and synchronises.
+template <int KIND, typename T>
+__device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
+  const Geom& g = L.g;
+  const bool one_warp = L.n[0] <= 64 && L.n[1] <= 64;
+  if (one_warp) {
+    if (threadIdx.x < 32) {
+      for (int s = 0; s < sweeps; ++s)
+        for (int c = 0; c < 2; ++c) {
+          for (uint32_t i = threadIdx.x; i < L.n[c]; i += 32) {
+            const uint32_t e = L.list[c][i];
+            const long long at = e & kListAt;
+            L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
+                           inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
+          }
+          __syncwarp();
+        }
+    }
+    __syncthreads();
+    return;
+  }
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      for (uint32_t i = threadIdx.x; i < L.n[c]; i += blockDim.x) {
+        const uint32_t e = L.list[c][i];
+        const long long at = e & kListAt;
+        L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
+                       inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
+      }
+      __syncthreads();
+    }
+}
+
+// residual of level f and R1 into level f+1 in one pass over the coarse
+// cells (each coarse cell evaluates its own children): b = -1/2 sum r^,
+// dPhi = 0.  Children of the black colour carry no residual after a full
+// sweep (black_zero).
+template <int KIND, typename T>
+__device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, bool black_zero) {
+  const Geom& g = F.g;
+  const Geom& gc = C.g;
+  const int nc = gc.nx * gc.ny * gc.nz;
+  for (int e = threadIdx.x; e < nc; e += blockDim.x) {
+    const int I = e % gc.nx, t = e / gc.nx, J = t % gc.ny, K = t / gc.ny;
+    T sum = 0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj, k = 2 * K + dk;
+        if (j >= g.ny || k >= g.nz) continue;
+        const long long at = g.at(I, j, k);
+        for (int c = 0; c < (black_zero ? 1 : 2); ++c) {
+          if (!(F.code[c][at] & bit)) continue;
+          const T nb = nbr_sum<T>(F.phi[c ^ 1], at, x_offset(c, j, k), g.P, g.sz);
+          sum += fma(-diag_of<KIND>(0, F.diag[c], at, (const T*)nullptr), F.phi[c][at], nb) - F.rhs[c][at];
+        }
+      }
+    const int Cc = (I + J + K) & 1;
+    const long long atc = gc.at(I >> 1, J, K);
+    C.rhs[Cc][atc] = T(-0.5) * sum;
+    C.phi[Cc][atc] = T(0);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ T bottom_coarse(const BottomView<T>& C, int X, int Y, int Z) {
+  return C.phi[(X + Y + Z) & 1][C.g.at(X >> 1, Y, Z)];
+}
+
+// P2 of level f+1 into the unknowns of level f
+template <typename T>
+__device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, int first_colour) {
+  const Geom& g = F.g;
+  const int n = g.hx * g.ny * g.nz;
+  for (int c = first_colour; c < 2; ++c)
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int q = e % g.hx, t = e / g.hx, j = t % g.ny, k = t / g.ny;
+      const long long at = g.at(q, j, k);
+      if (!(F.code[c][at] & bit)) continue;
+      const int ix = 2 * q + ((c ^ j ^ k) & 1);
+      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
+      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
+      const T e0 = bottom_coarse(C, Xn, Yn, Zn);
+      const T e1 = (bottom_coarse(C, Xf, Yn, Zn) + bottom_coarse(C, Xn, Yf, Zn)) + bottom_coarse(C, Xn, Yn, Zf);
+      const T e2 = (bottom_coarse(C, Xn, Yf, Zf) + bottom_coarse(C, Xf, Yn, Zf)) + bottom_coarse(C, Xf, Yf, Zn);
+      const T e3 = bottom_coarse(C, Xf, Yf, Zf);
+      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      F.phi[c][at] = fma(w, T(1) / T(64), F.phi[c][at]);
+    }
+  __syncthreads();
+}
+
+// The Section 2 recipe (V-cycle, N_cycles = 1) on the small coarse levels
+// lb .. deepest, from the state the restriction into level lb left (its
+// right-hand side set, its correction zero), inside one CTA.  With SMEM the
+// correction and right-hand side of every level (halo included) live in
+// shared memory for the whole kernel, so the many barrier-separated steps
+// (2 * coarse_sweeps of them on the deepest level) read on-chip data that
+// the previous step wrote; the results go back to global memory at the end.
+// Each step is a block-strided loop over the level's slots closed by
+// __syncthreads.  This replaces about six launches per level and the
+// 2 * coarse_sweeps launches of the coarsest solve.
+template <int KIND, typename T, bool SMEM>
+__device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
+  if (threadIdx.x == 0)
+    for (int i = 0; i < a.nlev; ++i) {
+      const BottomLevel<T>& L = a.L[i];
+      V[i].g = L.g;
+      for (int c = 0; c < 2; ++c) {
+        V[i].phi[c] = SMEM ? sm + L.smem_off + c * L.g.total : L.phi[c];
+        V[i].rhs[c] = SMEM ? sm + L.smem_off + (2 + c) * L.g.total : L.rhs[c];
+        V[i].invd[c] = L.invd[c];
+        V[i].diag[c] = L.diag[c];
+        V[i].code[c] = L.code[c];
+        V[i].list[c] = L.list[c];
+        V[i].n[c] = L.count[c];
+      }
+    }
+  __syncthreads();
+  if (SMEM) {
+    // stage: level lb's b and dPhi (= 0 after the restriction); the deeper
+    // levels are fully written before they are read, except their zero halo
+    for (int i = 0; i < a.nlev; ++i) {
+      const long long tot = a.L[i].g.total;
+      for (int c = 0; c < 2; ++c)
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+          V[i].phi[c][e] = T(0);
+          V[i].rhs[c][e] = i == 0 ? a.L[0].rhs[c][e] : T(0);
+        }
+    }
+    __syncthreads();
+  }
+  const int last = a.nlev - 1;
+  for (int i = 0; i < last; ++i) {
+    bottom_smooth<KIND>(V[i], a.n_pre);
+    bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
+  }
+  bottom_smooth<KIND>(V[last], a.coarse_sweeps);
+  for (int i = last - 1; i >= 0; --i) {
+    bottom_prolong(V[i], V[i + 1], a.bit, a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel
+    bottom_smooth<KIND>(V[i], a.n_post);
+  }
+  if (SMEM) {
+    for (int i = 0; i < a.nlev; ++i) {
+      const long long tot = a.L[i].g.total;
+      for (int c = 0; c < 2; ++c)
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+          a.L[i].phi[c][e] = V[i].phi[c][e];
+          a.L[i].rhs[c][e] = V[i].rhs[c][e];
+        }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gbmg

@@ -1,0 +1,71 @@
+// The hierarchy object behind the mg_hierarchy handle of the C ABI, shared
+// by the single-hierarchy driver (mg_capi.cu) and the batched multi-patch
+// driver (mg_batch.cu), which owns one hierarchy per patch.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+
+namespace gbmg {
+
+struct TimedPair {
+  cudaEvent_t a, b;
+};
+
+// A captured multigrid iteration (plus the residual norm and its copy to the
+// pinned host scalar) for one order; replayed once per cycle.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  int deepest = -2;                // deepest level at capture time
+  unsigned long long lists_hash = 0;  // list lengths at capture time (they size the grids)
+  unsigned long long nodes = 0;    // kernel launches per replay
+  std::vector<TimedPair> events;   // level-0 half-sweep event pairs (timing graphs)
+};
+
+}  // namespace gbmg
+
+struct mg_hierarchy {
+  using GraphSlot = gbmg::GraphSlot;
+  using TimedPair = gbmg::TimedPair;
+  using LevelDev = gbmg::LevelDev;
+  using FineExtra = gbmg::FineExtra;
+  mg_options opt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cur = nullptr;          // stream the emitters launch on (stream, or cap_stream while capturing)
+  cudaStream_t cap_stream = nullptr;
+  GraphSlot graphs[3][2];              // [order][timing]
+  std::vector<TimedPair>* cap_events = nullptr;
+  size_t cap_events_used = 0;
+  bool own_stream = false;
+  int device = 0;
+  int nlev = 0;
+  double h = 0;
+  LevelDev L[gbmg::kMaxLevels];
+  FineExtra F;
+  long long active[3][gbmg::kMaxLevels];
+  int deepest[3];
+  int hold = 0;
+  char* arena = nullptr;
+  int8_t* mask_dev = nullptr;
+  uint32_t* list_scratch = nullptr;
+  double* partials = nullptr;
+  int max_partials = 0;
+  double* dscal = nullptr;             // device scalars
+  int* err_flag = nullptr;
+  unsigned long long* counts = nullptr;  // [kMaxLevels][2]
+  double* hscal = nullptr;               // pinned host scalars
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  double r_zero = 0;
+  bool r_zero_valid = false;
+  bool prepared = false;  // mixed form: rhs32/e32 of level 0 match the current Phi and b
+  std::string last_error = "no error";
+  bool timing = false;
+  std::vector<TimedPair> events;
+  size_t events_used = 0;
+  long long timed_launches = 0;   // accumulated from graph replays
+  double timed_ms = 0;
+};

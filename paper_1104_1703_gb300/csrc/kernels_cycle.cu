@@ -26,76 +26,11 @@
 // compact lists of the unknowns (built once per mask), where every lane holds
 // an unknown, and issue as few FP64 instructions as the operator allows.
 // Neighbour values come through L1/L2.
-#include "mg_internal.h"
+#include "cycle_device.cuh"
 
 namespace gbmg {
 
 namespace {
-
-constexpr int kBlockX = 32, kBlockY = 4;
-constexpr int kListBlock = 256;
-
-// KIND 0: level 0 (D from the ghost-face count); 1: coarse, second order
-// (per-cell D and 1/D); 2: coarse, first order (D = 6).
-template <int KIND, typename T>
-__device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, long long at, const T* tab) {
-  if (KIND == 0) return tab[__popc((unsigned)code >> kGhostShift)];
-  if (KIND == 1) return invd[at];
-  return T(1) / T(6);
-}
-
-// The level-0 diagonal D = 6 + (ghost faces) comes from a table rather than
-// an int-to-double conversion, which would run on the FP64 pipe.
-template <int KIND, typename T>
-__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, long long at, const T* tab) {
-  if (KIND == 0) return tab[8 + __popc((unsigned)code >> kGhostShift)];
-  if (KIND == 1) return diag[at];
-  return T(6);
-}
-
-// FP32 <-> FP64 conversions with integer operations only (the conversion
-// instructions share the FP64 pipe, the binding resource of the mixed
-// form's FP64 kernels).  Narrowing truncates the mantissa (relative error
-// below 2^-23; it only feeds the FP32 correction problem) and flushes
-// magnitudes below 2^-126 to zero; widening is exact (FP32 subnormals, far
-// below any correction, flush to zero).  Infinities and NaNs are kept.
-__device__ __forceinline__ float narrow_f64(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-  const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
-  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
-}
-
-__device__ __forceinline__ double widen_f32(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  if (e == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | mant));
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | mant));
-}
-
-template <typename T>
-__device__ __forceinline__ T nbr_sum(const T* __restrict__ o, long long at, int dx, int P, long long sz) {
-  return ((o[at] + o[at + dx]) + (o[at - P] + o[at + P])) + (o[at - sz] + o[at + sz]);
-}
-
-// tab[0..7] = 1/(6+n), tab[8..15] = 6+n: the level-0 diagonal and its
-// inverse for n ghost faces
-template <typename T>
-__device__ __forceinline__ void init_tab(T* tab) {
-  const int t = threadIdx.x + threadIdx.y * blockDim.x;
-  if (t < 8) tab[t] = T(1) / (T)(6 + t);
-  else if (t < 16) tab[t] = (T)(t - 2);
-  __syncthreads();
-}
-
-// x offset of the non-shared x-neighbour of a colour-c cell in row (j, k)
-__device__ __forceinline__ int x_offset(int c, int j, int k) { return ((c ^ j ^ k) & 1) ? 1 : -1; }
 
 template <typename T>
 struct ListArgs {
@@ -108,7 +43,6 @@ struct ListArgs {
   const uint8_t* code;
   const uint32_t* list;
   const uint32_t* count;
-  T* res;
   double* partials;
   double* phi64;  // level 0 of the mixed form: Phi of the listed colour (fused update)
 };
@@ -161,27 +95,10 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   }
 }
 
-constexpr int kNormThreads = 256;
-
-__device__ __forceinline__ void block_reduce_store(double acc, double* out) {
-  __shared__ double warp_sums[32];
-  const int t = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nw = (blockDim.x * blockDim.y) >> 5;
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((t & 31) == 0) warp_sums[t >> 5] = acc;
-  __syncthreads();
-  if (t < 32) {
-    double v = t < nw ? warp_sums[t] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (t == 0) *out = v;
-  }
-}
-
-// Scaled residual r^ = sum_nbr Phi_j - D Phi_i - b of the listed unknowns
-// (Section 2, recipe step 2).  NORM = false stores it for the restriction;
-// NORM = true sums r^2 per block into partials[blockIdx.x] (K9, first pass;
-// the grid is fixed per level, so the partials do not depend on scheduling).
-template <int KIND, bool NORM, typename T>
+// K9, first pass: the sum of r^2 per block into partials[blockIdx.x], r^ =
+// sum_nbr Phi_j - D Phi_i - b the scaled residual of the listed unknowns
+// (the grid is fixed per level, so the partials do not depend on scheduling).
+template <int KIND, typename T>
 __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
   constexpr int PER = PerThread<T>::value;
   __shared__ T tab[16];
@@ -207,15 +124,10 @@ __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      if (!ok[u]) continue;
-      if (NORM)
-        acc = fma((double)r[u], (double)r[u], acc);
-      else
-        a.res[at[u]] = r[u];
-    }
+    for (int u = 0; u < PER; ++u)
+      if (ok[u]) acc = fma((double)r[u], (double)r[u], acc);
   }
-  if (NORM) block_reduce_store(acc, a.partials + blockIdx.x);
+  block_reduce_store(acc, a.partials + blockIdx.x);
 }
 
 template <typename T>
@@ -287,22 +199,28 @@ __global__ void __launch_bounds__(kSmallThreads) smooth_small_kernel(SmallArgs<T
 template <typename T>
 struct RestrictArgs {
   Geom gf, gc;
-  const T* res[2];
+  const T* phi[2];   // fine level
+  const T* rhs[2];
+  const T* diag[2];  // fine level >= 1, second order
   const uint8_t* code[2];
   uint8_t bit;
   T* crhs[2];
   T* cphi[2];
 };
 
-// K5 (second half): R1 of the stored fine residuals into the coarse
-// right-hand side, b_c = -1/2 sum of the children's r^ (Section 2, recipe
-// steps 3-5; Fig. 3), and dPhi_c = 0.  Thread (I, J) of coarse plane K; the
-// two x-children of coarse cell I are both at fine slot I of the child rows.
-// With BLACK_ZERO the last fine operation was a full red-black sweep, after
-// which every black cell satisfies its own equation, so only red children
-// carry a residual.  Children outside the active set (of this order) count 0.
-template <bool BLACK_ZERO, typename T>
-__global__ void __launch_bounds__(kBlockX * kBlockY) restrict_sum_kernel(RestrictArgs<T> a) {
+// K5: residual and R1 in one pass (Section 2, recipe steps 2-5; Fig. 3).
+// Thread (I, J) of coarse plane K evaluates the scaled residual
+// r^ = sum_nbr Phi_j - D Phi_i - b of each of its active children and
+// writes b_c = -1/2 sum r^ and dPhi_c = 0.  The two x-children of coarse
+// cell I are both at fine slot I of the child rows (one per colour), so a
+// warp reads consecutive slots of every array it touches.  With BLACK_ZERO
+// the last fine operation was a complete red-black sweep, after which every
+// black cell satisfies its own equation: only red children carry a
+// residual.  Children outside the active set (of this order) count 0.
+template <int KIND, bool BLACK_ZERO, typename T>
+__global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArgs<T> a) {
+  __shared__ T tab[16];
+  if (KIND == 0) init_tab(tab);
   const Geom gf = a.gf, gc = a.gc;
   const int I = blockIdx.x * kBlockX + threadIdx.x;
   const int J = blockIdx.y * kBlockY + threadIdx.y;
@@ -319,8 +237,12 @@ __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_sum_kernel(Restric
       if (j >= gf.ny) break;
       const long long at = gf.at(I, j, k);
 #pragma unroll
-      for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c)
-        if (a.code[c][at] & a.bit) sum += a.res[c][at];
+      for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c) {
+        const uint8_t cd = a.code[c][at];
+        if (!(cd & a.bit)) continue;
+        const T s = nbr_sum(a.phi[c ^ 1], at, x_offset(c, j, k), gf.P, gf.sz);
+        sum += fma(-diag_of<KIND>(cd, a.diag[c], at, tab), a.phi[c][at], s) - a.rhs[c][at];
+      }
     }
   }
   const int C = (I + J + K) & 1;
@@ -336,6 +258,7 @@ struct ProlongArgs {
   const uint32_t* list[2];
   const uint32_t* count[2];
   const T* cphi[2];
+  int skip_red;  // prolong the black unknowns only
 };
 
 template <typename T>
@@ -350,11 +273,15 @@ __device__ __forceinline__ T coarse_at(const ProlongArgs<T>& a, int X, int Y, in
 // and 1 (/64) for 0, 1, 2 and 3 far axes.  Grouping the corners by weight
 // costs 9 arithmetic instructions per fine cell.  Coarse cells outside
 // Omega_c hold 0 and out-of-box coarse indices read the zero halo.
+// With skip_red only the black unknowns are corrected: when post-smoothing
+// follows, its first (red) half-sweep overwrites every red unknown from its
+// black neighbours without reading the red value, so correcting the red
+// unknowns first would not change the result.
 template <typename T>
 __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T> a) {
   constexpr int PER = 2;
   const Geom gf = a.gf;
-  const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
+  const uint32_t n0 = a.skip_red ? 0u : *a.count[0], n = n0 + *a.count[1];
   const uint32_t stride = gridDim.x * kListBlock;
   for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
     long long at[PER];
@@ -392,208 +319,11 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
   }
 }
 
-// ---------------------------------------------------------------------------
-// Bottom of the V-cycle in one CTA
-// ---------------------------------------------------------------------------
-
-constexpr int kBottomThreads = 1024;
-constexpr int kBottomMaxLevels = 8;
-constexpr int kBottomSmemBytes = 200 * 1024;
-
-template <typename T>
-struct BottomLevel {
-  Geom g;
-  T* phi[2];             // global copies (read at entry for level lb's b, written at exit)
-  T* rhs[2];
-  const T* invd[2];
-  const T* diag[2];
-  const uint8_t* code[2];
-  const uint32_t* list[2];   // unknowns of this order, per colour
-  const uint32_t* count;     // their numbers (device memory), [colour]
-  long long smem_off;    // element offset of this level's staged arrays (phi0, phi1, rhs0, rhs1)
-};
-
-template <typename T>
-struct BottomArgs {
-  BottomLevel<T> L[kBottomMaxLevels];
-  int nlev;  // levels lb .. deepest
-  uint8_t bit;
-  int n_pre, n_post, coarse_sweeps;
-};
-
-// a level's working arrays: staged in shared memory for the whole kernel
-template <typename T>
-struct BottomView {
-  Geom g;
-  T* phi[2];
-  T* rhs[2];
-  const T* invd[2];
-  const T* diag[2];
-  const uint8_t* code[2];
-  const uint32_t* list[2];
-  uint32_t n[2];
-};
-
-// Gauss-Seidel sweeps of one bottom level over its lists of unknowns.  A
-// level with at most 64 unknowns per colour is swept by warp 0 alone, with
-// warp-level barriers between the half-sweeps (the deepest level of a
-// complex domain often has a handful of unknowns and gets 2 * coarse_sweeps
-// half-sweeps); otherwise the whole block works and synchronises.
-template <int KIND, typename T>
-__device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
-  const Geom& g = L.g;
-  const bool one_warp = L.n[0] <= 64 && L.n[1] <= 64;
-  if (one_warp) {
-    if (threadIdx.x < 32) {
-      for (int s = 0; s < sweeps; ++s)
-        for (int c = 0; c < 2; ++c) {
-          for (uint32_t i = threadIdx.x; i < L.n[c]; i += 32) {
-            const uint32_t e = L.list[c][i];
-            const long long at = e & kListAt;
-            L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
-                           inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
-          }
-          __syncwarp();
-        }
-    }
-    __syncthreads();
-    return;
-  }
-  for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < 2; ++c) {
-      for (uint32_t i = threadIdx.x; i < L.n[c]; i += blockDim.x) {
-        const uint32_t e = L.list[c][i];
-        const long long at = e & kListAt;
-        L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
-                       inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
-      }
-      __syncthreads();
-    }
-}
-
-// residual of level f and R1 into level f+1 in one pass over the coarse
-// cells (each coarse cell evaluates its own children): b = -1/2 sum r^,
-// dPhi = 0.  Children of the black colour carry no residual after a full
-// sweep (black_zero).
-template <int KIND, typename T>
-__device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, bool black_zero) {
-  const Geom& g = F.g;
-  const Geom& gc = C.g;
-  const int nc = gc.nx * gc.ny * gc.nz;
-  for (int e = threadIdx.x; e < nc; e += blockDim.x) {
-    const int I = e % gc.nx, t = e / gc.nx, J = t % gc.ny, K = t / gc.ny;
-    T sum = 0;
-    for (int dk = 0; dk < 2; ++dk)
-      for (int dj = 0; dj < 2; ++dj) {
-        const int j = 2 * J + dj, k = 2 * K + dk;
-        if (j >= g.ny || k >= g.nz) continue;
-        const long long at = g.at(I, j, k);
-        for (int c = 0; c < (black_zero ? 1 : 2); ++c) {
-          if (!(F.code[c][at] & bit)) continue;
-          const T nb = nbr_sum<T>(F.phi[c ^ 1], at, x_offset(c, j, k), g.P, g.sz);
-          sum += fma(-diag_of<KIND>(0, F.diag[c], at, (const T*)nullptr), F.phi[c][at], nb) - F.rhs[c][at];
-        }
-      }
-    const int Cc = (I + J + K) & 1;
-    const long long atc = gc.at(I >> 1, J, K);
-    C.rhs[Cc][atc] = T(-0.5) * sum;
-    C.phi[Cc][atc] = T(0);
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ T bottom_coarse(const BottomView<T>& C, int X, int Y, int Z) {
-  return C.phi[(X + Y + Z) & 1][C.g.at(X >> 1, Y, Z)];
-}
-
-// P2 of level f+1 into the unknowns of level f
-template <typename T>
-__device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit) {
-  const Geom& g = F.g;
-  const int n = g.hx * g.ny * g.nz;
-  for (int c = 0; c < 2; ++c)
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int q = e % g.hx, t = e / g.hx, j = t % g.ny, k = t / g.ny;
-      const long long at = g.at(q, j, k);
-      if (!(F.code[c][at] & bit)) continue;
-      const int ix = 2 * q + ((c ^ j ^ k) & 1);
-      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
-      const T e0 = bottom_coarse(C, Xn, Yn, Zn);
-      const T e1 = (bottom_coarse(C, Xf, Yn, Zn) + bottom_coarse(C, Xn, Yf, Zn)) + bottom_coarse(C, Xn, Yn, Zf);
-      const T e2 = (bottom_coarse(C, Xn, Yf, Zf) + bottom_coarse(C, Xf, Yn, Zf)) + bottom_coarse(C, Xf, Yf, Zn);
-      const T e3 = bottom_coarse(C, Xf, Yf, Zf);
-      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
-      F.phi[c][at] = fma(w, T(1) / T(64), F.phi[c][at]);
-    }
-  __syncthreads();
-}
-
-// The Section 2 recipe (V-cycle, N_cycles = 1) on the small coarse levels
-// lb .. deepest, from the state the restriction into level lb left (its
-// right-hand side set, its correction zero), inside one CTA.  With SMEM the
-// correction and right-hand side of every level (halo included) live in
-// shared memory for the whole kernel, so the many barrier-separated steps
-// (2 * coarse_sweeps of them on the deepest level) read on-chip data that
-// the previous step wrote; the results go back to global memory at the end.
-// Each step is a block-strided loop over the level's slots closed by
-// __syncthreads.  This replaces about six launches per level and the
-// 2 * coarse_sweeps launches of the coarsest solve.
+// The one-CTA bottom V-cycle (bottom_run) as a kernel of its own.
 template <int KIND, typename T, bool SMEM>
 __global__ void __launch_bounds__(kBottomThreads) bottom_kernel(BottomArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
-  if (threadIdx.x == 0)
-    for (int i = 0; i < a.nlev; ++i) {
-      const BottomLevel<T>& L = a.L[i];
-      V[i].g = L.g;
-      for (int c = 0; c < 2; ++c) {
-        V[i].phi[c] = SMEM ? sm + L.smem_off + c * L.g.total : L.phi[c];
-        V[i].rhs[c] = SMEM ? sm + L.smem_off + (2 + c) * L.g.total : L.rhs[c];
-        V[i].invd[c] = L.invd[c];
-        V[i].diag[c] = L.diag[c];
-        V[i].code[c] = L.code[c];
-        V[i].list[c] = L.list[c];
-        V[i].n[c] = L.count[c];
-      }
-    }
-  __syncthreads();
-  if (SMEM) {
-    // stage: level lb's b and dPhi (= 0 after the restriction); the deeper
-    // levels are fully written before they are read, except their zero halo
-    for (int i = 0; i < a.nlev; ++i) {
-      const long long tot = a.L[i].g.total;
-      for (int c = 0; c < 2; ++c)
-        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-          V[i].phi[c][e] = T(0);
-          V[i].rhs[c][e] = i == 0 ? a.L[0].rhs[c][e] : T(0);
-        }
-    }
-    __syncthreads();
-  }
-  const int last = a.nlev - 1;
-  for (int i = 0; i < last; ++i) {
-    bottom_smooth<KIND>(V[i], a.n_pre);
-    bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
-  }
-  bottom_smooth<KIND>(V[last], a.coarse_sweeps);
-  for (int i = last - 1; i >= 0; --i) {
-    bottom_prolong(V[i], V[i + 1], a.bit);
-    bottom_smooth<KIND>(V[i], a.n_post);
-  }
-  if (SMEM) {
-    for (int i = 0; i < a.nlev; ++i) {
-      const long long tot = a.L[i].g.total;
-      for (int c = 0; c < 2; ++c)
-        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-          a.L[i].phi[c][e] = V[i].phi[c][e];
-          a.L[i].rhs[c][e] = V[i].rhs[c][e];
-        }
-    }
-  }
+  bottom_run<KIND, T, SMEM>(a, smem_raw);
 }
 
 struct NormArgs {
@@ -752,11 +482,10 @@ struct Fields {
   T* const* rhs;
   T* const* invd;
   T* const* diag;
-  T* const* res;
 };
 
-Fields<double> fields(const LevelDev& L, double) { return {L.phi, L.rhs, L.invd, L.diag, L.res}; }
-Fields<float> fields(const LevelDev& L, float) { return {L.phi32, L.rhs32, L.invd32, L.diag32, L.res32}; }
+Fields<double> fields(const LevelDev& L, double) { return {L.phi, L.rhs, L.invd, L.diag}; }
+Fields<float> fields(const LevelDev& L, float) { return {L.phi32, L.rhs32, L.invd32, L.diag32}; }
 
 template <typename T>
 ListArgs<T> list_args(const LevelDev& L, int order, int colour) {
@@ -771,7 +500,6 @@ ListArgs<T> list_args(const LevelDev& L, int order, int colour) {
   a.code = L.code[colour];
   a.list = L.list[list_order(L, order)][colour];
   a.count = L.count + list_order(L, order) * 2 + colour;
-  a.res = f.res[colour];
   a.partials = nullptr;
   a.phi64 = nullptr;
   return a;
@@ -826,31 +554,16 @@ cudaError_t smooth_small_t(const LevelDev& L, int order, int sweeps, cudaStream_
   return cudaGetLastError();
 }
 
-// residual of the listed unknowns of one colour into res (NORM = false)
-template <typename T>
-cudaError_t residual_t(const LevelDev& L, int order, int colour, cudaStream_t s) {
-  const ListArgs<T> a = list_args<T>(L, order, colour);
-  const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], PerThread<T>::value);
-  count_launch();
-  switch (kind_of(L.level, order)) {
-    case 0: res_list_kernel<0, false, T><<<grid, kListBlock, 0, s>>>(a); break;
-    case 1: res_list_kernel<1, false, T><<<grid, kListBlock, 0, s>>>(a); break;
-    default: res_list_kernel<2, false, T><<<grid, kListBlock, 0, s>>>(a); break;
-  }
-  return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, cudaStream_t s) {
-  cudaError_t e = residual_t<T>(Lf, order, 0, s);
-  if (e == cudaSuccess && !black_zero) e = residual_t<T>(Lf, order, 1, s);
-  if (e != cudaSuccess) return e;
   const Fields<T> ff = fields(Lf, T()), fc = fields(Lc, T());
   RestrictArgs<T> a;
   a.gf = Lf.g;
   a.gc = Lc.g;
   for (int c = 0; c < 2; ++c) {
-    a.res[c] = ff.res[c];
+    a.phi[c] = ff.phi[c];
+    a.rhs[c] = ff.rhs[c];
+    a.diag[c] = Lf.level ? ff.diag[c] : nullptr;
     a.code[c] = Lf.code[c];
     a.crhs[c] = fc.rhs[c];
     a.cphi[c] = fc.phi[c];
@@ -859,15 +572,20 @@ cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool b
   const dim3 grid((Lc.g.nx + kBlockX - 1) / kBlockX, (Lc.g.ny + kBlockY - 1) / kBlockY, Lc.g.nz);
   const dim3 block(kBlockX, kBlockY);
   count_launch();
-  if (black_zero)
-    restrict_sum_kernel<true, T><<<grid, block, 0, s>>>(a);
-  else
-    restrict_sum_kernel<false, T><<<grid, block, 0, s>>>(a);
+#define GBMG_RESTRICT(K)                                                  \
+  if (black_zero) restrict_kernel<K, true, T><<<grid, block, 0, s>>>(a); \
+  else restrict_kernel<K, false, T><<<grid, block, 0, s>>>(a);
+  switch (kind_of(Lf.level, order)) {
+    case 0: GBMG_RESTRICT(0) break;
+    case 1: GBMG_RESTRICT(1) break;
+    default: GBMG_RESTRICT(2) break;
+  }
+#undef GBMG_RESTRICT
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t prolong_t(const LevelDev& Lc, const LevelDev& Lf, int order, cudaStream_t s) {
+cudaError_t prolong_t(const LevelDev& Lc, const LevelDev& Lf, int order, bool black_only, cudaStream_t s) {
   const Fields<T> ff = fields(Lf, T()), fc = fields(Lc, T());
   ProlongArgs<T> a;
   a.gf = Lf.g;
@@ -879,8 +597,10 @@ cudaError_t prolong_t(const LevelDev& Lc, const LevelDev& Lf, int order, cudaStr
     a.count[c] = Lf.count + lo * 2 + c;
     a.cphi[c] = fc.phi[c];
   }
+  a.skip_red = black_only ? 1 : 0;
+  const uint32_t n = (black_only ? 0u : Lf.hcount[lo * 2]) + Lf.hcount[lo * 2 + 1];
   count_launch();
-  prolong_list_kernel<T><<<exact_grid(Lf.hcount[lo * 2] + Lf.hcount[lo * 2 + 1], 2), kListBlock, 0, s>>>(a);
+  prolong_list_kernel<T><<<exact_grid(n, 2), kListBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -928,8 +648,10 @@ cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, b
                        : restrict_t<double>(Lf, Lc, order, black_zero, s);
 }
 
-cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, cudaStream_t s) {
-  return prec == kFP32 ? prolong_t<float>(Lc, Lf, order, s) : prolong_t<double>(Lc, Lf, order, s);
+cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, bool black_only,
+                           cudaStream_t s) {
+  return prec == kFP32 ? prolong_t<float>(Lc, Lf, order, black_only, s)
+                       : prolong_t<double>(Lc, Lf, order, black_only, s);
 }
 
 
@@ -1008,7 +730,7 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
       ListArgs<double> a = list_args<double>(L0, 2, c);
       a.partials = partials + c * grid;
       count_launch();
-      res_list_kernel<0, true, double><<<grid, kListBlock, 0, s>>>(a);
+      res_list_kernel<0, double><<<grid, kListBlock, 0, s>>>(a);
     }
   }
   count_launch();

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "hier_internal.h"
 #include "mg_internal.h"
 
 namespace gbmg {
@@ -24,6 +25,14 @@ static thread_local unsigned long long t_captured = 0;
 void count_launch(unsigned long long n) {
   if (t_capturing) t_captured += n;
   else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+void capture_count_begin() {
+  t_capturing = true;
+  t_captured = 0;
+}
+unsigned long long capture_count_end() {
+  t_capturing = false;
+  return t_captured;
 }
 
 }  // namespace gbmg
@@ -49,63 +58,6 @@ struct Arena {
     return off;
   }
 };
-
-struct TimedPair {
-  cudaEvent_t a, b;
-};
-
-// A captured multigrid iteration (plus the residual norm and its copy to the
-// pinned host scalar) for one order; replayed once per cycle.
-struct GraphSlot {
-  cudaGraphExec_t exec = nullptr;
-  int deepest = -2;                // deepest level at capture time
-  unsigned long long lists_hash = 0;  // list lengths at capture time (they size the grids)
-  unsigned long long nodes = 0;    // kernel launches per replay
-  std::vector<TimedPair> events;   // level-0 half-sweep event pairs (timing graphs)
-};
-
-}  // namespace
-
-struct mg_hierarchy {
-  mg_options opt;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cur = nullptr;          // stream the emitters launch on (stream, or cap_stream while capturing)
-  cudaStream_t cap_stream = nullptr;
-  GraphSlot graphs[3][2];              // [order][timing]
-  std::vector<TimedPair>* cap_events = nullptr;
-  size_t cap_events_used = 0;
-  bool own_stream = false;
-  int device = 0;
-  int nlev = 0;
-  double h = 0;
-  LevelDev L[kMaxLevels];
-  FineExtra F;
-  long long active[3][kMaxLevels];
-  int deepest[3];
-  int hold = 0;
-  char* arena = nullptr;
-  int8_t* mask_dev = nullptr;
-  uint32_t* list_scratch = nullptr;
-  double* partials = nullptr;
-  int max_partials = 0;
-  double* dscal = nullptr;             // device scalars
-  int* err_flag = nullptr;
-  unsigned long long* counts = nullptr;  // [kMaxLevels][2]
-  double* hscal = nullptr;               // pinned host scalars
-  void* staging = nullptr;
-  size_t staging_bytes = 0;
-  double r_zero = 0;
-  bool r_zero_valid = false;
-  bool prepared = false;  // mixed form: rhs32/e32 of level 0 match the current Phi and b
-  std::string last_error = "no error";
-  bool timing = false;
-  std::vector<TimedPair> events;
-  size_t events_used = 0;
-  long long timed_launches = 0;   // accumulated from graph replays
-  double timed_ms = 0;
-};
-
-namespace {
 
 struct DeviceGuard {
   int prev = -1;
@@ -260,7 +212,8 @@ mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool up
   CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, prec, H->cur),
                 "residual/restriction"));                                    // steps 2-5
   for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, l + 1, order, prec));  // step 5
-  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, prec, H->cur), "prolongation"));  // 6-7
+  CKS(launch_ok(H, launch_prolong(H->L[l + 1], H->L[l], order, prec, o.n_post >= 1, H->cur),
+                "prolongation"));  // steps 6-7
   return smooth(H, l, order, o.n_post, prec, update_last);                  // step 8
 }
 
@@ -596,8 +549,8 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   // one arena for every level array
   Arena A;
   struct Off {
-    size_t phi[2], rhs[2], invd[2], diag[2], code[2], res[2], list[3][2], count, S;
-    size_t f_phi[2], f_rhs[2], f_res[2], f_invd[2], f_diag[2];
+    size_t phi[2], rhs[2], invd[2], diag[2], code[2], list[3][2], count, S;
+    size_t f_phi[2], f_rhs[2], f_invd[2], f_diag[2];
   } off[kMaxLevels];
   const bool mixed = o.precision == 1;
   for (int l = 0; l < H->nlev; ++l) {
@@ -608,13 +561,11 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       off[l].phi[c] = A.reserve(sizeof(double) * g.total);
       off[l].rhs[c] = A.reserve(sizeof(double) * g.total);
       off[l].code[c] = A.reserve(g.total);
-      off[l].res[c] = A.reserve(sizeof(double) * g.total);
       for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
         off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)g.hx * g.ny * g.nz);
       if (mixed) {
         off[l].f_phi[c] = A.reserve(sizeof(float) * g.total);
         off[l].f_rhs[c] = A.reserve(sizeof(float) * g.total);
-        off[l].f_res[c] = A.reserve(sizeof(float) * g.total);
         if (l > 0) {
           off[l].f_invd[c] = A.reserve(sizeof(float) * g.total);
           off[l].f_diag[c] = A.reserve(sizeof(float) * g.total);
@@ -663,14 +614,12 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       H->L[l].phi[c] = (double*)(base + off[l].phi[c]);
       H->L[l].rhs[c] = (double*)(base + off[l].rhs[c]);
       H->L[l].code[c] = (uint8_t*)(base + off[l].code[c]);
-      H->L[l].res[c] = (double*)(base + off[l].res[c]);
       for (int o = (l == 0 ? 2 : 1); o <= 2; ++o) H->L[l].list[o][c] = (uint32_t*)(base + off[l].list[o][c]);
       if (l == 0) H->L[l].list[1][c] = H->L[l].list[2][c];
       H->L[l].list[0][c] = nullptr;
       LevelDev& Lm = H->L[l];
       Lm.phi32[c] = mixed ? (float*)(base + off[l].f_phi[c]) : nullptr;
       Lm.rhs32[c] = mixed ? (float*)(base + off[l].f_rhs[c]) : nullptr;
-      Lm.res32[c] = mixed ? (float*)(base + off[l].f_res[c]) : nullptr;
       Lm.invd32[c] = (mixed && l > 0) ? (float*)(base + off[l].f_invd[c]) : nullptr;
       Lm.diag32[c] = (mixed && l > 0) ? (float*)(base + off[l].f_diag[c]) : nullptr;
       H->L[l].invd[c] = l > 0 ? (double*)(base + off[l].invd[c]) : nullptr;
@@ -909,9 +858,14 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
         CK(H, cudaMemcpyAsync(H->F.save[c], H->L[0].phi[c], sizeof(double) * g0.total, cudaMemcpyDeviceToDevice,
                               H->stream));
     double r_prev = r_init;
+    // A step of the mixed form runs `inner` multigrid iterations, so the
+    // Section 4 test (per-iteration ratio > eta) compares the step's ratio
+    // with eta^inner: the geometric mean of the iterations' ratios against eta.
+    const int inner = o.precision == 1 ? o.inner_cycles : 1;
+    const double eta_step = std::pow(o.eta, (double)inner);
     for (cycles = 1; cycles <= max_cycles; ++cycles) {
       CKS(run_cycle(H, order, &r_n));
-      n_updates += updates(H, 0, order);
+      n_updates += updates(H, 0, order) * inner;
       if (info && cycles <= MG_HIST_MAX) info->hist[cycles] = r_n;
       if (!std::isfinite(r_n)) {
         st = MG_ERR_DIVERGED;
@@ -922,7 +876,7 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
         st = MG_OK;
         break;
       }
-      if (auto_switch && !switched && order == 2 && r_n >= 100.0 * DBL_EPSILON * r_zero && r_n / r_prev > o.eta) {
+      if (auto_switch && !switched && order == 2 && r_n >= 100.0 * DBL_EPSILON * r_zero && r_n / r_prev > eta_step) {
         order = 1;
         switched = true;
         H->hold = o.hold_solves;
@@ -1066,7 +1020,8 @@ mg_status mg_level_prolong(mg_hierarchy* H, int level, int order) {
   H->prepared = false;
   if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
   DeviceGuard guard(H->device);
-  CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, kFP64, H->stream), "prolongation"));
+  CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, kFP64, false, H->stream),
+                "prolongation"));
   CK(H, cudaStreamSynchronize(H->stream));
   return MG_OK;
 }

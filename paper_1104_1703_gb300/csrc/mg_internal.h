@@ -64,13 +64,11 @@ struct LevelDev {
   uint32_t* list[3][2];
   uint32_t* count;
   uint32_t hcount[6];  // host copy of count (sizes the launch grids)
-  double* res[2];    // scaled residual r^ of the active cells (restriction input)
   // FP32 copies for the inner cycles of the mixed-precision form (nullptr
   // when the hierarchy was created for FP64 only); level 0: phi32 is the
   // correction e, rhs32 is -r^ of the FP64 residual.
   float* phi32[2];
   float* rhs32[2];
-  float* res32[2];
   float* invd32[2];
   float* diag32[2];
 };
@@ -87,8 +85,13 @@ struct FineExtra {
   const int8_t* mask;  // natural-layout mask (device)
 };
 
-// Launch-count instrumentation.
+// Launch-count instrumentation.  Between capture_count_begin and
+// capture_count_end (one thread, around a stream capture) launches are
+// counted for the graph instead of the process; the graph's replays count
+// them with count_launch(nodes).
 void count_launch(unsigned long long n = 1);
+void capture_count_begin();
+unsigned long long capture_count_end();
 
 // ---- hierarchy build (kernels_build.cu) ----
 cudaError_t launch_build_fine(const LevelDev& L0, const int8_t* mask, unsigned long long* counts2,
@@ -130,7 +133,10 @@ cudaError_t init_cycle_kernels();
 // the black residual vanishes and only red cells are evaluated.
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, int prec,
                             cudaStream_t s);
-cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, cudaStream_t s);
+// black_only: correct the black unknowns only (a red half-sweep follows,
+// which overwrites the red ones without reading them).
+cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, bool black_only,
+                           cudaStream_t s);
 // Sum of squares of the scaled residual of level 0 into partials[0..nblocks),
 // then a fixed-order reduction into out[0].  red_only as black_zero above.
 // with_phi = false evaluates the residual of Phi = 0 (i.e. of the rhs alone).

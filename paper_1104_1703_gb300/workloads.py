@@ -269,3 +269,27 @@ def concentrated_patch(nc: int, r0: float, radius: float, d: float):
     return {"name": "concentrated_patch_d%.3f" % d, "mask": mask, "rho": concentrated_rho(x, y, z, r0),
             "h": h, "origin": (-2 * lo[0], -2 * lo[1], -2 * lo[2]),
             "phi_exact": concentrated_phi(x, y, z, r0), "corner": tuple(2 * v for v in lo)}
+
+
+# ---------------------------------------------------------------------------
+# Many AMR patches of one level (batched solve)
+# ---------------------------------------------------------------------------
+
+PATCH_EDGES = (32, 48, 64, 96, 128)
+
+
+def amr_patches(n: int = 96, seed: int = 4, edges=PATCH_EDGES, h: float = 1.0 / 512):
+    """n patches of one AMR level: each axis edge drawn uniformly from
+    `edges`, each patch a blob_patch (thresholded smoothed noise of
+    correlation length 8 cells, rho ~ U[-1,1], Dirichlet values from a
+    half-resolution coarse potential); all patches share the cell size h."""
+    rng = SplitMix64(seed)
+    picks = np.floor(rng.uniform(3 * n) * len(edges)).astype(int).reshape(n, 3)
+    out = []
+    for p in range(n):
+        nx, ny, nz = (edges[i] for i in picks[p])
+        w = blob_patch((nz, ny, nx), seed=seed * 100003 + p)
+        w["h"] = h
+        w["name"] = "patch%d_%dx%dx%d" % (p, nx, ny, nz)
+        out.append(w)
+    return out

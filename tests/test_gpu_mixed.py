@@ -99,6 +99,37 @@ def test_mixed_solve_against_oracle(dev, oracle, name):
     assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
 
 
+@pytest.mark.parametrize("name", ["ball64", "holes64", "blob48x32x40", "union64"])
+def test_mixed_three_inner_cycles(dev, oracle, name):
+    """Three FP32 V-cycles per refinement step: the same tolerance as checked
+    by the oracle's operator, the same order decision as the FP64 form (the
+    switch compares a step's ratio with eta^3), about a third of the steps,
+    and the update count of three V-cycles per step."""
+    w = CASES[name]
+    tol = w.get("tol", 1e-8)
+    faces = _faces(oracle, w)
+    H3 = _gpu(w, faces, precision=1, inner_cycles=3)
+    st, info = H3.solve(tol, 200)
+    assert st == 0 and info["rel"] < tol
+    R = oracle.Hierarchy(w["mask"], w["h"])
+    R.set_rhs(w["rho"])
+    if faces[0] is not None:
+        R.set_faces(*faces)
+    R.set_phi(H3.get_solution())
+    assert R.residual_norm() / R.residual_norm_zero() < tol * (1 + 1e-6)
+    H64 = _gpu(w, faces, precision=0)
+    st64, info64 = H64.solve(tol, 200)
+    assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
+    assert info64["cycles"] - 2 <= 3 * info["cycles"] <= info64["cycles"] + 5, (info["cycles"], info64["cycles"])
+    per = []
+    for order in (1, 2):   # updates of one V-cycle in each order
+        Ho = _gpu(w, faces, precision=1, order=order)
+        _, io = Ho.solve(1e-300, 1)
+        per.append(io["cell_updates"])
+    u = info["cell_updates"]
+    assert u % 3 == 0 and info["cycles"] * min(per) <= u // 3 <= info["cycles"] * max(per)
+
+
 def test_mixed_inner_cycles_and_graphs_agree(dev, oracle):
     w = CASES["ball64"]
     faces = _faces(oracle, w)
