@@ -79,7 +79,13 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *  inner_cycles    FP32 V-cycles per refinement step (precision 1), 1..8.
  *                  The stopping test and the switch act once per step; the
  *                  switch compares the step's residual ratio with
- *                  eta^inner_cycles (eta per multigrid iteration). */
+ *                  eta^inner_cycles (eta per multigrid iteration).
+ *  coarse_cluster  1 = run the middle coarse levels (4096 to 131072 cells per
+ *                  colour) and the bottom levels of a V-cycle as one launch of
+ *                  one thread-block cluster; 0 = one launch per step (faster
+ *                  on GB300: the replayed graph pipelines the launches, while
+ *                  each cluster-wide step costs a barrier).  The results are
+ *                  the same. */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -87,6 +93,7 @@ typedef struct {
   int use_graphs;
   int precision;
   int inner_cycles;
+  int coarse_cluster;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -107,7 +114,7 @@ typedef struct {
 
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
- * precision = 0 (FP64), inner_cycles = 1. */
+ * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

@@ -12,6 +12,37 @@ namespace {
 constexpr int kBlockX = 32, kBlockY = 4;
 constexpr int kListBlock = 256;
 
+// Programmatic dependent launch: the cycle's kernels are launched with
+// launch_pdl, so the GPU may schedule a kernel's blocks while the previous
+// kernel on the stream drains; each kernel waits here (griddepcontrol.wait,
+// a no-op without such a launch) before it reads or writes global memory,
+// which keeps the stream order of every memory access.
+// After its own wait, a kernel lets the next one be scheduled at once
+// (griddepcontrol.launch_dependents): that kernel's blocks become resident
+// and wait in their own pdl_wait until this kernel has completed, so the
+// next launch costs no gap.  The next kernel cannot start before every block
+// of this one has passed its wait, which keeps the chain one kernel deep.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // KIND 0: level 0 (D from the ghost-face count); 1: coarse, second order
 // (per-cell D and 1/D); 2: coarse, first order (D = 6).
 template <int KIND, typename T>

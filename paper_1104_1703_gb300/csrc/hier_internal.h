@@ -51,6 +51,15 @@ struct mg_hierarchy {
   char* arena = nullptr;
   int8_t* mask_dev = nullptr;
   uint32_t* list_scratch = nullptr;
+  // job tables (device, in the arena) of the batched build launches
+  gbmg::ListJob* list_jobs = nullptr;
+  int n_list_jobs = 0;
+  unsigned list_blocks = 0;
+  gbmg::ZeroJob* zero_jobs = nullptr;
+  int n_zero_jobs = 0;
+  gbmg::F32Job* f32_jobs = nullptr;
+  int n_f32_jobs = 0;
+  bool bc_zero = true;  // the folded boundary terms are all 0
   double* partials = nullptr;
   int max_partials = 0;
   double* dscal = nullptr;             // device scalars

@@ -69,6 +69,7 @@ template <bool FINE>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     batch_gs_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls,
                     const int* __restrict__ state) {
+  pdl_wait();
   __shared__ double tab[16];
   if (FINE) init_tab(tab);
   for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
@@ -126,6 +127,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     batch_norm_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls,
                       const int* __restrict__ state, double* __restrict__ partials) {
+  pdl_wait();
   __shared__ double tab[16];
   init_tab(tab);
   for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
@@ -156,11 +158,9 @@ __device__ __forceinline__ void restrict_chunk(const PatchLevel& Lc, const Patch
     const int i = threadIdx.x + u * blockDim.x;
     if (i >= C.n) continue;
     const long long at = list[i] & kListAt;
-    const int rel = (int)(at - gc.off0);
-    const int K = rel / (int)gc.sz;
-    const int rem = rel - K * (int)gc.sz;
-    const int J = rem / gc.P;
-    const int I = 2 * (rem - J * gc.P) + ((c ^ J ^ K) & 1);
+    int Q, J, K;
+    gc.slot_of(at, &Q, &J, &K);
+    const int I = 2 * Q + ((c ^ J ^ K) & 1);
     double sum = 0.0;
     for (int dk = 0; dk < 2; ++dk) {
       const int kf = 2 * K + dk;
@@ -185,6 +185,7 @@ __device__ __forceinline__ void restrict_chunk(const PatchLevel& Lc, const Patch
 __global__ void __launch_bounds__(kBatchMaxThreads)
     batch_restrict_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls,
                           const int* __restrict__ state, bool black_zero) {
+  pdl_wait();
   __shared__ double tab[16];
   init_tab(tab);
   for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
 __global__ void __launch_bounds__(kBatchMaxThreads)
     batch_prolong_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls,
                          const int* __restrict__ state) {
+  pdl_wait();
   for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
     const Chunk C = chunks[k];
     const PatchLevel& Lf = pls[C.pl];
@@ -225,11 +227,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
       ok[u] = i < C.n;
       if (!ok[u]) continue;
       at[u] = list[i] & kListAt;
-      const int rel = (int)(at[u] - gf.off0);
-      const int kk = rel / (int)gf.sz;
-      const int rem = rel - kk * (int)gf.sz;
-      const int j = rem / gf.P;
-      const int q = rem - j * gf.P;
+      int q, j, kk;
+      gf.slot_of(at[u], &q, &j, &kk);
       const int ix = 2 * q + ((c ^ j ^ kk) & 1);
       const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
       const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
@@ -275,6 +274,7 @@ __device__ void level0_sweeps(const PatchLevel& L, const uint32_t* n, int sweeps
 __global__ void __launch_bounds__(kBottomThreads)
     batch_bottom_kernel(const BatchBottom* __restrict__ args, int npatches, const PatchLevel* __restrict__ pls,
                         const int* __restrict__ state) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double tab[16];
   init_tab(tab);
@@ -299,6 +299,7 @@ constexpr int kSumThreads = 256;
 __global__ void __launch_bounds__(kSumThreads)
     batch_patch_sums_kernel(const double* __restrict__ partials, const int* __restrict__ first,
                             const int* __restrict__ count, int npatches, double* __restrict__ norm2) {
+  pdl_wait();
   for (int p = blockIdx.x; p < npatches; p += gridDim.x) {
     const double* part = partials + first[p];
     const int n = count[p];
@@ -370,8 +371,8 @@ cudaError_t launch_batch_gs(const Chunk* chunks, int nchunks, const PatchLevel* 
                             int threads, int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   count_launch();
-  if (fine) batch_gs_kernel<true><<<grid, threads, 0, s>>>(chunks, nchunks, pls, state);
-  else batch_gs_kernel<false><<<grid, threads, 0, s>>>(chunks, nchunks, pls, state);
+  if (fine) launch_pdl(batch_gs_kernel<true>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
+  else launch_pdl(batch_gs_kernel<false>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
   return cudaGetLastError();
 }
 
@@ -380,8 +381,8 @@ cudaError_t launch_batch_norm(const Chunk* chunks, int nchunks, const PatchLevel
   if (nchunks <= 0) return cudaSuccess;
   if (mode != 1 && mode != 2) return cudaErrorInvalidValue;
   count_launch();
-  if (mode == 1) batch_norm_kernel<1><<<grid, threads, 0, s>>>(chunks, nchunks, pls, state, partials);
-  else batch_norm_kernel<2><<<grid, threads, 0, s>>>(chunks, nchunks, pls, state, partials);
+  if (mode == 1) launch_pdl(batch_norm_kernel<1>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state, partials);
+  else launch_pdl(batch_norm_kernel<2>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state, partials);
   return cudaGetLastError();
 }
 
@@ -389,7 +390,7 @@ cudaError_t launch_batch_restrict(const Chunk* chunks, int nchunks, const PatchL
                                   bool black_zero, int threads, int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   count_launch();
-  batch_restrict_kernel<<<grid, threads, 0, s>>>(chunks, nchunks, pls, state, black_zero);
+  launch_pdl(batch_restrict_kernel, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state, black_zero);
   return cudaGetLastError();
 }
 
@@ -397,7 +398,7 @@ cudaError_t launch_batch_prolong(const Chunk* chunks, int nchunks, const PatchLe
                                  int threads, int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   count_launch();
-  batch_prolong_kernel<<<grid, threads, 0, s>>>(chunks, nchunks, pls, state);
+  launch_pdl(batch_prolong_kernel, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
   return cudaGetLastError();
 }
 
@@ -405,7 +406,7 @@ cudaError_t launch_batch_bottom(const void* dev_args, int npatches, const PatchL
                                 size_t smem_bytes, cudaStream_t s) {
   if (npatches <= 0) return cudaSuccess;
   count_launch();
-  batch_bottom_kernel<<<npatches, kBottomThreads, smem_bytes, s>>>(static_cast<const BatchBottom*>(dev_args),
+  launch_pdl(batch_bottom_kernel, dim3(npatches), dim3(kBottomThreads), smem_bytes, s, static_cast<const BatchBottom*>(dev_args),
                                                                    npatches, pls, state);
   return cudaGetLastError();
 }
@@ -414,7 +415,7 @@ cudaError_t launch_batch_patch_sums(const double* partials, const int* first, co
                                     double* norm2, cudaStream_t s) {
   if (npatches <= 0) return cudaSuccess;
   count_launch();
-  batch_patch_sums_kernel<<<npatches, kSumThreads, 0, s>>>(partials, first, count, npatches, norm2);
+  launch_pdl(batch_patch_sums_kernel, dim3(npatches), dim3(kSumThreads), 0, s, partials, first, count, npatches, norm2);
   return cudaGetLastError();
 }
 

@@ -152,6 +152,25 @@ __global__ void natural_to_split_kernel(Geom g, const double* __restrict__ nat, 
   }
 }
 
+// rho (natural layout) -> h^2 rho on the active cells (split layout) and the
+// folded right-hand side b = h^2 rho - (boundary terms) in the same pass
+// (bc null: the boundary terms are all zero).
+__global__ void set_rhs_kernel(Geom g, const double* __restrict__ rho, double h2, const uint8_t* code0,
+                               const uint8_t* code1, double* rh0, double* rh1, const double* __restrict__ bc0,
+                               const double* __restrict__ bc1, double* b0, double* b1) {
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const int c = colour_of(i, j, k);
+    const long long at = g.at(i >> 1, j, k);
+    const double v = ((c ? code1 : code0)[at] & kActive2) ? h2 * rho[idx] : 0.0;
+    (c ? rh1 : rh0)[at] = v;
+    (c ? b1 : b0)[at] = bc0 ? v - (c ? bc1 : bc0)[at] : v;
+  }
+}
+
 __global__ void split_to_natural_kernel(Geom g, const double* __restrict__ s0, const double* __restrict__ s1,
                                         double* __restrict__ nat) {
   const long long n = g.ncells();
@@ -286,20 +305,9 @@ __device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, 
   return (code[at] & bit) != 0;
 }
 
-__global__ void __launch_bounds__(kListThreads) list_count_kernel(Geom g, const uint8_t* __restrict__ code,
-                                                                  uint8_t bit, uint32_t* block_counts) {
-  const long long n = (long long)g.hx * g.ny * g.nz;
-  const long long e = blockIdx.x * (long long)kListThreads + threadIdx.x;
-  long long at;
-  int j, k;
-  const bool m = list_member(g, code, bit, e, n, at, j, k);
-  const int cnt = __syncthreads_count(m);
-  if (threadIdx.x == 0) block_counts[blockIdx.x] = (uint32_t)cnt;
-}
-
 // exclusive scan of nb block counts in place (one block of 1024 threads);
 // the total goes to *count
-__global__ void __launch_bounds__(1024) list_scan_kernel(uint32_t* block_counts, int nb, uint32_t* count) {
+__device__ void list_scan_block(uint32_t* block_counts, int nb, uint32_t* count) {
   __shared__ uint32_t part[1024];
   const int per = (nb + 1023) / 1024;
   const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
@@ -322,13 +330,13 @@ __global__ void __launch_bounds__(1024) list_scan_kernel(uint32_t* block_counts,
   if (threadIdx.x == 1023) *count = part[1023];
 }
 
-__global__ void __launch_bounds__(kListThreads) list_write_kernel(Geom g, const uint8_t* __restrict__ code,
-                                                                  int colour, uint8_t bit,
-                                                                  const uint32_t* __restrict__ block_offsets,
-                                                                  uint32_t* list) {
+// ordered writes of the members of local block `lb` of a list, from the
+// block's offset in it
+__device__ void list_write_block(const Geom& g, const uint8_t* __restrict__ code, int colour, uint8_t bit,
+                                 uint32_t block_offset, unsigned lb, uint32_t* list) {
   __shared__ uint32_t warp_base[kListThreads / 32];
   const long long n = (long long)g.hx * g.ny * g.nz;
-  const long long e = blockIdx.x * (long long)kListThreads + threadIdx.x;
+  const long long e = (long long)lb * kListThreads + threadIdx.x;
   long long at = 0;
   int j = 0, k = 0;
   const bool m = list_member(g, code, bit, e, n, at, j, k);
@@ -346,9 +354,70 @@ __global__ void __launch_bounds__(kListThreads) list_write_kernel(Geom g, const 
   }
   __syncthreads();
   if (m) {
-    const uint32_t pos = block_offsets[blockIdx.x] + warp_base[w] + __popc(bal & ((1u << lane) - 1u));
+    const uint32_t pos = block_offset + warp_base[w] + __popc(bal & ((1u << lane) - 1u));
     list[pos] = (uint32_t)at | (((colour ^ j ^ k) & 1) ? kListPlusX : 0u);
   }
+}
+
+// All the lists of a hierarchy in three launches: the same three passes,
+// with every block of a launch belonging to one list (a job) of the table.
+// Job b0 is the first global block of the job; the scratch holds one count
+// (then one offset) per global block.
+__device__ int find_job(const ListJob* jobs, int njobs, unsigned b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kListThreads) list_count_all_kernel(const ListJob* __restrict__ jobs, int njobs,
+                                                                      uint32_t* scratch) {
+  __shared__ int js;
+  if (threadIdx.x == 0) js = find_job(jobs, njobs, blockIdx.x);
+  __syncthreads();
+  const ListJob& J = jobs[js];
+  const Geom g = J.g;
+  const long long n = (long long)g.hx * g.ny * g.nz;
+  const long long e = (long long)(blockIdx.x - J.block0) * kListThreads + threadIdx.x;
+  long long at;
+  int j, k;
+  const bool m = list_member(g, J.code, J.bit, e, n, at, j, k);
+  const int cnt = __syncthreads_count(m);
+  if (threadIdx.x == 0) scratch[blockIdx.x] = (uint32_t)cnt;
+}
+
+// one block per job: exclusive scan of the job's block counts in place; the
+// job's total goes to *count
+__global__ void __launch_bounds__(1024) list_scan_all_kernel(const ListJob* __restrict__ jobs, uint32_t* scratch) {
+  const ListJob& J = jobs[blockIdx.x];
+  list_scan_block(scratch + J.block0, (int)J.nblocks, J.count);
+}
+
+__global__ void __launch_bounds__(kListThreads) list_write_all_kernel(const ListJob* __restrict__ jobs, int njobs,
+                                                                      const uint32_t* __restrict__ scratch) {
+  __shared__ int js;
+  if (threadIdx.x == 0) js = find_job(jobs, njobs, blockIdx.x);
+  __syncthreads();
+  const ListJob& J = jobs[js];
+  list_write_block(J.g, J.code, J.colour, J.bit, scratch[blockIdx.x], blockIdx.x - J.block0, J.list);
+}
+
+// Many device buffers zeroed, or converted FP64 -> FP32, in one launch:
+// blockIdx.y selects the buffer.
+__global__ void zero_many_kernel(const ZeroJob* __restrict__ jobs) {
+  const ZeroJob J = jobs[blockIdx.y];
+  unsigned long long* p = (unsigned long long*)J.ptr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.words; e += (long long)gridDim.x * blockDim.x)
+    p[e] = 0ull;
+}
+
+__global__ void to_f32_many_kernel(const F32Job* __restrict__ jobs) {
+  const F32Job J = jobs[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.n; e += (long long)gridDim.x * blockDim.x)
+    J.dst[e] = (float)J.src[e];
 }
 
 int grid_for(long long n) {
@@ -381,18 +450,27 @@ cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2
   return cudaGetLastError();
 }
 
-long long list_scratch_words(const Geom& g) {
-  return ((long long)g.hx * g.ny * g.nz + kListThreads - 1) / kListThreads + 1;
+cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_blocks, uint32_t* scratch,
+                               cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  count_launch(3);
+  list_count_all_kernel<<<total_blocks, kListThreads, 0, s>>>(jobs, njobs, scratch);
+  list_scan_all_kernel<<<njobs, 1024, 0, s>>>(jobs, scratch);
+  list_write_all_kernel<<<total_blocks, kListThreads, 0, s>>>(jobs, njobs, scratch);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_build_list(const Geom& g, const uint8_t* code, int colour, uint8_t bit, uint32_t* list,
-                              uint32_t* count, uint32_t* block_scratch, cudaStream_t s) {
-  const long long n = (long long)g.hx * g.ny * g.nz;
-  const int nb = (int)((n + kListThreads - 1) / kListThreads);
-  count_launch(3);
-  list_count_kernel<<<nb, kListThreads, 0, s>>>(g, code, bit, block_scratch);
-  list_scan_kernel<<<1, 1024, 0, s>>>(block_scratch, nb, count);
-  list_write_kernel<<<nb, kListThreads, 0, s>>>(g, code, colour, bit, block_scratch, list);
+cudaError_t launch_zero_many(const ZeroJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  count_launch();
+  zero_many_kernel<<<dim3(152 * 2, njobs), 256, 0, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32_many(const F32Job* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  count_launch();
+  to_f32_many_kernel<<<dim3(152 * 2, njobs), 256, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 
@@ -401,6 +479,15 @@ cudaError_t launch_natural_to_split(const Geom& g, const double* nat, double* ds
   count_launch();
   natural_to_split_kernel<<<grid_for(g.ncells()), kThreads, 0, s>>>(g, nat, dst0, dst1, scale, code[0], code[1],
                                                                      mask_bit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_rhs(const LevelDev& L0, const FineExtra& F, const double* rho, double h2, bool bc_zero,
+                           cudaStream_t s) {
+  count_launch();
+  set_rhs_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0.g, rho, h2, L0.code[0], L0.code[1], F.rhoh2[0],
+                                                               F.rhoh2[1], bc_zero ? nullptr : F.bc[0],
+                                                               bc_zero ? nullptr : F.bc[1], L0.rhs[0], L0.rhs[1]);
   return cudaGetLastError();
 }
 

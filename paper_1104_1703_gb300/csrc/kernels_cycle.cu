@@ -64,6 +64,7 @@ struct PerThread {
 // final once written, so Phi += e is applied in FP64 in the same pass.
 template <int KIND, typename T, bool UPDATE>
 __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
+  pdl_wait();
   constexpr int PER = PerThread<T>::value;
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
 // (the grid is fixed per level, so the partials do not depend on scheduling).
 template <int KIND, typename T>
 __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
+  pdl_wait();
   constexpr int PER = PerThread<T>::value;
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
@@ -154,6 +156,7 @@ constexpr int kSmallSmemBytes = 96 * 1024;
 // call, so every neighbour read is an on-chip load.
 template <int KIND, bool SMEM, typename T>
 __global__ void __launch_bounds__(kSmallThreads) smooth_small_kernel(SmallArgs<T> a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
@@ -219,6 +222,7 @@ struct RestrictArgs {
 // residual.  Children outside the active set (of this order) count 0.
 template <int KIND, bool BLACK_ZERO, typename T>
 __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArgs<T> a) {
+  pdl_wait();
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const Geom gf = a.gf, gc = a.gc;
@@ -279,6 +283,7 @@ __device__ __forceinline__ T coarse_at(const ProlongArgs<T>& a, int X, int Y, in
 // unknowns first would not change the result.
 template <typename T>
 __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T> a) {
+  pdl_wait();
   constexpr int PER = 2;
   const Geom gf = a.gf;
   const uint32_t n0 = a.skip_red ? 0u : *a.count[0], n = n0 + *a.count[1];
@@ -297,11 +302,8 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
       cc[u] = c;
       const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
       at[u] = e & kListAt;
-      const int rel = (int)(at[u] - gf.off0);
-      const int k = rel / (int)gf.sz;
-      const int rem = rel - k * (int)gf.sz;
-      const int j = rem / gf.P;
-      const int q = rem - j * gf.P;
+      int q, j, k;
+      gf.slot_of(at[u], &q, &j, &k);
       const int ix = 2 * q + ((c ^ j ^ k) & 1);
       const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
       const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
@@ -322,6 +324,7 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
 // The one-CTA bottom V-cycle (bottom_run) as a kernel of its own.
 template <int KIND, typename T, bool SMEM>
 __global__ void __launch_bounds__(kBottomThreads) bottom_kernel(BottomArgs<T> a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bottom_run<KIND, T, SMEM>(a, smem_raw);
 }
@@ -336,6 +339,7 @@ struct NormArgs {
 
 // sum of b^2 over the active cells (the residual of Phi = 0 is -b)
 __global__ void __launch_bounds__(kNormThreads) rhsnorm_kernel(NormArgs a) {
+  pdl_wait();
   const Geom g = a.g;
   const long long per_colour = (long long)g.hx * g.ny * g.nz;
   double acc = 0.0;
@@ -357,6 +361,7 @@ constexpr int kFinalThreads = 1024;
 
 __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const double* __restrict__ partials, int n,
                                                                  double* out) {
+  pdl_wait();
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int e = threadIdx.x;
   for (; e + 3 * kFinalThreads < n; e += 4 * kFinalThreads) {
@@ -388,6 +393,7 @@ struct RefineArgs {
 };
 
 __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs a) {
+  pdl_wait();
   constexpr int PER = 2;
   __shared__ double tab[16];
   init_tab(tab);
@@ -433,6 +439,7 @@ struct UpdateArgs {
 };
 
 __global__ void __launch_bounds__(kListBlock) refine_update_kernel(UpdateArgs a) {
+  pdl_wait();
   const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
   for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
     const int c = i >= n0;
@@ -441,10 +448,6 @@ __global__ void __launch_bounds__(kListBlock) refine_update_kernel(UpdateArgs a)
   }
 }
 
-__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    dst[e] = (float)src[e];
-}
 
 int kind_of(int level, int order) { return level == 0 ? 0 : (order == 1 ? 2 : 1); }
 uint8_t bit_of(int level, int order) { return (level >= 1 && order == 1) ? kActive1 : kActive2; }
@@ -513,13 +516,13 @@ cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, bool update, 
   count_launch();
   if (update) {
     if (L.level != 0 || sizeof(T) != 4) return cudaErrorInvalidValue;
-    gs_list_kernel<0, T, true><<<grid, kListBlock, 0, s>>>(a);
+    launch_pdl(gs_list_kernel<0, T, true>, dim3(grid), dim3(kListBlock), 0, s, a);
     return cudaGetLastError();
   }
   switch (kind_of(L.level, order)) {
-    case 0: gs_list_kernel<0, T, false><<<grid, kListBlock, 0, s>>>(a); break;
-    case 1: gs_list_kernel<1, T, false><<<grid, kListBlock, 0, s>>>(a); break;
-    default: gs_list_kernel<2, T, false><<<grid, kListBlock, 0, s>>>(a); break;
+    case 0: launch_pdl(gs_list_kernel<0, T, false>, dim3(grid), dim3(kListBlock), 0, s, a); break;
+    case 1: launch_pdl(gs_list_kernel<1, T, false>, dim3(grid), dim3(kListBlock), 0, s, a); break;
+    default: launch_pdl(gs_list_kernel<2, T, false>, dim3(grid), dim3(kListBlock), 0, s, a); break;
   }
   return cudaGetLastError();
 }
@@ -543,8 +546,8 @@ cudaError_t smooth_small_t(const LevelDev& L, int order, int sweeps, cudaStream_
   const size_t bytes = sm ? 2 * L.g.total * sizeof(T) : 0;
   count_launch();
 #define GBMG_SMALL(K)                                                         \
-  if (sm) smooth_small_kernel<K, true, T><<<1, kSmallThreads, bytes, s>>>(a); \
-  else smooth_small_kernel<K, false, T><<<1, kSmallThreads, 0, s>>>(a);
+  if (sm) launch_pdl(smooth_small_kernel<K, true, T>, dim3(1), dim3(kSmallThreads), bytes, s, a); \
+  else launch_pdl(smooth_small_kernel<K, false, T>, dim3(1), dim3(kSmallThreads), 0, s, a);
   switch (kind_of(L.level, order)) {
     case 0: GBMG_SMALL(0) break;
     case 1: GBMG_SMALL(1) break;
@@ -573,8 +576,8 @@ cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool b
   const dim3 block(kBlockX, kBlockY);
   count_launch();
 #define GBMG_RESTRICT(K)                                                  \
-  if (black_zero) restrict_kernel<K, true, T><<<grid, block, 0, s>>>(a); \
-  else restrict_kernel<K, false, T><<<grid, block, 0, s>>>(a);
+  if (black_zero) launch_pdl(restrict_kernel<K, true, T>, dim3(grid), dim3(block), 0, s, a); \
+  else launch_pdl(restrict_kernel<K, false, T>, dim3(grid), dim3(block), 0, s, a);
   switch (kind_of(Lf.level, order)) {
     case 0: GBMG_RESTRICT(0) break;
     case 1: GBMG_RESTRICT(1) break;
@@ -600,8 +603,182 @@ cudaError_t prolong_t(const LevelDev& Lc, const LevelDev& Lf, int order, bool bl
   a.skip_red = black_only ? 1 : 0;
   const uint32_t n = (black_only ? 0u : Lf.hcount[lo * 2]) + Lf.hcount[lo * 2 + 1];
   count_launch();
-  prolong_list_kernel<T><<<exact_grid(n, 2), kListBlock, 0, s>>>(a);
+  launch_pdl(prolong_list_kernel<T>, dim3(exact_grid(n, 2)), dim3(kListBlock), 0, s, a);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Middle levels in one thread-block cluster
+// ---------------------------------------------------------------------------
+//
+// The levels between the large ones (one launch per step, the whole GPU)
+// and the small ones (the one-CTA bottom) have from a few thousand to about
+// a hundred thousand unknowns per colour: too few to fill the GPU, so each
+// launch costs more in latency than in work.  mid_kernel runs them, and the
+// bottom after them, as one launch of one cluster of kMidCluster CTAs: the
+// steps of the Section 2 recipe are loops over the level's lists strided
+// over the cluster's threads, separated by hardware cluster barriers.  The
+// data stay in global memory (L2-resident at these sizes); values written by
+// another CTA of the cluster are read with ld.global.cg (L2, not the SM's
+// L1) after a __threadfence and the barrier.
+
+constexpr int kMidCluster = 8;
+constexpr int kMidThreads = 1024;
+constexpr int kMidMaxLevels = 4;
+constexpr int kMidPer = 4;  // list entries in flight per thread
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+template <typename T>
+__device__ __forceinline__ T nbr_sum_cg(const T* o, long long at, int dx, int P, long long sz) {
+  return ((ldcg(o + at) + ldcg(o + at + dx)) + (ldcg(o + at - P) + ldcg(o + at + P))) +
+         (ldcg(o + at - sz) + ldcg(o + at + sz));
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T>
+struct MidLevel {
+  Geom g;
+  T* phi[2];
+  T* rhs[2];
+  const T* invd[2];
+  const T* diag[2];
+  const uint8_t* code[2];
+  const uint32_t* list[2];  // unknowns of this order, per colour
+  const uint32_t* count;    // [colour], device memory
+};
+
+template <typename T>
+struct MidArgs {
+  MidLevel<T> L[kMidMaxLevels + 1];  // the middle levels m .. lb-1, then level lb
+  int nmid;
+  uint8_t bit;
+  int n_pre, n_post;
+  BottomArgs<T> bottom;  // levels lb .. deepest
+};
+
+// Gauss-Seidel sweeps of one middle level (as gs_list_kernel).
+template <int KIND, typename T>
+__device__ void mid_smooth(const MidLevel<T>& L, int sweeps, unsigned tid, unsigned nthr) {
+  const int P = L.g.P;
+  const long long sz = L.g.sz;
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t n = L.count[c];
+      const uint32_t* list = L.list[c];
+      for (uint32_t base = tid; base < n; base += kMidPer * nthr) {
+        long long at[kMidPer];
+        T v[kMidPer];
+        bool ok[kMidPer];
+#pragma unroll
+        for (int u = 0; u < kMidPer; ++u) {
+          const uint32_t i = base + u * nthr;
+          ok[u] = i < n;
+          const uint32_t e = ok[u] ? list[i] : 0u;
+          at[u] = e & kListAt;
+          if (ok[u])
+            v[u] = (nbr_sum_cg(L.phi[c ^ 1], at[u], (e & kListPlusX) ? 1 : -1, P, sz) - ldcg(L.rhs[c] + at[u])) *
+                   inv_diag<KIND>(0, L.invd[c], at[u], (const T*)nullptr);
+        }
+#pragma unroll
+        for (int u = 0; u < kMidPer; ++u)
+          if (ok[u]) L.phi[c][at[u]] = v[u];
+      }
+      cluster_barrier();
+    }
+}
+
+// Residual and R1 into the next level (as restrict_kernel), strided over
+// the coarse cells.
+template <int KIND, typename T>
+__device__ void mid_restrict(const MidLevel<T>& F, const MidLevel<T>& C, uint8_t bit, bool black_zero,
+                             unsigned tid, unsigned nthr) {
+  const Geom& g = F.g;
+  const Geom& gc = C.g;
+  const unsigned nc = (unsigned)(gc.nx * gc.ny * gc.nz);
+  for (unsigned e = tid; e < nc; e += nthr) {
+    const int I = (int)(e % gc.nx), t = (int)(e / gc.nx), J = t % gc.ny, K = t / gc.ny;
+    T sum = 0;
+    for (int dk = 0; dk < 2; ++dk) {
+      const int k = 2 * K + dk;
+      if (k >= g.nz) break;
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj;
+        if (j >= g.ny) break;
+        const long long at = g.at(I, j, k);
+        for (int c = 0; c < (black_zero ? 1 : 2); ++c) {
+          if (!(F.code[c][at] & bit)) continue;
+          const T nb = nbr_sum_cg(F.phi[c ^ 1], at, x_offset(c, j, k), g.P, g.sz);
+          sum += fma(-diag_of<KIND>(0, F.diag[c], at, (const T*)nullptr), ldcg(F.phi[c] + at), nb) -
+                 ldcg(F.rhs[c] + at);
+        }
+      }
+    }
+    const int Cc = (I + J + K) & 1;
+    const long long atc = gc.at(I >> 1, J, K);
+    C.rhs[Cc][atc] = T(-0.5) * sum;
+    C.phi[Cc][atc] = T(0);
+  }
+  cluster_barrier();
+}
+
+// P2 of level C into the listed unknowns of level F (as prolong_list_kernel).
+template <typename T>
+__device__ void mid_prolong(const MidLevel<T>& F, const MidLevel<T>& C, int first_colour, unsigned tid,
+                            unsigned nthr) {
+  const Geom& gf = F.g;
+  const Geom& gc = C.g;
+  auto coarse = [&](int X, int Y, int Z) { return ldcg(C.phi[(X + Y + Z) & 1] + gc.at(X >> 1, Y, Z)); };
+  for (int c = first_colour; c < 2; ++c) {
+    const uint32_t n = F.count[c];
+    for (uint32_t i = tid; i < n; i += nthr) {
+      const long long at = F.list[c][i] & kListAt;
+      int q, j, k;
+      gf.slot_of(at, &q, &j, &k);
+      const int ix = 2 * q + ((c ^ j ^ k) & 1);
+      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
+      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
+      const T e0 = coarse(Xn, Yn, Zn);
+      const T e1 = (coarse(Xf, Yn, Zn) + coarse(Xn, Yf, Zn)) + coarse(Xn, Yn, Zf);
+      const T e2 = (coarse(Xn, Yf, Zf) + coarse(Xf, Yn, Zf)) + coarse(Xf, Yf, Zn);
+      const T e3 = coarse(Xf, Yf, Zf);
+      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      F.phi[c][at] = fma(w, T(1) / T(64), ldcg(F.phi[c] + at));
+    }
+  }
+  cluster_barrier();
+}
+
+// The Section 2 recipe (V-cycle) from level m, whose right-hand side the
+// restriction from level m-1 has set, down through the middle levels, the
+// bottom (run by CTA 0 of the cluster, from shared memory when SMEM), and
+// back up to level m.  Launched as a single cluster of kMidCluster CTAs.
+template <int KIND, typename T, bool SMEM>
+__global__ void __launch_bounds__(kMidThreads, 1) mid_kernel(MidArgs<T> a) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const unsigned nthr = kMidCluster * blockDim.x;
+  const unsigned tid = rank * blockDim.x + threadIdx.x;
+  for (int i = 0; i < a.nmid; ++i) {
+    mid_smooth<KIND>(a.L[i], a.n_pre, tid, nthr);                              // step 1
+    mid_restrict<KIND>(a.L[i], a.L[i + 1], a.bit, a.n_pre >= 1, tid, nthr);  // steps 2-5
+  }
+  if (rank == 0) bottom_run<KIND, T, SMEM>(a.bottom, smem_raw);
+  cluster_barrier();
+  for (int i = a.nmid - 1; i >= 0; --i) {
+    mid_prolong(a.L[i], a.L[i + 1], a.n_post >= 1 ? 1 : 0, tid, nthr);  // steps 6-7
+    mid_smooth<KIND>(a.L[i], a.n_post, tid, nthr);                       // step 8
+  }
 }
 
 }  // namespace
@@ -630,6 +807,14 @@ cudaError_t init_cycle_kernels() {
   GBMG_BOTTOM_ATTR(1, float)
   GBMG_BOTTOM_ATTR(2, float)
 #undef GBMG_BOTTOM_ATTR
+#define GBMG_MID_ATTR(K, T)                                                                                    \
+  if (e == cudaSuccess)                                                                                        \
+    e = cudaFuncSetAttribute(mid_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemBytes);
+  GBMG_MID_ATTR(1, double)
+  GBMG_MID_ATTR(2, double)
+  GBMG_MID_ATTR(1, float)
+  GBMG_MID_ATTR(2, float)
+#undef GBMG_MID_ATTR
   return e;
 }
 
@@ -655,12 +840,13 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, in
 }
 
 
+// Fills the bottom arguments for levels lb .. deepest; returns the dynamic
+// shared memory they need staged (0 when they do not fit: global memory).
 template <typename T>
-cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
-                     cudaStream_t s) {
-  BottomArgs<T> a;
+bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
+                 BottomArgs<T>& a, size_t* smem_bytes) {
   a.nlev = deepest - lb + 1;
-  if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return cudaErrorInvalidValue;
+  if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return false;
   long long off = 0;
   for (int i = 0; i < a.nlev; ++i) {
     const LevelDev& L = levels[lb + i];
@@ -683,22 +869,88 @@ cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int
   a.n_post = n_post;
   a.coarse_sweeps = coarse_sweeps;
   const size_t bytes = (size_t)off * sizeof(T);
-  const bool sm = bytes <= (size_t)kBottomSmemBytes;
+  *smem_bytes = bytes <= (size_t)kBottomSmemBytes ? bytes : 0;
+  return true;
+}
+
+template <typename T>
+cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
+                     cudaStream_t s) {
+  BottomArgs<T> a;
+  size_t bytes = 0;
+  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, a, &bytes)) return cudaErrorInvalidValue;
+  const bool sm = bytes > 0;
   count_launch();
   if (order == 1) {
-    if (sm) bottom_kernel<2, T, true><<<1, kBottomThreads, bytes, s>>>(a);
-    else bottom_kernel<2, T, false><<<1, kBottomThreads, 0, s>>>(a);
+    if (sm) launch_pdl(bottom_kernel<2, T, true>, dim3(1), dim3(kBottomThreads), bytes, s, a);
+    else launch_pdl(bottom_kernel<2, T, false>, dim3(1), dim3(kBottomThreads), 0, s, a);
   } else {
-    if (sm) bottom_kernel<1, T, true><<<1, kBottomThreads, bytes, s>>>(a);
-    else bottom_kernel<1, T, false><<<1, kBottomThreads, 0, s>>>(a);
+    if (sm) launch_pdl(bottom_kernel<1, T, true>, dim3(1), dim3(kBottomThreads), bytes, s, a);
+    else launch_pdl(bottom_kernel<1, T, false>, dim3(1), dim3(kBottomThreads), 0, s, a);
   }
   return cudaGetLastError();
+}
+
+template <int KIND, typename T, bool SMEM>
+cudaError_t launch_mid_cluster(const MidArgs<T>& a, size_t bytes, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kMidCluster, 1, 1);
+  cfg.blockDim = dim3(kMidThreads, 1, 1);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kMidCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mid_kernel<KIND, T, SMEM>, a);
+}
+
+template <typename T>
+cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
+                  int coarse_sweeps, cudaStream_t s) {
+  MidArgs<T> a;
+  a.nmid = lb - m;
+  if (m < 1 || a.nmid < 1 || a.nmid > kMidMaxLevels) return cudaErrorInvalidValue;
+  for (int i = 0; i <= a.nmid; ++i) {
+    const LevelDev& L = levels[m + i];
+    const Fields<T> f = fields(L, T());
+    a.L[i].g = L.g;
+    for (int c = 0; c < 2; ++c) {
+      a.L[i].phi[c] = f.phi[c];
+      a.L[i].rhs[c] = f.rhs[c];
+      a.L[i].invd[c] = f.invd[c];
+      a.L[i].diag[c] = f.diag[c];
+      a.L[i].code[c] = L.code[c];
+      a.L[i].list[c] = L.list[order][c];
+    }
+    a.L[i].count = L.count + order * 2;
+  }
+  a.bit = bit_of(m, order);
+  a.n_pre = n_pre;
+  a.n_post = n_post;
+  size_t bytes = 0;
+  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, a.bottom, &bytes))
+    return cudaErrorInvalidValue;
+  count_launch();
+  if (order == 1) return bytes ? launch_mid_cluster<2, T, true>(a, bytes, s) : launch_mid_cluster<2, T, false>(a, 0, s);
+  return bytes ? launch_mid_cluster<1, T, true>(a, bytes, s) : launch_mid_cluster<1, T, false>(a, 0, s);
 }
 
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
                           int coarse_sweeps, int prec, cudaStream_t s) {
   return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s)
                        : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s);
+}
+
+bool mid_level(const Geom& g) { return (long long)g.hx * g.ny * g.nz <= kMidSlots; }
+
+cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
+                       int coarse_sweeps, int prec, cudaStream_t s) {
+  return prec == kFP32 ? mid_t<float>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps, s)
+                       : mid_t<double>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps, s);
 }
 
 int residual_norm_blocks(const Geom& g) {
@@ -721,7 +973,7 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
     a.partials = partials;
     blocks = 152 * 8;
     count_launch();
-    rhsnorm_kernel<<<blocks, kNormThreads, 0, s>>>(a);
+    launch_pdl(rhsnorm_kernel, dim3(blocks), dim3(kNormThreads), 0, s, a);
   } else {
     const int grid = list_grid(L0.g);
     blocks = red_only ? grid : 2 * grid;
@@ -730,11 +982,11 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
       ListArgs<double> a = list_args<double>(L0, 2, c);
       a.partials = partials + c * grid;
       count_launch();
-      res_list_kernel<0, double><<<grid, kListBlock, 0, s>>>(a);
+      launch_pdl(res_list_kernel<0, double>, dim3(grid), dim3(kListBlock), 0, s, a);
     }
   }
   count_launch();
-  finalize_kernel<<<1, kFinalThreads, 0, s>>>(partials, blocks, out);
+  launch_pdl(finalize_kernel, dim3(1), dim3(kFinalThreads), 0, s, partials, blocks, out);
   return cudaGetLastError();
 }
 
@@ -755,8 +1007,8 @@ cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max
   const int blocks = 2 * list_grid(L0.g);
   if (blocks > max_partials) return cudaErrorInvalidValue;
   count_launch(2);
-  refine_residual_kernel<<<blocks, kListBlock, 0, s>>>(a);
-  finalize_kernel<<<1, kFinalThreads, 0, s>>>(partials, blocks, out);
+  launch_pdl(refine_residual_kernel, dim3(blocks), dim3(kListBlock), 0, s, a);
+  launch_pdl(finalize_kernel, dim3(1), dim3(kFinalThreads), 0, s, partials, blocks, out);
   return cudaGetLastError();
 }
 
@@ -769,17 +1021,10 @@ cudaError_t launch_refine_update(const LevelDev& L0, cudaStream_t s) {
     a.count[c] = L0.count + 4 + c;
   }
   count_launch();
-  refine_update_kernel<<<exact_grid(L0.hcount[4] + L0.hcount[5], 1), kListBlock, 0, s>>>(a);
+  launch_pdl(refine_update_kernel, dim3(exact_grid(L0.hcount[4] + L0.hcount[5], 1)), dim3(kListBlock), 0, s, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
-  long long b = (n + 255) / 256;
-  if (b > 152 * 32) b = 152 * 32;
-  if (b < 1) b = 1;
-  count_launch();
-  to_f32_kernel<<<(int)b, 256, 0, s>>>(src, dst, n);
-  return cudaGetLastError();
-}
+
 
 }  // namespace gbmg

@@ -103,13 +103,15 @@ Geom make_geom(int nx, int ny, int nz) {
   g.sz = (long long)(ny + 2) * g.P;
   g.off0 = g.sz + g.P;
   g.total = (long long)(nz + 2) * g.sz;
+  g.set_divisors();
   return g;
 }
 
 bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
-         (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8;
+         (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
+         (o.coarse_cluster == 0 || o.coarse_cluster == 1);
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -207,6 +209,15 @@ mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool up
     return launch_ok(H, launch_bottom(H->L, l, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps, prec,
                                       H->cur),
                      "bottom cycle");
+  // the middle levels and the bottom as one launch of a thread-block cluster
+  if (l >= 1 && o.n_cycles == 1 && o.coarse_cluster && mid_level(H->L[l].g) && l < H->deepest[order]) {
+    int lb = l + 1;
+    while (lb < H->deepest[order] && !small_level(H->L[lb].g)) ++lb;
+    if (lb - l <= 4)
+      return launch_ok(H, launch_mid(H->L, l, lb, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps,
+                                     prec, H->cur),
+                       "middle levels");
+  }
   if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec, update_last);
   CKS(smooth(H, l, order, o.n_pre, prec));                                  // step 1
   CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, prec, H->cur),
@@ -231,13 +242,13 @@ bool ends_with_sweep(const mg_hierarchy* H, int order) {
   return H->deepest[order] == 0 ? H->opt.coarse_sweeps >= 1 : H->opt.n_post >= 1;
 }
 
-// Enqueues the residual norm (squared, scaled) and its copy to the pinned
-// host scalar on H->cur.
-mg_status emit_norm2(mg_hierarchy* H, bool red_only, bool with_phi) {
-  CKS(launch_ok(H, launch_residual_norm2(H->L[0], red_only, with_phi, H->partials, H->max_partials, H->dscal,
-                                        H->cur),
+// Enqueues the residual norm (squared, scaled) and its copy to pinned host
+// scalar `slot` on H->cur.
+mg_status emit_norm2(mg_hierarchy* H, bool red_only, bool with_phi, int slot = 0) {
+  CKS(launch_ok(H, launch_residual_norm2(H->L[0], red_only, with_phi, H->partials, H->max_partials,
+                                        H->dscal + slot, H->cur),
                 "residual norm"));
-  CK(H, cudaMemcpyAsync(H->hscal, H->dscal, sizeof(double), cudaMemcpyDeviceToHost, H->cur));
+  CK(H, cudaMemcpyAsync(H->hscal + slot, H->dscal + slot, sizeof(double), cudaMemcpyDeviceToHost, H->cur));
   return MG_OK;
 }
 
@@ -378,30 +389,25 @@ mg_status zero_split(mg_hierarchy* H, const Geom& g, double* const* a) {
 }
 
 // Hierarchy build (mask sums, codes, diagonals, counts) from H->mask_dev.
-mg_status build_levels(mg_hierarchy* H) {
+// fine_built: level 0's codes and counts were already built from that mask.
+mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
   cudaStream_t s = H->stream;
-  CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2 * kMaxLevels, s));
-  CKS(launch_ok(H, launch_build_fine(H->L[0], H->mask_dev, H->counts, s), "fine build"));
+  if (!fine_built) {
+    CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2 * kMaxLevels, s));
+    CKS(launch_ok(H, launch_build_fine(H->L[0], H->mask_dev, H->counts, s), "fine build"));
+  } else {
+    CK(H, cudaMemsetAsync(H->counts + 2, 0, sizeof(unsigned long long) * 2 * (kMaxLevels - 1), s));
+  }
   for (int l = 0; l + 1 < H->nlev; ++l) {
     CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? H->mask_dev : nullptr, H->L[l + 1], s), "mask R1"));
     CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
   }
-  // FP32 copies of the coarse diagonals for the mixed form
-  for (int l = 1; l < H->nlev; ++l)
-    if (H->L[l].invd32[0])
-      for (int c = 0; c < 2; ++c) {
-        CKS(launch_ok(H, launch_to_f32(H->L[l].invd[c], H->L[l].invd32[c], H->L[l].g.total, s), "fp32 copy"));
-        CKS(launch_ok(H, launch_to_f32(H->L[l].diag[c], H->L[l].diag32[c], H->L[l].g.total, s), "fp32 copy"));
-      }
-  // compact lists of the unknowns, per order and colour (level 0: one set)
-  for (int l = 0; l < H->nlev; ++l) {
-    LevelDev& L = H->L[l];
-    for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
-      for (int c = 0; c < 2; ++c)
-        CKS(launch_ok(H, launch_build_list(L.g, L.code[c], c, o == 2 ? kActive2 : kActive1, L.list[o][c],
-                                           L.count + o * 2 + c, H->list_scratch, s),
-                      "active lists"));
-  }
+  // FP32 copies of the coarse diagonals for the mixed form (one launch)
+  CKS(launch_ok(H, launch_to_f32_many(H->f32_jobs, H->n_f32_jobs, s), "fp32 copy"));
+  // compact lists of the unknowns, per order and colour (level 0: one set),
+  // all in three launches
+  CKS(launch_ok(H, launch_build_lists(H->list_jobs, H->n_list_jobs, H->list_blocks, H->list_scratch, s),
+                "active lists"));
   unsigned long long hc[2 * kMaxLevels];
   CK(H, cudaMemcpyAsync(hc, H->counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
   for (int l = 0; l < H->nlev; ++l)
@@ -420,12 +426,9 @@ mg_status build_levels(mg_hierarchy* H) {
 }
 
 mg_status reset_fields(mg_hierarchy* H) {
-  for (int l = 0; l < H->nlev; ++l) {
-    CKS(zero_split(H, H->L[l].g, H->L[l].phi));
-    CKS(zero_split(H, H->L[l].g, H->L[l].rhs));
-  }
-  CKS(zero_split(H, H->L[0].g, H->F.rhoh2));
-  CKS(zero_split(H, H->L[0].g, H->F.bc));
+  // Phi and b of every level, h^2 rho and the folded boundary terms: one launch
+  CKS(launch_ok(H, launch_zero_many(H->zero_jobs, H->n_zero_jobs, H->stream), "field reset"));
+  H->bc_zero = true;
   H->r_zero_valid = false;
   H->prepared = false;
   return MG_OK;
@@ -477,6 +480,7 @@ void mg_default_options(mg_options* opt) {
   opt->use_graphs = 1;
   opt->precision = 0;
   opt->inner_cycles = 1;
+  opt->coarse_cluster = 0;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -579,7 +583,30 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     if (l > 0) off[l].S = A.reserve(sizeof(int32_t) * g.ncells());
     off[l].count = A.reserve(sizeof(uint32_t) * 6);
   }
-  const size_t o_lscr = A.reserve(sizeof(uint32_t) * list_scratch_words(H->L[0].g));
+  // batched build launches: one scratch word per list block of every list
+  std::vector<ListJob> ljobs;
+  unsigned lblocks = 0;
+  for (int l = 0; l < H->nlev; ++l) {
+    const Geom& g = H->L[l].g;
+    const unsigned nb = (unsigned)(((long long)g.hx * g.ny * g.nz + 255) / 256);
+    for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+      for (int c = 0; c < 2; ++c) {
+        ListJob j = {};
+        j.g = g;
+        j.block0 = lblocks;
+        j.nblocks = nb;
+        j.colour = c;
+        j.bit = o == 2 ? kActive2 : kActive1;
+        ljobs.push_back(j);
+        lblocks += nb;
+      }
+  }
+  const int n_zero = 4 * H->nlev + 4;
+  const int n_f32 = mixed ? 4 * (H->nlev - 1) : 0;
+  const size_t o_lscr = A.reserve(sizeof(uint32_t) * ((size_t)lblocks + 1));
+  const size_t o_ljobs = A.reserve(sizeof(ListJob) * ljobs.size());
+  const size_t o_zjobs = A.reserve(sizeof(ZeroJob) * n_zero);
+  const size_t o_fjobs = A.reserve(sizeof(F32Job) * (n_f32 > 0 ? n_f32 : 1));
   const Geom& g0 = H->L[0].g;
   size_t o_rhoh2[2], o_bc[2], o_save[2];
   for (int c = 0; c < 2; ++c) {
@@ -629,6 +656,10 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     H->L[l].count = (uint32_t*)(base + off[l].count);
   }
   H->list_scratch = (uint32_t*)(base + o_lscr);
+  H->list_jobs = (ListJob*)(base + o_ljobs);
+  H->zero_jobs = (ZeroJob*)(base + o_zjobs);
+  H->f32_jobs = (F32Job*)(base + o_fjobs);
+  H->list_blocks = lblocks;
   for (int c = 0; c < 2; ++c) {
     H->F.rhoh2[c] = (double*)(base + o_rhoh2[c]);
     H->F.bc[c] = (double*)(base + o_bc[c]);
@@ -649,6 +680,47 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
                         where == MG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, H->stream);
     if (e != cudaSuccess) st = cuda_fail(H, e, "mask copy");
   }
+  // job tables of the batched build launches (after the arena is zeroed)
+  if (st == MG_OK) {
+    size_t jn = 0;
+    for (int l = 0; l < H->nlev; ++l)
+      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+        for (int c = 0; c < 2; ++c, ++jn) {
+          ljobs[jn].code = H->L[l].code[c];
+          ljobs[jn].list = H->L[l].list[o][c];
+          ljobs[jn].count = H->L[l].count + o * 2 + c;
+        }
+    std::vector<ZeroJob> zjobs;
+    for (int l = 0; l < H->nlev; ++l)
+      for (int c = 0; c < 2; ++c) {
+        zjobs.push_back({H->L[l].phi[c], H->L[l].g.total});
+        zjobs.push_back({H->L[l].rhs[c], H->L[l].g.total});
+      }
+    for (int c = 0; c < 2; ++c) {
+      zjobs.push_back({H->F.rhoh2[c], g0.total});
+      zjobs.push_back({H->F.bc[c], g0.total});
+    }
+    std::vector<F32Job> fjobs;
+    for (int l = 1; mixed && l < H->nlev; ++l)
+      for (int c = 0; c < 2; ++c) {
+        fjobs.push_back({H->L[l].invd[c], H->L[l].invd32[c], H->L[l].g.total});
+        fjobs.push_back({H->L[l].diag[c], H->L[l].diag32[c], H->L[l].g.total});
+      }
+    H->n_list_jobs = (int)ljobs.size();
+    H->n_zero_jobs = (int)zjobs.size();
+    H->n_f32_jobs = (int)fjobs.size();
+    cudaError_t ej = cudaMemcpyAsync(H->list_jobs, ljobs.data(), sizeof(ListJob) * ljobs.size(),
+                                     cudaMemcpyHostToDevice, H->stream);
+    if (ej == cudaSuccess)
+      ej = cudaMemcpyAsync(H->zero_jobs, zjobs.data(), sizeof(ZeroJob) * zjobs.size(), cudaMemcpyHostToDevice,
+                           H->stream);
+    if (ej == cudaSuccess && !fjobs.empty())
+      ej = cudaMemcpyAsync(H->f32_jobs, fjobs.data(), sizeof(F32Job) * fjobs.size(), cudaMemcpyHostToDevice,
+                           H->stream);
+    if (ej == cudaSuccess) ej = cudaStreamSynchronize(H->stream);  // the host tables go out of scope
+    if (ej != cudaSuccess) st = cuda_fail(H, ej, "job tables");
+  }
+
   if (st == MG_OK) st = build_levels(H);
   if (st == MG_OK && H->deepest[2] < 0) st = fail(H, MG_ERR_EMPTY_DOMAIN, "the mask has no active cell");
   if (st != MG_OK) {
@@ -683,7 +755,7 @@ mg_status mg_update_mask(mg_hierarchy* H, const int8_t* mask, mg_mem where) {
     return fail(H, MG_ERR_EMPTY_DOMAIN, "the mask has no active cell");
   }
   CK(H, cudaMemcpyAsync(H->mask_dev, H->staging, g0.ncells(), cudaMemcpyDeviceToDevice, H->stream));
-  CKS(build_levels(H));
+  CKS(build_levels(H, true));  // level 0 was just built from the same mask
   return reset_fields(H);
 }
 
@@ -695,10 +767,8 @@ mg_status mg_set_rhs(mg_hierarchy* H, const double* rho, mg_mem where) {
   if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
   const void* src;
   CKS(device_view(H, rho, where, bytes, 0, &src));
-  CKS(launch_ok(H, launch_natural_to_split(g0, (const double*)src, H->F.rhoh2[0], H->F.rhoh2[1], H->h * H->h,
-                                          H->L[0].code, kActive2, H->stream),
-                "rho layout"));
-  CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+  CKS(launch_ok(H, launch_set_rhs(H->L[0], H->F, (const double*)src, H->h * H->h, H->bc_zero, H->stream),
+                "rho layout and rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
   H->prepared = false;
@@ -709,6 +779,17 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   DeviceGuard guard(H->device);
   const Geom& g = H->L[0].g;
+  if (!bx && !by && !bz) {
+    // homogeneous Dirichlet values: nothing to fold when the folded terms
+    // are already zero
+    if (H->bc_zero) return MG_OK;
+    CKS(zero_split(H, g, H->F.bc));
+    CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
+    H->bc_zero = true;
+    H->r_zero_valid = false;
+    H->prepared = false;
+    return MG_OK;
+  }
   const size_t nfx = (size_t)(g.nx + 1) * g.ny * g.nz, nfy = (size_t)g.nx * (g.ny + 1) * g.nz,
                nfz = (size_t)g.nx * g.ny * (g.nz + 1);
   const void *dx = nullptr, *dy = nullptr, *dz = nullptr;
@@ -721,6 +802,7 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
   CKS(launch_ok(H, launch_fold_faces(H->L[0], H->F, (const double*)dx, (const double*)dy, (const double*)dz,
                                     H->stream),
                 "face fold"));
+  H->bc_zero = false;
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
@@ -739,6 +821,7 @@ mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_
   const void* src;
   CKS(device_view(H, phi_c, where, bytes, 0, &src));
   CK(H, cudaMemsetAsync(H->err_flag, 0, sizeof(int), H->stream));
+  H->bc_zero = false;
   CKS(launch_ok(H, launch_fold_coarse(H->L[0], H->F, (const double*)src, cnx, cny, cnz, ox, oy, oz, H->err_flag,
                                      H->stream),
                 "coarse interpolation"));
@@ -748,6 +831,7 @@ mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_
   std::memcpy(&err, H->hscal, sizeof(int));
   if (err) {
     CKS(zero_split(H, H->L[0].g, H->F.bc));
+    H->bc_zero = true;
     CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
     H->r_zero_valid = false;
   H->prepared = false;
@@ -821,16 +905,23 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
   if (H->deepest[order] < 0) order = 2;
   const Geom& g0 = H->L[0].g;
   double r_zero, r_init;
-  CKS(residual_zero(H, &r_zero));
+  // ||r(Phi = 0)|| (unless cached) and ||r(initial guess)||, one wait for both
+  const bool need_zero = !H->r_zero_valid;
+  if (need_zero) CKS(emit_norm2(H, false, false, 1));
   if (o.precision == 1) {
     // the FP64 residual of the initial guess also prepares the first FP32 step
     CKS(emit_refine_residual(H));
-    CK(H, cudaStreamSynchronize(H->stream));
-    r_init = std::sqrt(H->hscal[0]) / (H->h * H->h);
     H->prepared = true;
   } else {
-    CKS(residual(H, false, &r_init));
+    CKS(emit_norm2(H, false, true, 0));
   }
+  CK(H, cudaStreamSynchronize(H->stream));
+  if (need_zero) {
+    H->r_zero = std::sqrt(H->hscal[1]) / (H->h * H->h);
+    H->r_zero_valid = true;
+  }
+  r_zero = H->r_zero;
+  r_init = std::sqrt(H->hscal[0]) / (H->h * H->h);
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->r_zero = r_zero;

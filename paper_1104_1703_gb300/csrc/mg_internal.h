@@ -42,8 +42,34 @@ struct Geom {
   long long sz;        // plane stride: (ny + 2) * P
   long long off0;      // element offset of slot (0, 0, 0): sz + P
   long long total;     // elements per colour array: (nz + 2) * sz
+  // Division of an element offset n (0 <= n < 2^31) by sz and by P without
+  // an integer divide: floor(n / d) = (n * m) >> (31 + l) with l = ceil(log2 d)
+  // and m = ceil(2^(31+l) / d) (Granlund & Montgomery, PLDI 1994, Thm 4.2:
+  // exact when 2^(31+l) <= m d <= 2^(31+l) + 2^l).  Set by set_divisors().
+  unsigned long long m_sz, m_P;
+  int s_sz, s_P;
   __host__ __device__ long long at(int q, int j, int k) const { return off0 + k * sz + (long long)j * P + q; }
   __host__ __device__ long long ncells() const { return (long long)nx * ny * nz; }
+  __host__ __device__ int div_sz(unsigned n) const { return (int)(((unsigned long long)n * m_sz) >> s_sz); }
+  __host__ __device__ int div_P(unsigned n) const { return (int)(((unsigned long long)n * m_P) >> s_P); }
+  // (q, j, k) of the element at offset `at` of a colour array
+  __host__ __device__ void slot_of(long long at, int* q, int* j, int* k) const {
+    const unsigned rel = (unsigned)(at - off0);
+    *k = div_sz(rel);
+    const unsigned rem = rel - (unsigned)(*k) * (unsigned)sz;
+    *j = div_P(rem);
+    *q = (int)(rem - (unsigned)(*j) * (unsigned)P);
+  }
+  void set_divisors() {
+    auto magic = [](unsigned long long d, unsigned long long* m, int* s) {
+      int l = 0;
+      while ((1ULL << l) < d) ++l;
+      *s = 31 + l;
+      *m = ((1ULL << (31 + l)) + d - 1) / d;
+    };
+    magic((unsigned long long)sz, &m_sz, &s_sz);
+    magic((unsigned long long)P, &m_P, &s_P);
+  }
 };
 
 struct LevelDev {
@@ -99,11 +125,34 @@ cudaError_t launch_build_fine(const LevelDev& L0, const int8_t* mask, unsigned l
 cudaError_t launch_mask_coarsen(const LevelDev& Lf, const int8_t* mask_if_fine, const LevelDev& Lc,
                                 cudaStream_t s);
 cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2, cudaStream_t s);
-// Compact list of the cells of colour c whose code has `bit`, in slot order;
-// block_scratch holds (slots/256 + 1) uint32.  count receives the length.
-cudaError_t launch_build_list(const Geom& g, const uint8_t* code, int colour, uint8_t bit, uint32_t* list,
-                              uint32_t* count, uint32_t* block_scratch, cudaStream_t s);
-long long list_scratch_words(const Geom& g);
+// One compact list to build (launch_build_lists builds a table of them in
+// three launches).  block0: the job's first block in the launch, nblocks
+// its blocks of kListThreads (256) slots; the scratch holds one word per
+// block of all jobs.
+struct ListJob {
+  Geom g;
+  const uint8_t* code;
+  uint32_t* list;
+  uint32_t* count;
+  unsigned block0, nblocks;
+  int colour;
+  uint8_t bit;
+};
+cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_blocks, uint32_t* scratch,
+                               cudaStream_t s);
+// Buffers of `words` 8-byte words to zero, and FP64 -> FP32 copies, many
+// per launch.
+struct ZeroJob {
+  void* ptr;
+  long long words;
+};
+struct F32Job {
+  const double* src;
+  float* dst;
+  long long n;
+};
+cudaError_t launch_zero_many(const ZeroJob* jobs, int njobs, cudaStream_t s);
+cudaError_t launch_to_f32_many(const F32Job* jobs, int njobs, cudaStream_t s);
 
 // ---- data movement and boundary data (kernels_build.cu) ----
 // natural (nx*ny*nz) <-> split; `scale` multiplies, `mask_bit` zeroes cells
@@ -118,6 +167,9 @@ cudaError_t launch_fold_faces(const LevelDev& L0, const FineExtra& F, const doub
 cudaError_t launch_fold_coarse(const LevelDev& L0, const FineExtra& F, const double* pc, int cnx, int cny,
                                int cnz, int ox, int oy, int oz, int* err_flag, cudaStream_t s);
 cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStream_t s);
+// h^2 rho into F.rhoh2 and the folded b into L0.rhs in one pass.
+cudaError_t launch_set_rhs(const LevelDev& L0, const FineExtra& F, const double* rho, double h2, bool bc_zero,
+                           cudaStream_t s);
 
 // ---- V-cycle kernels (kernels_cycle.cu) ----
 // order: 1 or 2; the level's active bit and diagonal follow from it.
@@ -147,12 +199,18 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
                           int coarse_sweeps, int prec, cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
+// Middle levels (more than 4096, at most kMidSlots cells per colour): the
+// V-cycle from level m (1 <= m < lb) through levels m .. lb-1, and the bottom
+// lb .. deepest, in one launch of one thread-block cluster.
+constexpr long long kMidSlots = 1 << 17;
+bool mid_level(const Geom& g);
+cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
+                       int coarse_sweeps, int prec, cudaStream_t s);
 // Mixed precision: FP64 residual of level 0 over every unknown -> FP32
 // right-hand side -r^ and zero FP32 correction, plus the norm (like
 // launch_residual_norm2); and Phi += e in FP64.
 cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max_partials, double* out,
                                    cudaStream_t s);
 cudaError_t launch_refine_update(const LevelDev& L0, cudaStream_t s);
-cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 
 }  // namespace gbmg
