@@ -23,6 +23,7 @@ struct PatchLevel {
   const double* diag[2];
   const uint8_t* code[2];
   const uint32_t* list[3][2];  // [order][colour]; level 0: list[2] only
+  double* rhsd[2];             // level 0: b / D (the scaled sweep's right-hand side)
   int patch;
   int level;
 };
@@ -72,6 +73,9 @@ cudaError_t launch_batch_gs(const Chunk* chunks, int nchunks, const PatchLevel* 
 cudaError_t launch_batch_norm(const Chunk* chunks, int nchunks, const PatchLevel* pls, const int* state, int mode,
                               double* partials, int threads, int grid, cudaStream_t s);
 // Residual and R1 into the coarse level of each chunk (coarse-list chunks).
+// Level-0 chunks: rhsd = b / D of their unknowns (every patch).
+cudaError_t launch_batch_scale(const Chunk* chunks, int nchunks, const PatchLevel* pls, int threads, int grid,
+                               cudaStream_t s);
 cudaError_t launch_batch_restrict(const Chunk* chunks, int nchunks, const PatchLevel* pls, const int* state,
                                   bool black_zero, int threads, int grid, cudaStream_t s);
 cudaError_t launch_batch_prolong(const Chunk* chunks, int nchunks, const PatchLevel* pls, const int* state,

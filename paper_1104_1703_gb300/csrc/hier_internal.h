@@ -60,6 +60,7 @@ struct mg_hierarchy {
   gbmg::F32Job* f32_jobs = nullptr;
   int n_f32_jobs = 0;
   bool bc_zero = true;  // the folded boundary terms are all 0
+  bool rhsd_valid = false;  // level 0's b / D matches its b
   double* partials = nullptr;
   int max_partials = 0;
   double* dscal = nullptr;             // device scalars

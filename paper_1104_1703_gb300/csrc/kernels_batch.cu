@@ -33,13 +33,15 @@ __device__ __forceinline__ const uint32_t* chunk_list(const PatchLevel& L, const
   return L.list[C.tag ? C.tag : 2][C.colour] + C.start;
 }
 
-// One colour of a Gauss-Seidel sweep over the entries of one chunk.
+// One colour of a Gauss-Seidel sweep over the entries of one chunk.  At
+// level 0 the right-hand side is b / D and the update one fused
+// multiply-add, as in the single-hierarchy FP64 sweep.
 template <int KIND>
 __device__ __forceinline__ void gs_chunk(const PatchLevel& L, const Chunk& C, const double* tab) {
   const int c = C.colour;
   double* __restrict__ self = L.phi[c];
   const double* __restrict__ other = L.phi[c ^ 1];
-  const double* __restrict__ rhs = L.rhs[c];
+  const double* __restrict__ rhs = KIND == 0 ? L.rhsd[c] : L.rhs[c];
   const double* __restrict__ invd = L.invd[c];
   const uint8_t* __restrict__ code = L.code[c];
   const uint32_t* __restrict__ list = chunk_list(L, C);
@@ -62,7 +64,27 @@ __device__ __forceinline__ void gs_chunk(const PatchLevel& L, const Chunk& C, co
   }
 #pragma unroll
   for (int u = 0; u < kPer; ++u)
-    if (ok[u]) self[at[u]] = (s[u] - b[u]) * d[u];
+    if (ok[u]) self[at[u]] = KIND == 0 ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+}
+
+__global__ void __launch_bounds__(kBatchMaxThreads)
+    batch_scale_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls) {
+  pdl_wait();
+  __shared__ double tab[16];
+  init_tab(tab);
+  for (int k = blockIdx.x; k < nchunks; k += gridDim.x) {
+    const Chunk C = chunks[k];
+    const PatchLevel& L = pls[C.pl];
+    const int c = C.colour;
+    const uint32_t* __restrict__ list = L.list[2][c] + C.start;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i >= C.n) continue;
+      const long long at = list[i] & kListAt;
+      L.rhsd[c][at] = L.rhs[c][at] * tab[__popc((unsigned)L.code[c][at] >> kGhostShift)];
+    }
+  }
 }
 
 template <bool FINE>
@@ -383,6 +405,14 @@ cudaError_t launch_batch_norm(const Chunk* chunks, int nchunks, const PatchLevel
   count_launch();
   if (mode == 1) launch_pdl(batch_norm_kernel<1>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state, partials);
   else launch_pdl(batch_norm_kernel<2>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scale(const Chunk* chunks, int nchunks, const PatchLevel* pls, int threads, int grid,
+                               cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  count_launch();
+  launch_pdl(batch_scale_kernel, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls);
   return cudaGetLastError();
 }
 

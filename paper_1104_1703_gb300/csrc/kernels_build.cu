@@ -24,19 +24,32 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ int colour_of(int i, int j, int k) { return (i + j + k) & 1; }
 
+// (i, j, k) of natural index idx; grids hold fewer than 2^32 cells (a colour
+// array, about half of them, is limited to 2^31 elements), so 32-bit
+// division suffices.
 __device__ __forceinline__ void natural_coords(long long idx, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(idx % nx);
-  long long t = idx / nx;
-  j = (int)(t % ny);
-  k = (int)(t / ny);
+  const unsigned u = (unsigned)idx;
+  const unsigned t = u / (unsigned)nx;
+  i = (int)(u - t * (unsigned)nx);
+  k = (int)(t / (unsigned)ny);
+  j = (int)(t - (unsigned)k * (unsigned)ny);
 }
 
 __device__ __forceinline__ long long pow8(int l) { return 1LL << (3 * l); }
 
-// Warp-aggregated increment of a 64-bit counter.
-__device__ __forceinline__ void count_add(unsigned long long* ctr, bool pred) {
-  unsigned m = __ballot_sync(0xffffffffu, pred);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
+// Adds every thread's count into *ctr with one atomic per block (all
+// threads of the block call it, after their loop).
+__device__ void block_count_add(unsigned long long* ctr, unsigned n) {
+  __shared__ unsigned warp_n[32];
+  for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+  if ((threadIdx.x & 31) == 0) warp_n[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned v = threadIdx.x < (blockDim.x >> 5) ? warp_n[threadIdx.x] : 0u;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+  }
+  __syncthreads();
 }
 
 // Level 0: code byte (active bits and ghost-face flags) from the int8 mask,
@@ -44,30 +57,26 @@ __device__ __forceinline__ void count_add(unsigned long long* ctr, bool pred) {
 __global__ void build_fine_kernel(LevelDev L, const int8_t* __restrict__ mask, unsigned long long* counts2) {
   const Geom g = L.g;
   const long long n = g.ncells();
-  const int lane = threadIdx.x & 31;
-  // the trip count is uniform across each warp (blockDim is a multiple of 32),
-  // so every lane reaches the __ballot_sync in count_add
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx - lane < n;
+  unsigned n_act = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    bool act = false;
-    if (idx < n) {
-      int i, j, k;
-      natural_coords(idx, g.nx, g.ny, i, j, k);
-      act = mask[idx] > 0;
-      uint8_t code = 0;
-      if (act) {
-        code = kActive2 | kActive1;
-        const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-        bool nb[6] = {i > 0 && mask[idx - 1] > 0, i + 1 < g.nx && mask[idx + 1] > 0,
-                      j > 0 && mask[idx - sy] > 0, j + 1 < g.ny && mask[idx + sy] > 0,
-                      k > 0 && mask[idx - sz] > 0, k + 1 < g.nz && mask[idx + sz] > 0};
-        for (int d = 0; d < 6; ++d)
-          if (!nb[d]) code |= (uint8_t)(1u << (kGhostShift + d));
-      }
-      L.code[colour_of(i, j, k)][g.at(i >> 1, j, k)] = code;
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const bool act = mask[idx] > 0;
+    n_act += act;
+    uint8_t code = 0;
+    if (act) {
+      code = kActive2 | kActive1;
+      const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+      bool nb[6] = {i > 0 && mask[idx - 1] > 0, i + 1 < g.nx && mask[idx + 1] > 0,
+                    j > 0 && mask[idx - sy] > 0, j + 1 < g.ny && mask[idx + sy] > 0,
+                    k > 0 && mask[idx - sz] > 0, k + 1 < g.nz && mask[idx + sz] > 0};
+      for (int d = 0; d < 6; ++d)
+        if (!nb[d]) code |= (uint8_t)(1u << (kGhostShift + d));
     }
-    count_add(&counts2[0], act);
+    L.code[colour_of(i, j, k)][g.at(i >> 1, j, k)] = code;
   }
+  block_count_add(&counts2[0], n_act);
 }
 
 // K1: S_c = sum of the 8 children (missing children of an odd dimension are
@@ -103,11 +112,11 @@ __global__ void coarse_coeffs_kernel(LevelDev L, unsigned long long* counts2) {
   const Geom g = L.g;
   const long long n = g.ncells();
   const long long p8 = pow8(L.level);
-  const int lane = threadIdx.x & 31;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx - lane < n;
+  unsigned n2 = 0, n1 = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     bool a2 = false, a1 = false;
-    if (idx < n) {
+    {
       int i, j, k;
       natural_coords(idx, g.nx, g.ny, i, j, k);
       const long long Si = L.S[idx];
@@ -131,9 +140,11 @@ __global__ void coarse_coeffs_kernel(LevelDev L, unsigned long long* counts2) {
       L.invd[c][at] = invd;
       L.diag[c][at] = diag;
     }
-    count_add(&counts2[0], a2);
-    count_add(&counts2[1], a1);
+    n2 += a2;
+    n1 += a1;
   }
+  block_count_add(&counts2[0], n2);
+  block_count_add(&counts2[1], n1);
 }
 
 __global__ void natural_to_split_kernel(Geom g, const double* __restrict__ nat, double* dst0, double* dst1,
@@ -297,10 +308,11 @@ constexpr int kListThreads = 256;
 __device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, uint8_t bit, long long e,
                                             long long n, long long& at, int& j, int& k) {
   if (e >= n) return false;
-  const int q = (int)(e % g.hx);
-  const long long t = e / g.hx;
-  j = (int)(t % g.ny);
-  k = (int)(t / g.ny);
+  const unsigned u = (unsigned)e;  // slots per colour < 2^31
+  const unsigned t = u / (unsigned)g.hx;
+  const int q = (int)(u - t * (unsigned)g.hx);
+  k = (int)(t / (unsigned)g.ny);
+  j = (int)(t - (unsigned)k * (unsigned)g.ny);
   at = g.at(q, j, k);
   return (code[at] & bit) != 0;
 }

@@ -265,6 +265,7 @@ mg_status build_tables(mg_batch* B) {
         d.invd[c] = L.invd[c];
         d.diag[c] = L.diag[c];
         d.code[c] = L.code[c];
+        d.rhsd[c] = L.rhsd[c];
         for (int o = 0; o < 3; ++o) d.list[o][c] = L.list[o][c];
       }
       d.patch = p;
@@ -399,9 +400,25 @@ mg_status capture(mg_batch* B) {
   return MG_OK;
 }
 
+// b / D of every patch's level 0 (the scaled sweeps), when some patch's b
+// changed since it was last computed.
+mg_status ensure_rhsd(mg_batch* B) {
+  bool stale = false;
+  for (const mg_hierarchy* H : B->P) stale = stale || !H->rhsd_valid;
+  if (!stale) return MG_OK;
+  for (int c = 0; c < 2; ++c) {
+    const Table& T = B->gs[0][c];
+    BCKS(lok(B, launch_batch_scale(B->d_chunks + T.off, T.n, B->d_pls, B->tune.threads, grid_of(B, T), B->stream),
+             "batched b / D"));
+  }
+  for (mg_hierarchy* H : B->P) H->rhsd_valid = true;
+  return MG_OK;
+}
+
 // Replays the batched cycle graph (capturing it first if needed) and waits
 // for the norms.
 mg_status run_cycle(mg_batch* B) {
+  BCKS(ensure_rhsd(B));
   if (!B->graph) BCKS(capture(B));
   BCK(B, cudaGraphLaunch(B->graph, B->stream));
   count_launch((unsigned long long)B->graph_nodes);

@@ -339,7 +339,16 @@ mg_status capture_cycle(mg_hierarchy* H, int order, GraphSlot& gs) {
 // One multigrid iteration of `order` followed by the end-of-cycle residual
 // norm, replayed from a CUDA graph when use_graphs is set.  If r_out is
 // non-null the stream is synchronised and ||r|| is returned.
+// b / D of level 0 for the FP64 sweeps, recomputed after b changed.
+mg_status ensure_rhsd(mg_hierarchy* H) {
+  if (H->rhsd_valid || !H->L[0].rhsd[0]) return MG_OK;
+  CKS(launch_ok(H, launch_scale_rhs(H->L[0], H->stream), "b / D"));
+  H->rhsd_valid = true;
+  return MG_OK;
+}
+
 mg_status run_cycle(mg_hierarchy* H, int order, double* r_out) {
+  CKS(ensure_rhsd(H));
   if (H->opt.precision == 1 && !H->prepared) CKS(emit_refine_residual(H));
   H->prepared = true;
   if (!H->opt.use_graphs) {
@@ -427,9 +436,11 @@ mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
 
 mg_status reset_fields(mg_hierarchy* H) {
   // Phi and b of every level, h^2 rho and the folded boundary terms: one launch
-  CKS(launch_ok(H, launch_zero_many(H->zero_jobs, H->n_zero_jobs, H->stream), "field reset"));
+  CKS(launch_ok(H, launch_zero_many(H->zero_jobs, H->n_zero_jobs - (H->bc_zero ? 2 : 0), H->stream),
+                "field reset"));
   H->bc_zero = true;
   H->r_zero_valid = false;
+  H->rhsd_valid = false;
   H->prepared = false;
   return MG_OK;
 }
@@ -608,8 +619,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   const size_t o_zjobs = A.reserve(sizeof(ZeroJob) * n_zero);
   const size_t o_fjobs = A.reserve(sizeof(F32Job) * (n_f32 > 0 ? n_f32 : 1));
   const Geom& g0 = H->L[0].g;
-  size_t o_rhoh2[2], o_bc[2], o_save[2];
+  size_t o_rhoh2[2], o_bc[2], o_save[2], o_rhsd[2] = {0, 0};
   for (int c = 0; c < 2; ++c) {
+    if (!mixed) o_rhsd[c] = A.reserve(sizeof(double) * g0.total);
     o_rhoh2[c] = A.reserve(sizeof(double) * g0.total);
     o_bc[c] = A.reserve(sizeof(double) * g0.total);
     o_save[c] = A.reserve(sizeof(double) * g0.total);
@@ -660,7 +672,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->zero_jobs = (ZeroJob*)(base + o_zjobs);
   H->f32_jobs = (F32Job*)(base + o_fjobs);
   H->list_blocks = lblocks;
+  for (int l = 0; l < H->nlev; ++l) H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
   for (int c = 0; c < 2; ++c) {
+    H->L[0].rhsd[c] = mixed ? nullptr : (double*)(base + o_rhsd[c]);
     H->F.rhoh2[c] = (double*)(base + o_rhoh2[c]);
     H->F.bc[c] = (double*)(base + o_bc[c]);
     H->F.save[c] = (double*)(base + o_save[c]);
@@ -696,10 +710,8 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
         zjobs.push_back({H->L[l].phi[c], H->L[l].g.total});
         zjobs.push_back({H->L[l].rhs[c], H->L[l].g.total});
       }
-    for (int c = 0; c < 2; ++c) {
-      zjobs.push_back({H->F.rhoh2[c], g0.total});
-      zjobs.push_back({H->F.bc[c], g0.total});
-    }
+    for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.rhoh2[c], g0.total});
+    for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.bc[c], g0.total});  // last: skipped when already 0
     std::vector<F32Job> fjobs;
     for (int l = 1; mixed && l < H->nlev; ++l)
       for (int c = 0; c < 2; ++c) {
@@ -771,6 +783,7 @@ mg_status mg_set_rhs(mg_hierarchy* H, const double* rho, mg_mem where) {
                 "rho layout and rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
+  H->rhsd_valid = false;
   H->prepared = false;
   return MG_OK;
 }
@@ -787,6 +800,7 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
     CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
     H->bc_zero = true;
     H->r_zero_valid = false;
+    H->rhsd_valid = false;
     H->prepared = false;
     return MG_OK;
   }
@@ -806,6 +820,7 @@ mg_status mg_set_dirichlet(mg_hierarchy* H, const double* bx, const double* by, 
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
   H->r_zero_valid = false;
+  H->rhsd_valid = false;
   H->prepared = false;
   return MG_OK;
 }
@@ -834,12 +849,14 @@ mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_
     H->bc_zero = true;
     CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
     H->r_zero_valid = false;
+    H->rhsd_valid = false;
   H->prepared = false;
     return fail(H, MG_ERR_INVALID_ARG,
                 "a boundary face lies outside the coarse cell centres; Dirichlet values reset to 0");
   }
   CKS(launch_ok(H, launch_combine_rhs(H->L[0], H->F, H->stream), "rhs fold"));
   H->r_zero_valid = false;
+  H->rhsd_valid = false;
   H->prepared = false;
   return MG_OK;
 }
@@ -1081,7 +1098,10 @@ mg_status mg_level_set(mg_hierarchy* H, int level, int field, const void* in, mg
                                           H->stream),
                 "layout"));
   if (where == MG_MEM_HOST) CK(H, cudaStreamSynchronize(H->stream));
-  if (level == 0 && field == MG_FIELD_RHS) H->r_zero_valid = false;
+  if (level == 0 && field == MG_FIELD_RHS) {
+    H->r_zero_valid = false;
+    H->rhsd_valid = false;
+  }
   H->prepared = false;
   return MG_OK;
 }
@@ -1091,6 +1111,7 @@ mg_status mg_level_smooth(mg_hierarchy* H, int level, int order, int sweeps) {
   H->prepared = false;
   if ((order != 1 && order != 2) || sweeps < 0) return fail(H, MG_ERR_INVALID_ARG, "bad order or sweeps");
   DeviceGuard guard(H->device);
+  if (level == 0) CKS(ensure_rhsd(H));
   CKS(smooth(H, level, order, sweeps));
   CK(H, cudaStreamSynchronize(H->stream));
   return MG_OK;

@@ -90,6 +90,7 @@ struct LevelDev {
   uint32_t* list[3][2];
   uint32_t* count;
   uint32_t hcount[6];  // host copy of count (sizes the launch grids)
+  double* rhsd[2];     // level 0 of the FP64 method: b / D (nullptr elsewhere)
   // FP32 copies for the inner cycles of the mixed-precision form (nullptr
   // when the hierarchy was created for FP64 only); level 0: phi32 is the
   // correction e, rhs32 is -r^ of the FP64 residual.
@@ -212,5 +213,7 @@ cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int o
 cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max_partials, double* out,
                                    cudaStream_t s);
 cudaError_t launch_refine_update(const LevelDev& L0, cudaStream_t s);
+// rhsd = b / D over level 0 (no-op when the level has no rhsd).
+cudaError_t launch_scale_rhs(const LevelDev& L0, cudaStream_t s);
 
 }  // namespace gbmg

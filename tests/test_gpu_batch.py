@@ -219,6 +219,7 @@ def test_autotune_restores_state_and_keeps_parity(dev, oracle):
 
 def test_batch_launch_count_and_errors(dev, oracle):
     Bt, _ = make_batch(dev, oracle, PATCHES[:3])
+    Bt.vcycle(want_rel=False)  # the first cycle also computes each patch's b / D
     c0 = B.mg_launch_count()
     Bt.vcycle(want_rel=False)
     nodes = Bt.launches_per_cycle()
