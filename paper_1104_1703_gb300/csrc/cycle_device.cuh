@@ -105,6 +105,39 @@ __device__ __forceinline__ void init_tab(T* tab) {
 // x offset of the non-shared x-neighbour of a colour-c cell in row (j, k)
 __device__ __forceinline__ int x_offset(int c, int j, int k) { return ((c ^ j ^ k) & 1) ? 1 : -1; }
 
+// P2 (Fig. 3) of a fine unknown at slot q of row (j, k), colour c: the
+// weighted sum 27 e0 + 9 e1 + 3 e2 + e3 over its 8 nearest coarse cells
+// (e0 the parent, e1 / e2 / e3 the corners one, two and three axis steps
+// away; divide by 64 for the correction).  The corners are addressed from
+// one coarse row base with 32-bit offsets: a step along y or z moves by the
+// pitch or the plane stride, and every axis step flips the colour.  `ld`
+// loads one coarse value.  Out-of-box corners read the zero halo.
+struct PlainLoad {
+  template <typename T>
+  __device__ __forceinline__ T operator()(const T* p) const {
+    return *p;
+  }
+};
+
+template <typename T, typename LD>
+__device__ __forceinline__ T p2_sum(const Geom& gc, const T* c0, const T* c1, int q, int j, int k, int c, LD ld) {
+  const int ix = 2 * q + ((c ^ j ^ k) & 1);
+  const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
+  const int Yn = j >> 1, Zn = k >> 1;
+  const int dY = (j & 1) ? gc.P : -gc.P;
+  const int dZ = (k & 1) ? (int)gc.sz : -(int)gc.sz;
+  const int row = (int)gc.off0 + Zn * (int)gc.sz + Yn * gc.P;
+  const int sn = row + (Xn >> 1), sf = row + (Xf >> 1);
+  const bool p = (Xn + Yn + Zn) & 1;
+  const T* cp = p ? c1 : c0;  // the parent's colour: corners an even number of steps away
+  const T* cq = p ? c0 : c1;  // an odd number of steps away
+  const T e0 = ld(cp + sn);
+  const T e1 = (ld(cq + sf) + ld(cq + sn + dY)) + ld(cq + sn + dZ);
+  const T e2 = (ld(cp + sn + dY + dZ) + ld(cp + sf + dZ)) + ld(cp + sf + dY);
+  const T e3 = ld(cq + sf + dY + dZ);
+  return fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+}
+
 constexpr int kNormThreads = 256;
 
 __device__ __forceinline__ void block_reduce_store(double acc, double* out) {
@@ -231,10 +264,6 @@ __device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, 
   __syncthreads();
 }
 
-template <typename T>
-__device__ T bottom_coarse(const BottomView<T>& C, int X, int Y, int Z) {
-  return C.phi[(X + Y + Z) & 1][C.g.at(X >> 1, Y, Z)];
-}
 
 // P2 of level f+1 into the unknowns of level f
 template <typename T>
@@ -246,15 +275,7 @@ __device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, u
       const int q = e % g.hx, t = e / g.hx, j = t % g.ny, k = t / g.ny;
       const long long at = g.at(q, j, k);
       if (!(F.code[c][at] & bit)) continue;
-      const int ix = 2 * q + ((c ^ j ^ k) & 1);
-      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
-      const T e0 = bottom_coarse(C, Xn, Yn, Zn);
-      const T e1 = (bottom_coarse(C, Xf, Yn, Zn) + bottom_coarse(C, Xn, Yf, Zn)) + bottom_coarse(C, Xn, Yn, Zf);
-      const T e2 = (bottom_coarse(C, Xn, Yf, Zf) + bottom_coarse(C, Xf, Yn, Zf)) + bottom_coarse(C, Xf, Yf, Zn);
-      const T e3 = bottom_coarse(C, Xf, Yf, Zf);
-      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      const T w = p2_sum(C.g, (const T*)C.phi[0], (const T*)C.phi[1], q, j, k, c, PlainLoad());
       F.phi[c][at] = fma(w, T(1) / T(64), F.phi[c][at]);
     }
   __syncthreads();

@@ -237,9 +237,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const int c = C.colour;
     const uint32_t* __restrict__ list = chunk_list(Lf, C);
     const Geom gf = Lf.g, gc = Lc.g;
-    const double* __restrict__ e0a = Lc.phi[0];
-    const double* __restrict__ e1a = Lc.phi[1];
-    auto coarse = [&](int X, int Y, int Z) { return ((X + Y + Z) & 1 ? e1a : e0a)[gc.at(X >> 1, Y, Z)]; };
     long long at[kPer];
     double w[kPer], old[kPer];
     bool ok[kPer];
@@ -251,15 +248,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
       at[u] = list[i] & kListAt;
       int q, j, kk;
       gf.slot_of(at[u], &q, &j, &kk);
-      const int ix = 2 * q + ((c ^ j ^ kk) & 1);
-      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-      const int Zn = kk >> 1, Zf = Zn + ((kk & 1) ? 1 : -1);
-      const double v0 = coarse(Xn, Yn, Zn);
-      const double v1 = (coarse(Xf, Yn, Zn) + coarse(Xn, Yf, Zn)) + coarse(Xn, Yn, Zf);
-      const double v2 = (coarse(Xn, Yf, Zf) + coarse(Xf, Yn, Zf)) + coarse(Xf, Yf, Zn);
-      const double v3 = coarse(Xf, Yf, Zf);
-      w[u] = fma(3.0, v2, fma(27.0, v0, 9.0 * v1)) + v3;
+      w[u] = p2_sum(gc, (const double*)Lc.phi[0], (const double*)Lc.phi[1], q, j, kk, c, PlainLoad());
       old[u] = Lf.phi[c][at[u]];
     }
 #pragma unroll

@@ -271,10 +271,6 @@ struct ProlongArgs {
   int skip_red;  // prolong the black unknowns only
 };
 
-template <typename T>
-__device__ __forceinline__ T coarse_at(const ProlongArgs<T>& a, int X, int Y, int Z) {
-  return a.cphi[(X + Y + Z) & 1][a.gc.at(X >> 1, Y, Z)];
-}
 
 // K6: Phi_f += P2(dPhi_c) on the unknowns of the fine level (Section 2,
 // recipe steps 6-7; Fig. 3).  Per axis a fine cell lies 1/4 of a coarse cell
@@ -310,15 +306,7 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
       at[u] = e & kListAt;
       int q, j, k;
       gf.slot_of(at[u], &q, &j, &k);
-      const int ix = 2 * q + ((c ^ j ^ k) & 1);
-      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
-      const T e0 = coarse_at(a, Xn, Yn, Zn);
-      const T e1 = (coarse_at(a, Xf, Yn, Zn) + coarse_at(a, Xn, Yf, Zn)) + coarse_at(a, Xn, Yn, Zf);
-      const T e2 = (coarse_at(a, Xn, Yf, Zf) + coarse_at(a, Xf, Yn, Zf)) + coarse_at(a, Xf, Yf, Zn);
-      const T e3 = coarse_at(a, Xf, Yf, Zf);
-      w[u] = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      w[u] = p2_sum(a.gc, a.cphi[0], a.cphi[1], q, j, k, c, PlainLoad());
       old[u] = a.phi[c][at[u]];
     }
 #pragma unroll
@@ -643,6 +631,13 @@ __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
 }
 
+struct CgLoad {
+  template <typename T>
+  __device__ __forceinline__ T operator()(const T* p) const {
+    return __ldcg(p);
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ T nbr_sum_cg(const T* o, long long at, int dx, int P, long long sz) {
   return ((ldcg(o + at) + ldcg(o + at + dx)) + (ldcg(o + at - P) + ldcg(o + at + P))) +
@@ -746,22 +741,13 @@ __device__ void mid_prolong(const MidLevel<T>& F, const MidLevel<T>& C, int firs
                             unsigned nthr) {
   const Geom& gf = F.g;
   const Geom& gc = C.g;
-  auto coarse = [&](int X, int Y, int Z) { return ldcg(C.phi[(X + Y + Z) & 1] + gc.at(X >> 1, Y, Z)); };
   for (int c = first_colour; c < 2; ++c) {
     const uint32_t n = F.count[c];
     for (uint32_t i = tid; i < n; i += nthr) {
       const long long at = F.list[c][i] & kListAt;
       int q, j, k;
       gf.slot_of(at, &q, &j, &k);
-      const int ix = 2 * q + ((c ^ j ^ k) & 1);
-      const int Xn = q, Xf = q + ((ix & 1) ? 1 : -1);
-      const int Yn = j >> 1, Yf = Yn + ((j & 1) ? 1 : -1);
-      const int Zn = k >> 1, Zf = Zn + ((k & 1) ? 1 : -1);
-      const T e0 = coarse(Xn, Yn, Zn);
-      const T e1 = (coarse(Xf, Yn, Zn) + coarse(Xn, Yf, Zn)) + coarse(Xn, Yn, Zf);
-      const T e2 = (coarse(Xn, Yf, Zf) + coarse(Xf, Yn, Zf)) + coarse(Xf, Yf, Zn);
-      const T e3 = coarse(Xf, Yf, Zf);
-      const T w = fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
+      const T w = p2_sum(gc, (const T*)C.phi[0], (const T*)C.phi[1], q, j, k, c, CgLoad());
       F.phi[c][at] = fma(w, T(1) / T(64), ldcg(F.phi[c] + at));
     }
   }
