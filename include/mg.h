@@ -318,8 +318,8 @@ typedef struct mg_batch mg_batch; /* opaque, library-owned */
  * smoother schedule n_pre / n_post, which is part of the method):
  *  threads          threads per block of the chunked kernels: 128, 256 or
  *                   512; every block takes chunks of 2 * threads unknowns
- *  persistent_ctas  0: one block per chunk; > 0: at most this many blocks,
- *                   each looping over chunks
+ *  persistent_ctas  0: one block per chunk; 1 .. 2^20: at most this many
+ *                   blocks, each looping over chunks
  *  bottom_slots     a patch's coarse levels with at most this many cells per
  *                   colour (64 .. 16384) run inside the one-CTA bottom cycle
  *  n_pre, n_post    Gauss-Seidel sweeps around the coarse correction (0..8)
@@ -369,7 +369,7 @@ mg_status mg_batch_get_tuning(const mg_batch* batch, mg_batch_tuning* out);
 mg_status mg_batch_set_tuning(mg_batch* batch, const mg_batch_tuning* tuning);
 
 /* Autotuner: times candidate launch parameters (threads 128/256/512, one
- * block per chunk or 4 / 8 resident blocks per SM, bottom_slots
+ * block per chunk or 4 / 8 resident blocks per multiprocessor, bottom_slots
  * 1024/2048/4096) on `reps` batched cycles each (CUDA events on the batch's
  * stream) and keeps the fastest.  With flags & MG_TUNE_SCHEDULE it then
  * times whole solves to tol from a zero initial guess for the smoother

@@ -38,6 +38,7 @@ struct mg_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
+  int sms = 152;  // multiprocessors of the device (resident-block candidates of the autotuner)
   std::string last_error = "no error";
 
   // per patch and order (index o - 1): bottom start level (0: level 0 is the
@@ -110,7 +111,7 @@ long long slots(const Geom& g) { return (long long)g.hx * g.ny * g.nz; }
 
 bool valid_tuning(const mg_batch_tuning& t) {
   return (t.threads == 128 || t.threads == 256 || t.threads == 512) && t.persistent_ctas >= 0 &&
-         t.persistent_ctas <= 152 * 64 && t.bottom_slots >= 64 && t.bottom_slots <= 16384 && t.n_pre >= 0 &&
+         t.persistent_ctas <= (1 << 20) && t.bottom_slots >= 64 && t.bottom_slots <= 16384 && t.n_pre >= 0 &&
          t.n_pre <= 8 && t.n_post >= 0 && t.n_post <= 8;
 }
 
@@ -640,6 +641,8 @@ mg_status mg_batch_create(int n_patches, const int8_t* const* masks, mg_mem wher
     delete B;
     return bfail(nullptr, MG_ERR_CUDA, "no CUDA device");
   }
+  if (cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess || B->sms < 1)
+    B->sms = 152;
   if (cuda_stream) {
     B->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -784,7 +787,7 @@ mg_status mg_batch_autotune(mg_batch* B, int reps, double tol, int max_cycles, i
   };
   if (st == MG_OK) {
     const int threads[3] = {128, 256, 512};
-    const int pers[3] = {0, 152 * 4, 152 * 8};
+    const int pers[3] = {0, B->sms * 4, B->sms * 8};
     const int bots[3] = {1024, 2048, 4096};
     for (int a = 0; a < 3 && st == MG_OK; ++a)
       for (int b = 0; b < 3 && st == MG_OK; ++b)
