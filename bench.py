@@ -579,6 +579,9 @@ def run_ours(args):
         "inner_cycles": args.inner_cycles,
         "inner_cycles_probe_ms": ic_ms or None,
         "time_to_tol_ms": ms(st_main), "cycles_per_solve": st_main["cycles"], "orders": st_main["orders"],
+        # active fine cells x multigrid V-cycles (the mixed form's FP32 cycles: steps x inner cycles) per second
+        "fine_cell_vcycles_per_s": world * n_active * st_main["cycles"] * (args.inner_cycles if args.precision == 1 else 1)
+                                   * args.steps / st_main["elapsed"],
         "roofline": roofline(st_main_k, n_active, args.precision, peaks),
         FORMS[1 - args.precision]: {"time_to_tol_ms": ms(st_other),
                                      "value": st_other["updates"] / st_other["elapsed"],

@@ -215,27 +215,14 @@ struct RestrictArgs {
   uint8_t bit;
   T* crhs[2];
   T* cphi[2];
+  const uint32_t* clist[2];   // restrict_list_kernel: second-order unknowns of the coarse level
+  const uint32_t* ccount[2];
 };
 
-// K5: residual and R1 in one pass (Section 2, recipe steps 2-5; Fig. 3).
-// Thread (I, J) of coarse plane K evaluates the scaled residual
-// r^ = sum_nbr Phi_j - D Phi_i - b of each of its active children and
-// writes b_c = -1/2 sum r^ and dPhi_c = 0.  The two x-children of coarse
-// cell I are both at fine slot I of the child rows (one per colour), so a
-// warp reads consecutive slots of every array it touches.  With BLACK_ZERO
-// the last fine operation was a complete red-black sweep, after which every
-// black cell satisfies its own equation: only red children carry a
-// residual.  Children outside the active set (of this order) count 0.
+// Children residuals of coarse cell (I, J, K) (the scaled residuals r^ of its active children, summed in a fixed order).
 template <int KIND, bool BLACK_ZERO, typename T>
-__global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArgs<T> a) {
-  pdl_wait();
-  __shared__ T tab[16];
-  if (KIND == 0) init_tab(tab);
-  const Geom gf = a.gf, gc = a.gc;
-  const int I = blockIdx.x * kBlockX + threadIdx.x;
-  const int J = blockIdx.y * kBlockY + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I >= gc.nx || J >= gc.ny) return;
+__device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, int I, int J, int K, const T* tab) {
+  const Geom& gf = a.gf;
   T sum = 0;
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk) {
@@ -255,10 +242,74 @@ __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArg
       }
     }
   }
+  return sum;
+}
+
+// K5: residual and R1 in one pass (Section 2, recipe steps 2-5; Fig. 3).
+// Thread (I, J) of coarse plane K evaluates the scaled residual
+// r^ = sum_nbr Phi_j - D Phi_i - b of each of its active children and
+// writes b_c = -1/2 sum r^ and dPhi_c = 0.  The two x-children of coarse
+// cell I are both at fine slot I of the child rows (one per colour), so a
+// warp reads consecutive slots of every array it touches.  With BLACK_ZERO
+// the last fine operation was a complete red-black sweep, after which every
+// black cell satisfies its own equation: only red children carry a
+// residual.  Children outside the active set (of this order) count 0.
+template <int KIND, bool BLACK_ZERO, typename T>
+__global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArgs<T> a) {
+  pdl_wait();
+  __shared__ T tab[16];
+  if (KIND == 0) init_tab(tab);
+  const Geom gc = a.gc;
+  const int I = blockIdx.x * kBlockX + threadIdx.x;
+  const int J = blockIdx.y * kBlockY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= gc.nx || J >= gc.ny) return;
+  const T sum = child_residual_sum<KIND, BLACK_ZERO>(a, I, J, K, tab);
   const int C = (I + J + K) & 1;
   const long long atc = gc.at(I >> 1, J, K);
   a.crhs[C][atc] = T(-0.5) * sum;
   a.cphi[C][atc] = T(0);
+}
+
+// K5 from level 0 in the V-cycle: the same residual + R1, over the
+// second-order unknowns of the coarse level only (a superset of the first-order ones, so a switch
+// of order leaves no stale correction).  Coarse cells outside that set are
+// never written in a cycle: their correction stays the 0 it was reset to,
+// and their right-hand side is never read.  Every lane holds a coarse
+// unknown, which spares the FP64 pipe the idle lanes of a box-wide grid.
+template <int KIND, bool BLACK_ZERO, typename T>
+__global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<T> a) {
+  pdl_wait();
+  constexpr int PER = 2;
+  __shared__ T tab[16];
+  if (KIND == 0) init_tab(tab);
+  const Geom gc = a.gc;
+  const uint32_t n0 = *a.ccount[0], n = n0 + *a.ccount[1];
+  const uint32_t stride = gridDim.x * kListBlock;
+  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+    long long atc[PER];
+    int cc[PER];
+    T sum[PER];
+    bool ok[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * stride;
+      ok[u] = i < n;
+      if (!ok[u]) continue;
+      const int C = i >= n0;
+      cc[u] = C;
+      atc[u] = (C ? a.clist[1][i - n0] : a.clist[0][i]) & kListAt;
+      int Q, J, K;
+      gc.slot_of(atc[u], &Q, &J, &K);
+      sum[u] = child_residual_sum<KIND, BLACK_ZERO>(a, 2 * Q + ((C ^ J ^ K) & 1), J, K, tab);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok[u]) continue;
+      a.crhs[cc[u]][atc[u]] = T(-0.5) * sum[u];
+      a.cphi[cc[u]][atc[u]] = T(0);
+    }
+  }
 }
 
 template <typename T>
@@ -557,7 +608,8 @@ cudaError_t smooth_small_t(const LevelDev& L, int order, int sweeps, cudaStream_
 }
 
 template <typename T>
-cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, cudaStream_t s) {
+cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, bool all_cells,
+                       cudaStream_t s) {
   const Fields<T> ff = fields(Lf, T()), fc = fields(Lc, T());
   RestrictArgs<T> a;
   a.gf = Lf.g;
@@ -571,6 +623,27 @@ cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool b
     a.cphi[c] = fc.phi[c];
   }
   a.bit = bit_of(Lf.level, order);
+  for (int c = 0; c < 2; ++c) {
+    a.clist[c] = Lc.list[2][c];
+    a.ccount[c] = Lc.count + 4 + c;
+  }
+  // over the coarse unknowns from level 0 (FP64: no idle lanes on the FP64
+  // pipe; FP32: fewer threads); from a coarse level the box-wide grid, whose
+  // extra warps hide more latency, is faster
+  if (!all_cells && Lf.level == 0) {
+    const int lgrid = exact_grid(Lc.hcount[4] + Lc.hcount[5], 2);
+    count_launch();
+#define GBMG_RESTRICT_LIST(K)                                                                            \
+  if (black_zero) launch_pdl(restrict_list_kernel<K, true, T>, dim3(lgrid), dim3(kListBlock), 0, s, a); \
+  else launch_pdl(restrict_list_kernel<K, false, T>, dim3(lgrid), dim3(kListBlock), 0, s, a);
+    switch (kind_of(Lf.level, order)) {
+      case 0: GBMG_RESTRICT_LIST(0) break;
+      case 1: GBMG_RESTRICT_LIST(1) break;
+      default: GBMG_RESTRICT_LIST(2) break;
+    }
+#undef GBMG_RESTRICT_LIST
+    return cudaGetLastError();
+  }
   const dim3 grid((Lc.g.nx + kBlockX - 1) / kBlockX, (Lc.g.ny + kBlockY - 1) / kBlockY, Lc.g.nz);
   const dim3 block(kBlockX, kBlockY);
   count_launch();
@@ -840,9 +913,9 @@ cudaError_t launch_smooth_small(const LevelDev& L, int order, int sweeps, int pr
 }
 
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, int prec,
-                            cudaStream_t s) {
-  return prec == kFP32 ? restrict_t<float>(Lf, Lc, order, black_zero, s)
-                       : restrict_t<double>(Lf, Lc, order, black_zero, s);
+                            cudaStream_t s, bool all_cells) {
+  return prec == kFP32 ? restrict_t<float>(Lf, Lc, order, black_zero, all_cells, s)
+                       : restrict_t<double>(Lf, Lc, order, black_zero, all_cells, s);
 }
 
 cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, bool black_only,

@@ -1122,7 +1122,8 @@ mg_status mg_level_restrict(mg_hierarchy* H, int level, int order) {
   H->prepared = false;
   if (level + 1 >= H->nlev || (order != 1 && order != 2)) return fail(H, MG_ERR_INVALID_ARG, "bad level/order");
   DeviceGuard guard(H->device);
-  CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, kFP64, H->stream), "restriction"));
+  CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, kFP64, H->stream, true),
+                "restriction"));
   CK(H, cudaStreamSynchronize(H->stream));
   return MG_OK;
 }

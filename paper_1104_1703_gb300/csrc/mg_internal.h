@@ -184,8 +184,11 @@ cudaError_t init_cycle_kernels();
 // Residual of level Lf restricted into the rhs of Lc as -R1(r) (scaled), dPhi_c = 0.
 // black_zero: the last operation on Lf was a complete red-black sweep, so
 // the black residual vanishes and only red cells are evaluated.
+// all_cells: write every coarse cell (the level API, which exposes the
+// whole coarse right-hand side); otherwise, from level 0, only the coarse
+// level's second-order unknowns (the V-cycle).
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, int order, bool black_zero, int prec,
-                            cudaStream_t s);
+                            cudaStream_t s, bool all_cells = false);
 // black_only: correct the black unknowns only (a red half-sweep follows,
 // which overwrites the red ones without reading them).
 cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, int prec, bool black_only,
