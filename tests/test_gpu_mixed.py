@@ -99,35 +99,40 @@ def test_mixed_solve_against_oracle(dev, oracle, name):
     assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
 
 
+@pytest.mark.parametrize("inner", [3, 6, 8])
 @pytest.mark.parametrize("name", ["ball64", "holes64", "blob48x32x40", "union64"])
-def test_mixed_three_inner_cycles(dev, oracle, name):
-    """Three FP32 V-cycles per refinement step: the same tolerance as checked
-    by the oracle's operator, the same order decision as the FP64 form (the
-    switch compares a step's ratio with eta^3), about a third of the steps,
-    and the update count of three V-cycles per step."""
+def test_mixed_several_inner_cycles(dev, oracle, name, inner):
+    """Several FP32 V-cycles per refinement step: the same tolerance as
+    checked by the oracle's operator, the same order decision as the FP64
+    form (the switch compares a step's ratio with eta^inner), about 1/inner
+    of the steps, and the update count of `inner` V-cycles per step."""
     w = CASES[name]
     tol = w.get("tol", 1e-8)
     faces = _faces(oracle, w)
-    H3 = _gpu(w, faces, precision=1, inner_cycles=3)
-    st, info = H3.solve(tol, 200)
+    Hm = _gpu(w, faces, precision=1, inner_cycles=inner)
+    st, info = Hm.solve(tol, 200)
     assert st == 0 and info["rel"] < tol
     R = oracle.Hierarchy(w["mask"], w["h"])
     R.set_rhs(w["rho"])
     if faces[0] is not None:
         R.set_faces(*faces)
-    R.set_phi(H3.get_solution())
+    R.set_phi(Hm.get_solution())
     assert R.residual_norm() / R.residual_norm_zero() < tol * (1 + 1e-6)
     H64 = _gpu(w, faces, precision=0)
     st64, info64 = H64.solve(tol, 200)
     assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
-    assert info64["cycles"] - 2 <= 3 * info["cycles"] <= info64["cycles"] + 5, (info["cycles"], info64["cycles"])
+    # the switch is tested once per step, so a switching solve can spend up
+    # to a step of second-order cycles (and restart) before it trips
+    slack = inner + 2 if not info["switched"] else 3 * inner
+    assert info64["cycles"] - 2 <= inner * info["cycles"] <= info64["cycles"] + slack, (info["cycles"],
+                                                                                      info64["cycles"])
     per = []
     for order in (1, 2):   # updates of one V-cycle in each order
         Ho = _gpu(w, faces, precision=1, order=order)
         _, io = Ho.solve(1e-300, 1)
         per.append(io["cell_updates"])
     u = info["cell_updates"]
-    assert u % 3 == 0 and info["cycles"] * min(per) <= u // 3 <= info["cycles"] * max(per)
+    assert u % inner == 0 and info["cycles"] * min(per) <= u // inner <= info["cycles"] * max(per)
 
 
 def test_mixed_inner_cycles_and_graphs_agree(dev, oracle):
