@@ -16,8 +16,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mg_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# MG_ORACLE_SRC / MG_ORACLE_BUILD let the mutation tests load a copy of the
+# source with one planted mistake; nothing else sets them.
+_SRC = os.environ.get("MG_ORACLE_SRC") or os.path.join(_HERE, "mg_oracle.c")
+_BUILD = os.environ.get("MG_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _LOCK = threading.Lock()
 _LIB = None

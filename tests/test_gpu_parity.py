@@ -243,6 +243,29 @@ def test_small_islands_switch_and_hold(dev):
     assert info["switched"] == 1  # solve 12 is back in second order and trips again
 
 
+def test_switch_restart_parity(dev, oracle):
+    """The switch trips on a residual above the initial one and the solve
+    restarts in first order from the initial guess (the oracle's reading of
+    Section 4): same status, cycles, decisions, history and solution.  The
+    guess carries the error mode that second-order cycles amplify on the
+    64^3 holes domain; the oracle makes it."""
+    from test_oracle_pins import diverging_guess
+    w = W.holes(64)
+    g = diverging_guess(oracle, w)
+    H, R = make_pair(w, dev)
+    H.set_solution(torch.from_numpy(g).to(dev))
+    R.set_phi(g)
+    st, info = H.solve(1e-10, 80)
+    st_o, info_o = R.solve(1e-10, 80)
+    assert st == st_o == 0 and info_o["switched"] == 1 and info_o["hist"][1] > info_o["hist"][0]
+    for key in ("cycles", "order", "switched"):
+        assert info[key] == info_o[key], key
+    ho, hg = info_o["hist"], info["hist"]
+    assert (np.abs(hg - ho) <= HIST_REL * ho + HIST_FLOOR * info_o["r_zero"]).all()
+    assert relerr(H.get_solution(), R.get_phi()) < TOL
+    assert H.hold == R.hold == 10
+
+
 def test_dirichlet_from_coarse(dev):
     w = CASES["blob48x32x40"]
     H, R = make_pair(w, dev)

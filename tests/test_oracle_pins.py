@@ -347,6 +347,54 @@ def test_small_islands_first_order_fix_and_switch(oracle):
     assert info["switched"] == 1  # back to second order first, which trips again
 
 
+def diverging_guess(oracle, w, scale=1e-3):
+    """Initial guess Phi* + e on `w`: Phi* is the converged discrete solution
+    (first order, 1e-13) and e the error mode that second-order V-cycles
+    amplify most, found by 30 normalised V-cycles on rho = 0 from a seeded
+    random field; e is scaled so that ||r(guess)|| = scale * ||r(0)||."""
+    act = w["mask"] > 0
+    H = oracle.Hierarchy(w["mask"], w["h"])
+    H.set_rhs(np.zeros_like(w["rho"]))
+    H.set_phi(W.random_field(w["mask"].shape, seed=11) * act)
+    for _ in range(30):
+        H.vcycle(order=2)
+        e = H.get_phi()
+        H.set_phi(e / np.abs(e).max())
+    e, r_e = H.get_phi(), H.residual_norm()
+    H.set_rhs(w["rho"])
+    H.set_phi(None)
+    st, _ = H.solve(1e-13, 200, order=1)
+    assert st == 0
+    return H.get_phi() + e * (scale * H.residual_norm_zero() / r_e)
+
+
+def test_switch_restart_from_initial_guess(oracle):
+    """Reading of Section 4 (the paper does not say what becomes of the
+    iterate when the switch trips): if the tripping residual is above the
+    initial one, the solve restarts in first order from the initial guess.
+    On the 64^3 holes domain the second-order V-cycle amplifies its dominant
+    error mode (ratio > 1), so a guess carrying that mode trips the switch
+    on the first cycle above r_init; every later residual must then be, to
+    rounding, the history of a first-order solve from the same guess."""
+    w = W.holes(64)
+    g = diverging_guess(oracle, w)
+    H = oracle.Hierarchy(w["mask"], w["h"])
+    H.set_rhs(w["rho"])
+    H.set_phi(g)
+    st0, i0 = H.solve(1e-10, 80, order=0)
+    h0 = i0["hist"]
+    assert st0 == 0 and i0["switched"] == 1 and i0["order"] == 1 and H.hold == 10
+    assert h0[1] > h0[0]
+    phi0 = H.get_phi()
+    H.hold = 0
+    H.set_phi(g)
+    st1, i1 = H.solve(1e-10, 80, order=1)
+    h1 = i1["hist"]
+    assert st1 == 0 and i1["cycles"] == i0["cycles"] - 1
+    np.testing.assert_allclose(h0[2:], h1[1:], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(phi0, H.get_phi(), rtol=0, atol=1e-12 * np.abs(phi0).max())
+
+
 def test_relative_residual_reference(oracle):
     """||r(Phi=0)|| with zero Dirichlet values on an all-active box is
     ||rho||: the reference of the relative residual."""
