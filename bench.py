@@ -16,10 +16,12 @@ through the public C ABI with host buffers: the mask and rho are copied from
 pinned host memory and the solution is read back every step.
 `ms_per_step` is the time to the tolerance per solve.
 
-Two more workloads are timed in the same run and reported beside the
-headline: 96 AMR patches solved as one batch (`batched_96_patches`, with the
-same patches solved one after the other for comparison) and the 512^3 cube
-with 20000 sub-cell holes (`holes_512`, both forms).
+More is timed in the same run and reported beside the headline:
+- 96 AMR patches solved as one batch (`batched_96_patches`), with the same
+  patches solved one after the other for comparison;
+- the 512^3 cube with 20000 sub-cell holes (`holes_512`, both forms);
+- the headline workload in the FP64 method with N_cycles = 1, 2 and 3
+  coarse iterations per level (`w_cycles`, Section 5.3).
 
 --impl reference times the FP64 CPU oracle on the host cores (bounded
 sample: hierarchy build + right-hand side + one multigrid iteration of the
@@ -66,6 +68,7 @@ def parse():
                         "measured before the timed run)")
     p.add_argument("--batch-only", action="store_true", help="time only the 96-patch batched workload")
     p.add_argument("--no-holes", action="store_true", help="skip the 512^3 complex-boundary workload")
+    p.add_argument("--no-wcycles", action="store_true", help="skip the W-cycle schedules (N_cycles = 2, 3)")
     p.add_argument("--profile", action="store_true",
                    help="profiling runs: time the headline form only (no second form, e2e or CPU leg)")
     p.add_argument("--precision", type=int, default=1, choices=[0, 1],
@@ -255,10 +258,10 @@ class Form:
     """One solver form (precision 0 = FP64 method, 1 = FP32 V-cycles inside
     FP64 iterative refinement) on the resident workload."""
 
-    def __init__(self, B, precision, mask_d, rho_d, h, stream, inner_cycles=1):
+    def __init__(self, B, precision, mask_d, rho_d, h, stream, inner_cycles=1, **extra):
         self.B = B
         self.precision = precision
-        opts = {"precision": precision}
+        opts = dict(extra, precision=precision)
         if precision == 1:
             opts["inner_cycles"] = inner_cycles
         self.H = B.Hierarchy(mask_d, h, stream=stream, **opts)
@@ -483,6 +486,22 @@ def run_holes(args, B, device, stream, world):
     return out
 
 
+def run_wcycles(args, B, device, stream, world, mask_d, rho_d, h):
+    """The multigrid schedules of Section 5.3 on the headline workload: the
+    plain FP64 method with N_cycles = 1 (V), 2 and 3 (W) coarse iterations
+    per level, each solved to 1e-8 from a zero guess (the headline step)."""
+    probe = argparse.Namespace(steps=min(args.steps, 3), warmup=args.warmup)
+    out = {"workload": "the headline workload, FP64 method, tol 1e-8", "unit": UNIT}
+    for nc in (1, 2, 3):
+        f = Form(B, 0, mask_d, rho_d, h, stream.cuda_stream, n_cycles=nc)
+        st = time_form(f, probe, mask_d, rho_d, stream, world, device)
+        out["n_cycles_%d" % nc] = {"time_to_tol_ms": 1e3 * st["elapsed"] / probe.steps,
+                                   "value": st["updates"] / st["elapsed"], "cycles_per_solve": st["cycles"],
+                                   "orders": st["orders"], "steps": probe.steps}
+        del f
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -558,6 +577,7 @@ def run_ours(args):
     h2d = w["mask"].nbytes + w["rho"].nbytes
     d2h = w["rho"].nbytes
     del main, other
+    wcyc = None if args.no_wcycles else run_wcycles(args, B, device, stream, world, mask_d, rho_d, w["h"])
     batched = None if args.no_batch else run_batched(args, B, device, stream, world)
     holes = None if args.no_holes else run_holes(args, B, device, stream, world)
 
@@ -596,6 +616,8 @@ def run_ours(args):
         line["batched_96_patches"] = batched
     if holes is not None:
         line["holes_512"] = holes
+    if wcyc is not None:
+        line["w_cycles"] = wcyc
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.size)
     print(json.dumps(line), flush=True)
