@@ -181,6 +181,7 @@ struct BottomArgs {
   int nlev;  // levels lb .. deepest
   uint8_t bit;
   int n_pre, n_post, coarse_sweeps;
+  int n_cycles;  // coarse iterations per level (Section 5.3): 1 V-cycle, 2 or more W-cycle
 };
 
 // a level's working arrays: staged in shared memory for the whole kernel
@@ -281,16 +282,19 @@ __device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, u
   __syncthreads();
 }
 
-// The Section 2 recipe (V-cycle, N_cycles = 1) on the small coarse levels
-// lb .. deepest, from the state the restriction into level lb left (its
-// right-hand side set, its correction zero), inside one CTA.  With SMEM the
-// correction and right-hand side of every level (halo included) live in
-// shared memory for the whole kernel, so the many barrier-separated steps
-// (2 * coarse_sweeps of them on the deepest level) read on-chip data that
-// the previous step wrote; the results go back to global memory at the end.
-// Each step is a block-strided loop over the level's slots closed by
-// __syncthreads.  This replaces about six launches per level and the
-// 2 * coarse_sweeps launches of the coarsest solve.
+// The Section 2 recipe with N_cycles coarse iterations per level (Section
+// 5.3: 1 is the V-cycle, 2 or more a W-cycle) on the small coarse levels
+// lb .. deepest, inside one CTA, from level lb's current state: its
+// right-hand side as the restriction left it and its correction (zero on
+// the first of a W-cycle's visits, the previous visit's result after that).
+// With SMEM the correction and right-hand side of every level (halo
+// included) live in shared memory for the whole kernel, so the many
+// barrier-separated steps (2 * coarse_sweeps of them on each visit of the
+// deepest level) read on-chip data that the previous step wrote; the results
+// go back to global memory at the end.  Each step is a block-strided loop
+// over the level's slots closed by __syncthreads.  This replaces about six
+// launches per level visit and the 2 * coarse_sweeps launches of each
+// coarsest solve.
 template <int KIND, typename T, bool SMEM>
 __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -311,27 +315,42 @@ __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
     }
   __syncthreads();
   if (SMEM) {
-    // stage: level lb's b and dPhi (= 0 after the restriction); the deeper
-    // levels are fully written before they are read, except their zero halo
+    // stage: level lb's b, and its dPhi (zero after the restriction, so
+    // read only for a W-cycle, whose later visits start from the previous
+    // one's result); the deeper levels are fully written before they are
+    // read, except their zero halo
+    const bool keep = a.n_cycles > 1;
     for (int i = 0; i < a.nlev; ++i) {
       const long long tot = a.L[i].g.total;
       for (int c = 0; c < 2; ++c)
         for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-          V[i].phi[c][e] = T(0);
+          V[i].phi[c][e] = i == 0 && keep ? a.L[0].phi[c][e] : T(0);
           V[i].rhs[c][e] = i == 0 ? a.L[0].rhs[c][e] : T(0);
         }
     }
     __syncthreads();
   }
+  // The recursion mg(i) = {smooth n_pre; restrict into i+1; N_cycles times
+  // mg(i+1); prolong; smooth n_post}, with mg(deepest) = coarse_sweeps
+  // sweeps, unrolled with one counter per level (the same in every thread):
+  // owe[i] is the number of visits of level i+1 that level i still owes.
   const int last = a.nlev - 1;
-  for (int i = 0; i < last; ++i) {
-    bottom_smooth<KIND>(V[i], a.n_pre);
-    bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
-  }
-  bottom_smooth<KIND>(V[last], a.coarse_sweeps);
-  for (int i = last - 1; i >= 0; --i) {
-    bottom_prolong(V[i], V[i + 1], a.bit, a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel
-    bottom_smooth<KIND>(V[i], a.n_post);
+  int owe[kBottomMaxLevels];
+  int i = 0;
+  for (;;) {
+    for (; i < last; ++i) {  // descend: a fresh visit of level i
+      bottom_smooth<KIND>(V[i], a.n_pre);
+      bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
+      owe[i] = a.n_cycles;
+    }
+    bottom_smooth<KIND>(V[last], a.coarse_sweeps);
+    for (i = last - 1; i >= 0; --i) {  // ascend until a level owes a visit
+      if (--owe[i] > 0) break;
+      bottom_prolong(V[i], V[i + 1], a.bit, a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel
+      bottom_smooth<KIND>(V[i], a.n_post);
+    }
+    if (i < 0) break;
+    ++i;  // visit level i+1 again, from its current correction
   }
   if (SMEM) {
     for (int i = 0; i < a.nlev; ++i) {

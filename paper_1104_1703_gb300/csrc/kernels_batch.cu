@@ -334,6 +334,7 @@ size_t batch_fill_bottom(void* host_args, int slot, const LevelDev* levels, int 
   a.n_pre = n_pre;
   a.n_post = n_post;
   a.coarse_sweeps = coarse_sweeps;
+  a.n_cycles = 1;  // a batch runs V-cycles
   if (deepest == 0) {
     B.kind = 0;
     B.smem = 0;

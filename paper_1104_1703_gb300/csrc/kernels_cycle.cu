@@ -929,7 +929,7 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, in
 // shared memory they need staged (0 when they do not fit: global memory).
 template <typename T>
 bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
-                 BottomArgs<T>& a, size_t* smem_bytes) {
+                 int n_cycles, BottomArgs<T>& a, size_t* smem_bytes) {
   a.nlev = deepest - lb + 1;
   if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return false;
   long long off = 0;
@@ -953,6 +953,7 @@ bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_p
   a.n_pre = n_pre;
   a.n_post = n_post;
   a.coarse_sweeps = coarse_sweeps;
+  a.n_cycles = n_cycles;
   const size_t bytes = (size_t)off * sizeof(T);
   *smem_bytes = bytes <= (size_t)kBottomSmemBytes ? bytes : 0;
   return true;
@@ -960,10 +961,11 @@ bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_p
 
 template <typename T>
 cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
-                     cudaStream_t s) {
+                     int n_cycles, cudaStream_t s) {
   BottomArgs<T> a;
   size_t bytes = 0;
-  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, a, &bytes)) return cudaErrorInvalidValue;
+  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, a, &bytes))
+    return cudaErrorInvalidValue;
   const bool sm = bytes > 0;
   count_launch();
   if (order == 1) {
@@ -1017,7 +1019,7 @@ cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order,
   a.n_pre = n_pre;
   a.n_post = n_post;
   size_t bytes = 0;
-  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, a.bottom, &bytes))
+  if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, 1, a.bottom, &bytes))
     return cudaErrorInvalidValue;
   count_launch();
   if (order == 1) return bytes ? launch_mid_cluster<2, T, true>(a, bytes, s) : launch_mid_cluster<2, T, false>(a, 0, s);
@@ -1025,9 +1027,9 @@ cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order,
 }
 
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
-                          int coarse_sweeps, int prec, cudaStream_t s) {
-  return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s)
-                       : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, s);
+                          int coarse_sweeps, int n_cycles, int prec, cudaStream_t s) {
+  return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, s)
+                       : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, s);
 }
 
 bool mid_level(const Geom& g) { return (long long)g.hx * g.ny * g.nz <= kMidSlots; }

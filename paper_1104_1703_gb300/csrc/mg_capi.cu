@@ -204,10 +204,11 @@ mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps, int prec = kFP64
 // FP64 or (inner cycles of the mixed form) FP32.
 mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool update_last = false) {
   const mg_options& o = H->opt;
-  // the small coarse levels run as one single-CTA launch (V-cycles only)
-  if (l >= 1 && o.n_cycles == 1 && small_level(H->L[l].g))
-    return launch_ok(H, launch_bottom(H->L, l, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps, prec,
-                                      H->cur),
+  // the small coarse levels run as one single-CTA launch, which carries
+  // the N_cycles recursion below level l itself
+  if (l >= 1 && small_level(H->L[l].g))
+    return launch_ok(H, launch_bottom(H->L, l, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps,
+                                      o.n_cycles, prec, H->cur),
                      "bottom cycle");
   // the middle levels and the bottom as one launch of a thread-block cluster
   if (l >= 1 && o.n_cycles == 1 && o.coarse_cluster && mid_level(H->L[l].g) && l < H->deepest[order]) {

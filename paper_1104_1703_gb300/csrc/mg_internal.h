@@ -198,10 +198,11 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, in
 // with_phi = false evaluates the residual of Phi = 0 (i.e. of the rhs alone).
 cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_phi, double* partials,
                                   int max_partials, double* out, cudaStream_t s);
-// The whole V-cycle (N_cycles = 1) on levels lb .. deepest in one CTA, for
-// small levels (every level lb..deepest satisfies small_level); lb >= 1.
+// One multigrid iteration with n_cycles coarse iterations per level (1: V,
+// 2 or more: W) on levels lb .. deepest in one CTA, for small levels (every
+// level lb..deepest satisfies small_level); lb >= 1.
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
-                          int coarse_sweeps, int prec, cudaStream_t s);
+                          int coarse_sweeps, int n_cycles, int prec, cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
 // Middle levels (more than 4096, at most kMidSlots cells per colour): the
 // V-cycle from level m (1 <= m < lb) through levels m .. lb-1, and the bottom
