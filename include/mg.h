@@ -18,7 +18,9 @@
  *    ((i+1/2)h, (j+1/2)h, (k+1/2)h).
  *  - `where` says whether a pointer is host memory (MG_MEM_HOST, any pageable
  *    or pinned host pointer) or device memory of the hierarchy's GPU
- *    (MG_MEM_DEVICE).  The caller owns every buffer it passes; the library
+ *    (MG_MEM_DEVICE).  An MG_MEM_DEVICE pointer that is not device (or
+ *    managed) memory of that GPU is refused with MG_ERR_INVALID_ARG before
+ *    any copy or launch.  The caller owns every buffer it passes; the library
  *    copies what it needs before returning and never keeps a caller pointer.
  *    All library memory is device memory owned by the hierarchy.
  *  - Work is issued on the hierarchy's CUDA stream.  Calls that return host

@@ -44,6 +44,18 @@ thread_local std::string t_last_error = "no error";
 namespace gbmg {
 // Sets the message mg_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg) { t_last_error = msg; }
+
+// A caller's MG_MEM_DEVICE pointer is read or written by kernels, so it must
+// be device (or managed) memory of `device`; a host pointer or another GPU's
+// buffer is refused before any copy or launch.  The query allocates nothing.
+bool is_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();  // leave no error behind for the next check
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
+}
 }  // namespace gbmg
 
 using namespace gbmg;
@@ -146,6 +158,8 @@ mg_status ensure_staging(mg_hierarchy* H, size_t bytes) {
 mg_status device_view(mg_hierarchy* H, const void* src, mg_mem where, size_t bytes, size_t offset,
                       const void** out) {
   if (where == MG_MEM_DEVICE) {
+    if (!is_device_ptr(src, H->device))
+      return fail(H, MG_ERR_INVALID_ARG, "an MG_MEM_DEVICE input is not device memory of the hierarchy's GPU");
     *out = src;
     return MG_OK;
   }
@@ -525,6 +539,12 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   mg_default_options(&o);
   if (opt) o = *opt;
   if (!valid_options(o)) return fail(nullptr, MG_ERR_INVALID_ARG, "invalid options");
+  if (where == MG_MEM_DEVICE) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, MG_ERR_CUDA, "no CUDA device");
+    if (!is_device_ptr(mask, dev))
+      return fail(nullptr, MG_ERR_INVALID_ARG, "the MG_MEM_DEVICE mask is not device memory of the current GPU");
+  }
 
   mg_hierarchy* H = new mg_hierarchy();
   H->opt = o;
@@ -753,6 +773,8 @@ mg_status mg_destroy_hierarchy(mg_hierarchy* H) {
 mg_status mg_update_mask(mg_hierarchy* H, const int8_t* mask, mg_mem where) {
   if (!H || !mask) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy or mask");
   DeviceGuard guard(H->device);
+  if (where == MG_MEM_DEVICE && !is_device_ptr(mask, H->device))
+    return fail(H, MG_ERR_INVALID_ARG, "the MG_MEM_DEVICE mask is not device memory of the hierarchy's GPU");
   const Geom& g0 = H->L[0].g;
   // validate on a copy first so that an empty mask leaves the old one in force
   CKS(ensure_staging(H, g0.ncells()));
@@ -1062,6 +1084,8 @@ mg_status mg_level_get(mg_hierarchy* H, int level, int field, void* out, mg_mem 
   if (where == MG_MEM_HOST) {
     CKS(ensure_staging(H, n * elem));
     dst = H->staging;
+  } else if (!is_device_ptr(out, H->device)) {
+    return fail(H, MG_ERR_INVALID_ARG, "the MG_MEM_DEVICE output is not device memory of the hierarchy's GPU");
   }
   if (field == MG_FIELD_PHI) {
     CKS(launch_ok(H, launch_split_to_natural(g, L.phi, (double*)dst, H->stream), "layout"));

@@ -22,7 +22,8 @@
 
 namespace gbmg {
 
-void set_thread_error(const char* msg);  // mg_capi.cu
+void set_thread_error(const char* msg);        // mg_capi.cu
+bool is_device_ptr(const void* p, int device);  // mg_capi.cu
 
 namespace {
 
@@ -127,6 +128,12 @@ extern "C" mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* 
     set_thread_error("mg_residual_norm_noalloc: no usable current CUDA device");
     return MG_ERR_CUDA;
   }
+  const void* const bufs[] = {mask, phi, rho, bx, by, bz, norm_out};
+  for (const void* p : bufs)
+    if (p && !is_device_ptr(p, dev)) {
+      set_thread_error("mg_residual_norm_noalloc: a buffer is not device memory of the current GPU");
+      return MG_ERR_INVALID_ARG;
+    }
   double* scratch;
   {
     std::lock_guard<std::mutex> lock(g_mutex);

@@ -350,6 +350,47 @@ def test_errors(dev):
     assert st == 0 and info["cycles"] == 0 and not H.get_solution().any()
 
 
+def test_device_pointers_are_checked(dev):
+    """A pointer passed as MG_MEM_DEVICE that is not device memory of the
+    hierarchy's GPU (pageable or pinned host memory here) is refused with
+    INVALID_ARG on the host, before any copy or launch touches it, by every
+    entry point that takes one; the hierarchy stays usable and unchanged."""
+    import ctypes
+    L = B.lib()
+    w = CASES["random17x12x10"]
+    H, R = make_pair(w, dev)
+    shape = w["mask"].shape
+    nz, ny, nx = shape
+    mask_h = np.ascontiguousarray(w["mask"])
+    pageable = np.zeros(shape, np.float64)
+    pinned = torch.zeros(shape, dtype=torch.float64).pin_memory()
+
+    def vp(a):
+        return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+
+    bad = B.MG_ERR_INVALID_ARG
+    for buf in (pageable, pinned):
+        assert L.mg_set_rhs(H.handle, vp(buf), B.MG_MEM_DEVICE) == bad
+        assert L.mg_set_solution(H.handle, vp(buf), B.MG_MEM_DEVICE) == bad
+        assert L.mg_get_solution(H.handle, vp(buf), B.MG_MEM_DEVICE) == bad
+    assert L.mg_update_mask(H.handle, vp(mask_h), B.MG_MEM_DEVICE) == bad
+    assert "not device memory" in B.mg_last_error(H.handle)
+    out = ctypes.c_void_p()
+    assert L.mg_create_hierarchy(vp(mask_h), B.MG_MEM_DEVICE, nx, ny, nz, w["h"], None, None,
+                                 ctypes.byref(out)) == bad and not out.value
+    mask_d = torch.from_numpy(mask_h).to(dev)
+    rho_d = torch.from_numpy(w["rho"]).to(dev)
+    norm_d = torch.zeros(1, dtype=torch.float64, device=dev)
+    assert L.mg_residual_norm_noalloc(vp(pageable), vp(rho_d), vp(rho_d), None, None, None, nx, ny, nz, w["h"],
+                                      vp(norm_d), None) == bad
+    assert L.mg_residual_norm_noalloc(vp(mask_d), vp(rho_d), vp(rho_d), None, None, None, nx, ny, nz, w["h"],
+                                      vp(pinned), None) == bad
+    st, info = H.solve(1e-9, 80)
+    st_o, info_o = R.solve(1e-9, 80)
+    assert st == st_o == 0 and info["cycles"] == info_o["cycles"]
+    assert relerr(H.get_solution(), R.get_phi()) < TOL
+
+
 def test_launch_counter_and_timing(dev):
     w = CASES["ball64"]
     H, _ = make_pair(w, dev)
