@@ -61,8 +61,9 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
 /* Parameters of the multigrid iteration.
  *  n_pre, n_post   Gauss-Seidel sweeps before and after the coarse correction
  *                  (Section 2, recipe steps 1 and 8; the paper uses 2 and 2).
- *  n_cycles        coarse iterations per level: 1 = V-cycle, 2 = W-cycle
- *                  (Section 5.3, N_cycles).
+ *  n_cycles        coarse iterations per level, 1..4: 1 = V-cycle, 2 =
+ *                  W-cycle, 3 and 4 the deeper recursions of Section 5.3
+ *                  (N_cycles).
  *  coarse_sweeps   red-black sweeps on the deepest level that has an active
  *                  cell (the paper does not specify the coarsest solve).
  *  order           0 = automatic switch (start in second order, Section 4),
@@ -125,7 +126,10 @@ void mg_default_options(mg_options* opt);
  * colours), the per-level active sets of both reconstruction orders and the
  * modified-Laplacian diagonals (Sections 3 and 4).
  *  mask         nx*ny*nz int8: > 0 active, <= 0 inactive (Omega = {m > 0}).
- *  nx, ny, nz   1..2048 each.
+ *  nx, ny, nz   1..2048 each, and (nz+2)*(ny+2)*pitch < 2^31 with pitch =
+ *               (nx+1)/2 + 1 rounded up to 8: each colour array of the padded
+ *               red/black layout must hold fewer than 2^31 elements (about
+ *               1600^3 cells for a cube); larger grids return INVALID_ARG.
  *  h            fine cell size, > 0.
  *  opt          NULL for mg_default_options.
  *  cuda_stream  a cudaStream_t of the current device, or NULL for a stream
