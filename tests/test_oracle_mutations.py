@@ -2,17 +2,20 @@
 
 Each entry below plants one mistake against the paper in a copy of
 `oracle/mg_oracle.c`: a dropped term, a wrong sign, index or weight, a
-skipped rule of Section 4.  The test builds that copy in a temporary folder,
-points the oracle loader at it (MG_ORACLE_SRC, MG_ORACLE_BUILD) and runs
-the pins listed for it in a child pytest, which must report failures.  The
-unmodified source runs the union of those pins as a control and must pass,
-so a failure is the planted mistake's doing.  Everything runs on the CPU.
+skipped rule of Section 4.  The test builds that copy in a temporary folder
+under the oracle's build folder, points the oracle loader at it
+(MG_ORACLE_SRC, MG_ORACLE_BUILD) and runs the pins listed for it in a child
+pytest, which must report failures.  The unmodified source runs the union
+of those pins as a control and must pass, so a failure is the planted
+mistake's doing.  Everything runs on the CPU.
 """
 import concurrent.futures as cf
 import os
 import re
+import shutil
 import subprocess
 import sys
+import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mg_oracle.c")
@@ -99,7 +102,7 @@ def _run_pins(tmp, name, src_text, pins, threads):
     return name, out.returncode, lines[-1] if lines else out.stderr[-500:]
 
 
-def test_pins_catch_planted_mistakes(tmp_path):
+def test_pins_catch_planted_mistakes():
     with open(SRC) as f:
         text = f.read()
     jobs = []
@@ -110,8 +113,15 @@ def test_pins_catch_planted_mistakes(tmp_path):
     jobs.append(("control", text, control_pins))
     workers = max(1, min(4, (os.cpu_count() or 2) // 2))
     threads = max(1, (os.cpu_count() or 2) // workers)
-    with cf.ThreadPoolExecutor(workers) as ex:
-        results = list(ex.map(lambda j: _run_pins(str(tmp_path), *j, threads), jobs))
+    # the mutants build in the oracle's own (git-ignored) build folder
+    base = os.path.join(ROOT, "oracle", "_build")
+    os.makedirs(base, exist_ok=True)
+    tmp = tempfile.mkdtemp(prefix="mutants_", dir=base)
+    try:
+        with cf.ThreadPoolExecutor(workers) as ex:
+            results = list(ex.map(lambda j: _run_pins(tmp, *j, threads), jobs))
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
     missed = []
     for name, rc, last in results:
         if name == "control":
