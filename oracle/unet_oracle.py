@@ -1,5 +1,5 @@
-"""Plain FP64 CPU definition of the learned initial guess's network: a 3D
-U-Net forward and backward pass and its Adam update.
+"""Plain FP64 CPU definition of the learned initial guess's network: its
+input channels, a 3D U-Net forward and backward pass, and its Adam update.
 
 TEST INFRASTRUCTURE ONLY.  The paper has no network; this module writes out
 the definition of the one the learned-guess form uses, so that its GPU
@@ -25,6 +25,54 @@ Algorithm 1) with bias correction.
 from __future__ import annotations
 
 import numpy as np
+
+
+# --------------------------------------------------------------------------
+# Inputs and target
+# --------------------------------------------------------------------------
+
+def features(mask, rho, faces, h):
+    """The network's three input channels for one fine level, and the scale s
+    that maps its output back to Phi (Phi = s * prediction).
+    - channel 0: h^2 rho n^2 / s on active cells (n = the largest dimension,
+      so h^2 n^2 is the squared box size: Phi ~ rho L^2), 0 elsewhere;
+    - channel 1: +1 on active cells, -1 elsewhere;
+    - channel 2: the mean Dirichlet value over the cell's ghost faces (faces
+      toward an inactive or out-of-box neighbour) / s, 0 where there are none;
+    - s: the root of the mean square of channel 0's numerator over active
+      cells plus the mean square of the ghost-face values, so that scaling rho
+      and the boundary values by c > 0 leaves the channels unchanged and
+      scales s by c (the problem is linear in both).
+    faces = (bx, by, bz) as in mg_set_dirichlet: bx [nz, ny, nx+1], by
+    [nz, ny+1, nx], bz [nz+1, ny, nx]; None for zero values."""
+    act = mask > 0
+    nz, ny, nx = act.shape
+    bx, by, bz = faces
+    bx = np.zeros((nz, ny, nx + 1)) if bx is None else bx
+    by = np.zeros((nz, ny + 1, nx)) if by is None else by
+    bz = np.zeros((nz + 1, ny, nx)) if bz is None else bz
+    pad = np.pad(act, 1, constant_values=False)
+    nbr_and_face = [(pad[1:-1, 1:-1, :-2], bx[:, :, :-1]), (pad[1:-1, 1:-1, 2:], bx[:, :, 1:]),
+                    (pad[1:-1, :-2, 1:-1], by[:, :-1, :]), (pad[1:-1, 2:, 1:-1], by[:, 1:, :]),
+                    (pad[:-2, 1:-1, 1:-1], bz[:-1, :, :]), (pad[2:, 1:-1, 1:-1], bz[1:, :, :])]
+    total = np.zeros(act.shape)
+    count = np.zeros(act.shape)
+    sq, nfaces = 0.0, 0
+    for nbr_active, face in nbr_and_face:
+        ghost = act & ~nbr_active
+        total += np.where(ghost, face, 0.0)
+        count += ghost
+        sq += float((face[ghost] ** 2).sum())
+        nfaces += int(ghost.sum())
+    n = max(act.shape)
+    src = np.where(act, h * h * n * n * rho, 0.0)
+    ms_src = float((src[act] ** 2).mean()) if act.any() else 0.0
+    ms_face = sq / nfaces if nfaces else 0.0
+    s = np.sqrt(ms_src + ms_face)
+    if not s > 0:
+        s = 1.0
+    bval = np.where(count > 0, total / np.maximum(count, 1), 0.0)
+    return np.stack([src / s, np.where(act, 1.0, -1.0), bval / s]), s
 
 
 # --------------------------------------------------------------------------

@@ -167,3 +167,38 @@ def test_planted_backward_mistakes_are_caught(old, new):
     mod = types.ModuleType("unet_mutant")
     exec(compile(src.replace(old, new), "unet_mutant", "exec"), mod.__dict__)
     assert not (_backward_agrees(mod, 2) and _backward_agrees(mod, 3))
+
+
+def test_features_scale_invariance_and_channels():
+    """Scaling rho and the boundary values by c leaves the channels unchanged
+    and scales s by c; inactive cells carry 0 in channels 0 and 2; the mask
+    channel is +-1."""
+    rng = np.random.default_rng(20)
+    shape = (5, 6, 7)
+    mask = (rng.random(shape) < 0.6).astype(np.int8)
+    rho = rng.normal(size=shape)
+    faces = (rng.normal(size=(5, 6, 8)), rng.normal(size=(5, 7, 7)), rng.normal(size=(6, 6, 7)))
+    x, s = U.features(mask, rho, faces, 0.1)
+    x3, s3 = U.features(mask, 3.0 * rho, tuple(3.0 * f for f in faces), 0.1)
+    np.testing.assert_allclose(x3, x, rtol=1e-13, atol=1e-15)
+    assert s3 == pytest.approx(3.0 * s, rel=1e-14)
+    act = mask > 0
+    assert not x[0][~act].any() and not x[2][~act].any()
+    assert set(np.unique(x[1])) <= {-1.0, 1.0} and (x[1] > 0).sum() == act.sum()
+
+
+def test_features_boundary_channel_single_cell():
+    """One active cell alone in the box: all six faces are ghost faces and the
+    boundary channel is their mean over s; with rho = 0, s is their root mean
+    square."""
+    mask = np.zeros((3, 3, 3), np.int8)
+    mask[1, 1, 1] = 1
+    bx, by, bz = np.zeros((3, 3, 4)), np.zeros((3, 4, 3)), np.zeros((4, 3, 3))
+    vals = [1.0, 2.0, -3.0, 4.0, 5.0, -6.0]
+    bx[1, 1, 1], bx[1, 1, 2] = vals[0], vals[1]
+    by[1, 1, 1], by[1, 2, 1] = vals[2], vals[3]
+    bz[1, 1, 1], bz[2, 1, 1] = vals[4], vals[5]
+    x, s = U.features(mask, np.zeros((3, 3, 3)), (bx, by, bz), 0.5)
+    assert s == pytest.approx(np.sqrt(np.mean(np.square(vals))), rel=1e-14)
+    assert x[2][1, 1, 1] == pytest.approx(np.mean(vals) / s, rel=1e-14)
+    assert np.count_nonzero(x[2]) == 1 and not x[0].any()
