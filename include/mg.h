@@ -276,11 +276,10 @@ mg_status mg_level_prolong(mg_hierarchy* hier, int level, int order);
  * that reserve the GPU's memory up front in their own pool, where a
  * cudaMalloc outside the pool can fail, and host code that must not block
  * on the allocator.  It computes ||r|| = ||Laplacian(Phi) - rho||_2 over the
- * active cells of a fine level (the operator of mg_residual_norm: Section 2
- * stencil with the Section 3 ghost faces at theta = 1/2 through the face
- * values) directly from the caller's device buffers, with no hierarchy and
- * no allocation of any kind (no cudaMalloc, cudaFree or allocating library
- * call).
+ * active cells of a fine level, with the same operator, boundary treatment
+ * and norm as mg_residual_norm, directly from the caller's device buffers,
+ * with no hierarchy and no allocation of any kind (no cudaMalloc, cudaFree
+ * or allocating library call).
  *  mask, phi, rho   device, nx*ny*nz, natural layout (as mg_create_hierarchy,
  *                   mg_set_solution and mg_set_rhs); values of phi and rho on
  *                   inactive cells are ignored.
@@ -292,12 +291,13 @@ mg_status mg_level_prolong(mg_hierarchy* hier, int level, int order);
  * The work is enqueued on the stream and the call returns without waiting;
  * norm_out is valid once the stream reaches that point.  Scratch: 4096
  * doubles (32 KB) of static device memory in the library, which every GPU
- * that loads the library holds until the process exits.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress), so
- * make the first call on each device before any stream capture.  All calls on
- * a device share the array: calls that can overlap on the GPU (different
- * streams, no ordering between them) race on it and must be serialised by
- * the caller.  Errors (mg_last_error(NULL)): INVALID_ARG, CUDA. */
+ * that loads the library holds until the process exits.  Each call looks up
+ * that array's device address (cudaGetSymbolAddress); the first call on a
+ * device also loads the library's kernels for it, so make the first call on
+ * each device before any stream capture.  All calls on a device share the
+ * array: calls that can overlap on the GPU (different streams, no ordering
+ * between them) race on it and must be serialised by the caller.
+ * Errors (mg_last_error(NULL)): INVALID_ARG, CUDA. */
 mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* phi, const double* rho, const double* bx,
                                    const double* by, const double* bz, int nx, int ny, int nz, double h,
                                    double* norm_out, void* cuda_stream);
@@ -409,6 +409,33 @@ unsigned long long mg_launch_count(void);
  * accumulators.  Errors: CUDA. */
 mg_status mg_timing_enable(mg_hierarchy* hier, int enable);
 mg_status mg_timing_read(mg_hierarchy* hier, long long* launches, double* total_ms);
+
+/* Measured FP64 fused multiply-add throughput of the current GPU, in FP64
+ * lane operations (one FMA per lane) per second: 8 independent FMA chains of
+ * `iters` steps (1 .. 2^20; 4096 is plenty) per thread, 8 blocks of 256
+ * threads per multiprocessor, the best of three timed launches (CUDA events
+ * on the legacy default stream, after one warm-up launch).  This is the
+ * ceiling of the FP64 form's Gauss-Seidel sweeps, which issue more FP64
+ * instructions per byte than the GPU's FP64 pipe retires at the HBM rate.
+ * Allocates nothing.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_probe_fp64_rate(int iters, double* lane_ops_per_s);
+
+/* ---------------------------------------------------------------------------
+ * Debugging aids
+ * ------------------------------------------------------------------------- */
+
+/* 1 if this library was built with MG_CHECKED: every kernel that reads a
+ * compact list of unknowns checks each entry against its level's slots,
+ * skips an entry outside them and records the kernel site; the entry point
+ * that ran the kernel then returns MG_ERR_INTERNAL and mg_last_error names
+ * the site.  0 for the normal build, which has no such checks. */
+int mg_checked_build(void);
+
+/* Test hook: the nth device or pinned-host allocation the library makes from
+ * now on (nth >= 1) fails as if the device were out of memory; nth = 0
+ * disarms the hook.  It fires once.  The failing call returns MG_ERR_OOM and
+ * releases everything it had allocated. */
+void mg_debug_fail_alloc(int nth);
 
 #ifdef __cplusplus
 }

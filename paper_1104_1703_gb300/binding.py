@@ -9,6 +9,7 @@ path: if the CUDA library cannot be built or loaded, ``lib()`` raises.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
@@ -80,6 +81,9 @@ SIGNATURES = {
     "mg_level_prolong": (_i, [_vp, _i, _i]),
     "mg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp]),
     "mg_launch_count": (ctypes.c_ulonglong, []),
+    "mg_probe_fp64_rate": (_i, [_i, _vp]),
+    "mg_checked_build": (_i, []),
+    "mg_debug_fail_alloc": (None, [_i]),
     "mg_timing_enable": (_i, [_vp, _i]),
     "mg_timing_read": (_i, [_vp, _vp, _vp]),
     "mg_batch_create": (_i, [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -99,11 +103,14 @@ _LOCK = threading.Lock()
 
 
 def lib() -> ctypes.CDLL:
-    """Loads libgbmg.so, building it first if it is missing or stale."""
+    """Loads libgbmg.so, building it first if it is missing or stale.  With
+    MG_CHECKED=1 in the environment it loads the bounds-checked build
+    libgbmg_checked.so instead (a debugging aid: every list-driven kernel
+    checks its entries, see mg_checked_build in mg.h)."""
     global _LIB
     with _LOCK:
         if _LIB is None:
-            path = _build.build()
+            path = _build.build(checked=os.environ.get("MG_CHECKED") == "1")
             L = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)
@@ -338,6 +345,20 @@ def mg_residual_norm_noalloc(mask, phi, rho, h, norm_out, bx=None, by=None, bz=N
 
 def mg_launch_count() -> int:
     return int(lib().mg_launch_count())
+
+
+def mg_probe_fp64_rate(iters=4096) -> float:
+    v = _d()
+    _check(lib().mg_probe_fp64_rate(int(iters), ctypes.byref(v)))
+    return v.value
+
+
+def mg_checked_build() -> bool:
+    return bool(lib().mg_checked_build())
+
+
+def mg_debug_fail_alloc(nth: int):
+    lib().mg_debug_fail_alloc(int(nth))
 
 
 def mg_timing_enable(h, enable=True):

@@ -63,17 +63,22 @@ __device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, l
 
 // FP32 <-> FP64 conversions with integer operations only (the conversion
 // instructions share the FP64 pipe, the binding resource of the mixed
-// form's FP64 kernels).  Narrowing truncates the mantissa (relative error
-// below 2^-23; it only feeds the FP32 correction problem) and flushes
-// magnitudes below 2^-126 to zero; widening is exact (FP32 subnormals, far
-// below any correction, flush to zero).  Infinities and NaNs are kept.
+// form's FP64 kernels).  Narrowing rounds toward zero (it truncates the
+// mantissa: relative error below 2^-23; it only feeds the FP32 correction
+// problem), so a finite value beyond the float range saturates at +-FLT_MAX
+// as round-toward-zero does, and magnitudes below 2^-126 flush to a zero of
+// the same sign.  Infinities stay infinite and every NaN stays a NaN.
+// Widening is exact (FP32 subnormals, far below any correction, flush to
+// zero).
 __device__ __forceinline__ float narrow_f64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned ex = (unsigned)(b >> 52) & 0x7ffu;
+  if (ex == 0x7ffu) return __uint_as_float(sign | ((b & 0xfffffffffffffull) ? 0x7fc00000u : 0x7f800000u));
+  const int e = (int)ex - 1023 + 127;
   const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
   if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
+  if (e >= 255) return __uint_as_float(sign | 0x7f7fffffu);
   return __uint_as_float(sign | ((unsigned)e << 23) | mant);
 }
 
@@ -85,6 +90,26 @@ __device__ __forceinline__ double widen_f32(float x) {
   if (e == 0) return __longlong_as_double((long long)sign);
   if (e == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | mant));
   return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | mant));
+}
+
+// Bounds check of a list entry's offset, compiled in only for the
+// MG_CHECKED build: an entry outside the level's slots records `site` in
+// the geometry's fault word (first failure wins) and is skipped, so the
+// host can report MG_ERR_INTERNAL instead of the kernel touching memory
+// outside its arrays.  Without MG_CHECKED it is always true and costs
+// nothing.
+__device__ __forceinline__ bool entry_ok(const Geom& g, long long at, unsigned site) {
+#ifdef MG_CHECKED
+  if (!g.slot_in_bounds(at)) {
+    if (g.fault) atomicCAS(g.fault, 0u, site);
+    return false;
+  }
+#else
+  (void)g;
+  (void)at;
+  (void)site;
+#endif
+  return true;
 }
 
 template <typename T>
@@ -213,6 +238,7 @@ __device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
           for (uint32_t i = threadIdx.x; i < L.n[c]; i += 32) {
             const uint32_t e = L.list[c][i];
             const long long at = e & kListAt;
+            if (!entry_ok(g, at, 1)) continue;
             L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
                            inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
           }
@@ -227,6 +253,7 @@ __device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
       for (uint32_t i = threadIdx.x; i < L.n[c]; i += blockDim.x) {
         const uint32_t e = L.list[c][i];
         const long long at = e & kListAt;
+        if (!entry_ok(g, at, 2)) continue;
         L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
                        inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
       }

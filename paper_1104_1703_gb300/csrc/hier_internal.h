@@ -79,3 +79,7 @@ struct mg_hierarchy {
   long long timed_launches = 0;   // accumulated from graph replays
   double timed_ms = 0;
 };
+
+namespace gbmg {
+mg_status check_faults(mg_hierarchy* H);  // mg_capi.cu
+}  // namespace gbmg

@@ -56,6 +56,7 @@ __device__ __forceinline__ void gs_chunk(const PatchLevel& L, const Chunk& C, co
     ok[u] = i < C.n;
     const uint32_t e = ok[u] ? list[i] : 0u;
     at[u] = e & kListAt;
+    ok[u] = ok[u] && entry_ok(L.g, at[u], 20);
     if (ok[u]) {
       s[u] = nbr_sum(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
       b[u] = rhs[at[u]];
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
       const int i = threadIdx.x + u * blockDim.x;
       if (i >= C.n) continue;
       const long long at = list[i] & kListAt;
+      if (!entry_ok(L.g, at, 21)) continue;
       L.rhsd[c][at] = L.rhs[c][at] * tab[__popc((unsigned)L.code[c][at] >> kGhostShift)];
     }
   }
@@ -127,6 +129,7 @@ __device__ __forceinline__ double res_chunk(const PatchLevel& L, const Chunk& C,
     ok[u] = i < C.n;
     const uint32_t e = ok[u] ? list[i] : 0u;
     at[u] = e & kListAt;
+    ok[u] = ok[u] && entry_ok(L.g, at[u], 22);
     if (ok[u]) {
       if (MODE == 2) {
         r[u] = -rhs[at[u]];
@@ -180,6 +183,7 @@ __device__ __forceinline__ void restrict_chunk(const PatchLevel& Lc, const Patch
     const int i = threadIdx.x + u * blockDim.x;
     if (i >= C.n) continue;
     const long long at = list[i] & kListAt;
+    if (!entry_ok(gc, at, 23)) continue;
     int Q, J, K;
     gc.slot_of(at, &Q, &J, &K);
     const int I = 2 * Q + ((c ^ J ^ K) & 1);
@@ -246,6 +250,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
       ok[u] = i < C.n;
       if (!ok[u]) continue;
       at[u] = list[i] & kListAt;
+      ok[u] = entry_ok(gf, at[u], 24);
+      if (!ok[u]) continue;
       int q, j, kk;
       gf.slot_of(at[u], &q, &j, &kk);
       w[u] = p2_sum(gc, (const double*)Lc.phi[0], (const double*)Lc.phi[1], q, j, kk, c, PlainLoad());
@@ -275,6 +281,7 @@ __device__ void level0_sweeps(const PatchLevel& L, const uint32_t* n, int sweeps
       for (uint32_t i = threadIdx.x; i < n[c]; i += blockDim.x) {
         const uint32_t e = list[i];
         const long long at = e & kListAt;
+        if (!entry_ok(L.g, at, 25)) continue;
         L.phi[c][at] = (nbr_sum(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, P, sz) - L.rhs[c][at]) *
                        inv_diag<0>(L.code[c][at], (const double*)nullptr, at, tab);
       }

@@ -435,7 +435,7 @@ __global__ void to_f32_many_kernel(const F32Job* __restrict__ jobs) {
 int grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  if (b > 152 * 32) b = 152 * 32;
+  if (b > 32LL * device_sms()) b = 32LL * device_sms();
   return (int)b;
 }
 
@@ -475,14 +475,14 @@ cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_bl
 cudaError_t launch_zero_many(const ZeroJob* jobs, int njobs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   count_launch();
-  zero_many_kernel<<<dim3(152 * 2, njobs), 256, 0, s>>>(jobs);
+  zero_many_kernel<<<dim3(device_sms() * 2, njobs), 256, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32_many(const F32Job* jobs, int njobs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   count_launch();
-  to_f32_many_kernel<<<dim3(152 * 2, njobs), 256, 0, s>>>(jobs);
+  to_f32_many_kernel<<<dim3(device_sms() * 2, njobs), 256, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
       ok[u] = i < n;
       const uint32_t e = ok[u] ? a.list[i] : 0u;
       at[u] = e & kListAt;
+      ok[u] = ok[u] && entry_ok(a.g, at[u], 3);
       if (ok[u]) {
         s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
         b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
       ok[u] = i < n;
       const uint32_t e = ok[u] ? a.list[i] : 0u;
       at[u] = e & kListAt;
+      ok[u] = ok[u] && entry_ok(g, at[u], 4);
       if (ok[u]) {
         const T s = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
         const uint8_t code = KIND == 0 ? a.code[at[u]] : 0;
@@ -299,6 +301,8 @@ __global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<
       const int C = i >= n0;
       cc[u] = C;
       atc[u] = (C ? a.clist[1][i - n0] : a.clist[0][i]) & kListAt;
+      ok[u] = entry_ok(gc, atc[u], 5);
+      if (!ok[u]) continue;
       int Q, J, K;
       gc.slot_of(atc[u], &Q, &J, &K);
       sum[u] = child_residual_sum<KIND, BLACK_ZERO>(a, 2 * Q + ((C ^ J ^ K) & 1), J, K, tab);
@@ -355,6 +359,8 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
       cc[u] = c;
       const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
       at[u] = e & kListAt;
+      ok[u] = entry_ok(gf, at[u], 6);
+      if (!ok[u]) continue;
       int q, j, k;
       gf.slot_of(at[u], &q, &j, &k);
       w[u] = p2_sum(a.gc, a.cphi[0], a.cphi[1], q, j, k, c, PlainLoad());
@@ -459,6 +465,8 @@ __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs 
       cc[u] = c;
       const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
       at[u] = e & kListAt;
+      ok[u] = entry_ok(g, at[u], 7);
+      if (!ok[u]) continue;
       const double s = nbr_sum(a.phi[1 - c], at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
       const double D = tab[8 + __popc((unsigned)a.code[c][at[u]] >> kGhostShift)];
       r[u] = fma(-D, a.phi[c][at[u]], s) - a.rhs[c][at[u]];
@@ -476,6 +484,7 @@ __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs 
 
 // Mixed precision, end of a refinement step: Phi += e in FP64.
 struct UpdateArgs {
+  Geom g;
   double* phi[2];
   const float* e32[2];
   const uint32_t* list[2];
@@ -488,6 +497,7 @@ __global__ void __launch_bounds__(kListBlock) refine_update_kernel(UpdateArgs a)
   for (uint32_t i = blockIdx.x * kListBlock + threadIdx.x; i < n; i += gridDim.x * kListBlock) {
     const int c = i >= n0;
     const long long at = (c ? a.list[1][i - n0] : a.list[0][i]) & kListAt;
+    if (!entry_ok(a.g, at, 8)) continue;
     a.phi[c][at] += widen_f32(a.e32[c][at]);
   }
 }
@@ -501,7 +511,8 @@ uint8_t bit_of(int level, int order) { return (level >= 1 && order == 1) ? kActi
 int list_grid(const Geom& g) {
   const long long n = (long long)g.hx * g.ny * g.nz;
   long long b = (n + kListBlock - 1) / kListBlock;
-  if (b > 152 * 16) b = 152 * 16;
+  const long long cap = 16LL * device_sms();
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -510,7 +521,7 @@ int list_grid(const Geom& g) {
 // entry per thread for short ones (so that short lists still spread over
 // all SMs); the kernels loop over their entries up to n either way
 int exact_grid(uint32_t n, int per) {
-  if ((long long)n < 4LL * 152 * kListBlock * per) per = 1;
+  if ((long long)n < 4LL * device_sms() * kListBlock * per) per = 1;
   const long long b = ((long long)n + (long long)kListBlock * per - 1) / ((long long)kListBlock * per);
   return b < 1 ? 1 : (int)b;
 }
@@ -762,6 +773,7 @@ __device__ void mid_smooth(const MidLevel<T>& L, int sweeps, unsigned tid, unsig
           ok[u] = i < n;
           const uint32_t e = ok[u] ? list[i] : 0u;
           at[u] = e & kListAt;
+          ok[u] = ok[u] && entry_ok(L.g, at[u], 9);
           if (ok[u])
             v[u] = (nbr_sum_cg(L.phi[c ^ 1], at[u], (e & kListPlusX) ? 1 : -1, P, sz) - ldcg(L.rhs[c] + at[u])) *
                    inv_diag<KIND>(0, L.invd[c], at[u], (const T*)nullptr);
@@ -818,6 +830,7 @@ __device__ void mid_prolong(const MidLevel<T>& F, const MidLevel<T>& C, int firs
     const uint32_t n = F.count[c];
     for (uint32_t i = tid; i < n; i += nthr) {
       const long long at = F.list[c][i] & kListAt;
+      if (!entry_ok(gf, at, 10)) continue;
       int q, j, k;
       gf.slot_of(at, &q, &j, &k);
       const T w = p2_sum(gc, (const T*)C.phi[0], (const T*)C.phi[1], q, j, k, c, CgLoad());
@@ -1043,7 +1056,7 @@ cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int o
 cudaError_t launch_scale_rhs(const LevelDev& L0, cudaStream_t s) {
   if (!L0.rhsd[0]) return cudaSuccess;
   long long b = (L0.g.total + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > 16LL * device_sms()) b = 16LL * device_sms();
   count_launch();
   launch_pdl(scale_rhs_kernel, dim3((unsigned)b), dim3(256), 0, s, L0.g.total, (const double*)L0.rhs[0],
              (const double*)L0.rhs[1], (const uint8_t*)L0.code[0], (const uint8_t*)L0.code[1], L0.rhsd[0], L0.rhsd[1]);
@@ -1051,7 +1064,7 @@ cudaError_t launch_scale_rhs(const LevelDev& L0, cudaStream_t s) {
 }
 
 int residual_norm_blocks(const Geom& g) {
-  const int plain = 152 * 8;
+  const int plain = device_sms() * 8;
   const int lists = 2 * list_grid(g);
   return lists > plain ? lists : plain;
 }
@@ -1068,7 +1081,7 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
     }
     a.bit = kActive2;
     a.partials = partials;
-    blocks = 152 * 8;
+    blocks = device_sms() * 8;
     count_launch();
     launch_pdl(rhsnorm_kernel, dim3(blocks), dim3(kNormThreads), 0, s, a);
   } else {
@@ -1111,6 +1124,7 @@ cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max
 
 cudaError_t launch_refine_update(const LevelDev& L0, cudaStream_t s) {
   UpdateArgs a;
+  a.g = L0.g;
   for (int c = 0; c < 2; ++c) {
     a.phi[c] = L0.phi[c];
     a.e32[c] = L0.phi32[c];

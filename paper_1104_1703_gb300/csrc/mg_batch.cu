@@ -38,7 +38,7 @@ struct mg_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
-  int sms = 152;  // multiprocessors of the device (resident-block candidates of the autotuner)
+  int sms = 0;  // multiprocessors of the device (resident-block candidates of the autotuner)
   std::string last_error = "no error";
 
   // per patch and order (index o - 1): bottom start level (0: level 0 is the
@@ -300,7 +300,7 @@ mg_status build_tables(mg_batch* B) {
   const size_t o_state = o_part + al(sizeof(double) * std::max(1, B->norm0.n));
   const size_t o_norm = o_state + al(sizeof(int) * n);
   const size_t total = o_norm + al(sizeof(double) * n);
-  BCK(B, cudaMalloc(&B->tables, total));
+  BCK(B, dev_malloc((void**)&B->tables, total));
   B->d_chunks = (Chunk*)(B->tables + o_ch);
   B->d_pls = (PatchLevel*)(B->tables + o_pl);
   B->d_bottom = B->tables + o_bot;
@@ -591,6 +591,9 @@ mg_status solve_impl(mg_batch* B, double tol, int max_cycles, mg_solve_info* inf
     if (st[p] == MG_ERR_DIVERGED) worst = MG_ERR_DIVERGED;
     else if (st[p] == MG_ERR_NOT_CONVERGED && worst == MG_OK) worst = MG_ERR_NOT_CONVERGED;
   }
+  for (int p = 0; p < n; ++p)
+    if (check_faults(B->P[p]) != MG_OK) return bfail(B, MG_ERR_INTERNAL, "patch " + std::to_string(p) + ": " +
+                                                                          B->P[p]->last_error);
   if (worst == MG_ERR_NOT_CONVERGED) return bfail(B, worst, "a patch did not reach the tolerance within max_cycles");
   if (worst == MG_ERR_DIVERGED) return bfail(B, worst, "a patch's residual norm became non-finite");
   return MG_OK;
@@ -641,8 +644,7 @@ mg_status mg_batch_create(int n_patches, const int8_t* const* masks, mg_mem wher
     delete B;
     return bfail(nullptr, MG_ERR_CUDA, "no CUDA device");
   }
-  if (cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess || B->sms < 1)
-    B->sms = 152;
+  B->sms = device_sms();
   if (cuda_stream) {
     B->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -657,8 +659,8 @@ mg_status mg_batch_create(int n_patches, const int8_t* const* masks, mg_mem wher
   cudaError_t e = init_batch_kernels();
   if (e != cudaSuccess) st = bcuda(B, e, "batched kernel attributes");
   if (st == MG_OK) {
-    e = cudaMallocHost(&B->h_state, sizeof(int) * n_patches);
-    if (e == cudaSuccess) e = cudaMallocHost(&B->h_norm2, sizeof(double) * n_patches);
+    e = host_malloc((void**)&B->h_state, sizeof(int) * n_patches);
+    if (e == cudaSuccess) e = host_malloc((void**)&B->h_norm2, sizeof(double) * n_patches);
     if (e != cudaSuccess) st = bcuda(B, e, "cudaMallocHost");
   }
   B->P.assign(n_patches, nullptr);
@@ -704,6 +706,9 @@ mg_status mg_batch_vcycle(mg_batch* B, double* rel_out) {
     B->P[p]->prepared = false;
   }
   BCKS(run_cycle(B));
+  for (int p = 0; p < B->n; ++p)
+    if (check_faults(B->P[p]) != MG_OK) return bfail(B, MG_ERR_INTERNAL, "patch " + std::to_string(p) + ": " +
+                                                                          B->P[p]->last_error);
   if (!rel_out) return MG_OK;
   bool finite = true;
   for (int p = 0; p < B->n; ++p) {
@@ -755,7 +760,7 @@ mg_status mg_batch_autotune(mg_batch* B, int reps, double tol, int max_cycles, i
     mg_hierarchy* H = B->P[p];
     holds[p] = H->hold;
     const size_t bytes = sizeof(double) * H->L[0].g.total;
-    cudaError_t e = cudaMalloc(&keep[p], 2 * bytes);
+    cudaError_t e = dev_malloc((void**)&keep[p], 2 * bytes);
     if (e != cudaSuccess) {
       keep[p] = nullptr;
       st = bcuda(B, e, "cudaMalloc(autotune backup)");

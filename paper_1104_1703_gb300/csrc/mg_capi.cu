@@ -35,7 +35,49 @@ unsigned long long capture_count_end() {
   return t_captured;
 }
 
+constexpr int kMaxDevices = 64;
+static std::atomic<int> g_sms[kMaxDevices];
+
+int device_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 152;
+  int n = g_sms[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    (void)cudaGetLastError();
+    n = 152;
+  }
+  g_sms[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// Allocation-failure test hook: when g_fail_countdown is positive, each
+// allocation decrements it and the one that brings it to 0 fails.
+static std::atomic<int> g_fail_countdown{0};
+
+static bool alloc_should_fail() {
+  int c = g_fail_countdown.load();
+  while (c > 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
 }  // namespace gbmg
+
+extern "C" void mg_debug_fail_alloc(int nth) { gbmg::g_fail_countdown.store(nth > 0 ? nth : 0); }
 
 namespace {
 thread_local std::string t_last_error = "no error";
@@ -147,7 +189,7 @@ mg_status ensure_staging(mg_hierarchy* H, size_t bytes) {
   if (H->staging) cudaFree(H->staging);
   H->staging = nullptr;
   H->staging_bytes = 0;
-  CK(H, cudaMalloc(&H->staging, bytes));
+  CK(H, dev_malloc(&H->staging, bytes));
   H->staging_bytes = bytes;
   return MG_OK;
 }
@@ -484,6 +526,31 @@ void destroy(mg_hierarchy* H) {
   delete H;
 }
 
+}  // namespace
+
+namespace gbmg {
+// Bounds-checked builds: MG_ERR_INTERNAL when a kernel of this hierarchy
+// recorded a list entry outside its level (the fault word is then cleared);
+// MG_OK otherwise and always in normal builds.
+mg_status check_faults(mg_hierarchy* H) {
+#ifdef MG_CHECKED
+  unsigned site = 0;
+  CK(H, cudaStreamSynchronize(H->stream));
+  CK(H, cudaMemcpy(&site, H->err_flag + 1, sizeof(site), cudaMemcpyDeviceToHost));
+  if (site) {
+    CK(H, cudaMemset(H->err_flag + 1, 0, sizeof(unsigned)));
+    return fail(H, MG_ERR_INTERNAL, "bounds check: a list entry outside its level at kernel site " +
+                                        std::to_string(site));
+  }
+#else
+  (void)H;
+#endif
+  return MG_OK;
+}
+}  // namespace gbmg
+
+namespace {
+
 mg_status check_level(mg_hierarchy* H, int level) {
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   if (level < 0 || level >= H->nlev) return fail(H, MG_ERR_INVALID_ARG, "level out of range");
@@ -526,6 +593,14 @@ const char* mg_status_string(mg_status st) {
 const char* mg_last_error(const mg_hierarchy* H) { return H ? H->last_error.c_str() : t_last_error.c_str(); }
 
 unsigned long long mg_launch_count(void) { return g_launches.load(); }
+
+int mg_checked_build(void) {
+#ifdef MG_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, int nz, double h,
                               const mg_options* opt, void* cuda_stream, mg_hierarchy** out) {
@@ -654,14 +729,14 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   size_t o_err = A.reserve(sizeof(int) * 4);
   size_t o_cnt = A.reserve(sizeof(unsigned long long) * 2 * kMaxLevels);
 
-  cudaError_t e = cudaMalloc(&H->arena, A.used);
+  cudaError_t e = dev_malloc((void**)&H->arena, A.used);
   if (e != cudaSuccess) {
     mg_status st = cuda_fail(nullptr, e, "cudaMalloc(arena)");
     H->arena = nullptr;
     destroy(H);
     return st;
   }
-  e = cudaMallocHost(&H->hscal, sizeof(double) * 8);
+  e = host_malloc((void**)&H->hscal, sizeof(double) * 8);
   if (e != cudaSuccess) {
     H->hscal = nullptr;
     mg_status st = cuda_fail(nullptr, e, "cudaMallocHost");
@@ -705,6 +780,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->partials = (double*)(base + o_part);
   H->dscal = (double*)(base + o_scal);
   H->err_flag = (int*)(base + o_err);
+  for (int l = 0; l < H->nlev; ++l) H->L[l].g.fault = (unsigned*)(H->err_flag + 1);
   H->counts = (unsigned long long*)(base + o_cnt);
 
   mg_status st = MG_OK;
@@ -910,17 +986,21 @@ mg_status mg_residual_norm(mg_hierarchy* H, double* norm_out, double* norm_zero_
   DeviceGuard guard(H->device);
   if (norm_out) CKS(residual(H, false, norm_out));
   if (norm_zero_out) CKS(residual_zero(H, norm_zero_out));
-  return MG_OK;
+  return check_faults(H);
 }
 
 mg_status mg_vcycle(mg_hierarchy* H, double* rel_out) {
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   DeviceGuard guard(H->device);
   const int order = kind_order(H);
-  if (!rel_out) return run_cycle(H, order, nullptr);
+  if (!rel_out) {
+    CKS(run_cycle(H, order, nullptr));
+    return check_faults(H);
+  }
   double r, r0;
   CKS(run_cycle(H, order, &r));
   CKS(residual_zero(H, &r0));
+  CKS(check_faults(H));
   *rel_out = r0 > 0 ? r / r0 : 0.0;
   if (!std::isfinite(r)) return fail(H, MG_ERR_DIVERGED, "non-finite residual");
   return MG_OK;
@@ -1032,6 +1112,7 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
     info->rel = rel;
     info->status = st;
   }
+  CKS(check_faults(H));
   if (st == MG_ERR_NOT_CONVERGED) return fail(H, st, "tolerance not reached within max_cycles");
   if (st == MG_ERR_DIVERGED) return fail(H, st, "non-finite residual norm");
   return st;
@@ -1139,7 +1220,7 @@ mg_status mg_level_smooth(mg_hierarchy* H, int level, int order, int sweeps) {
   if (level == 0) CKS(ensure_rhsd(H));
   CKS(smooth(H, level, order, sweeps));
   CK(H, cudaStreamSynchronize(H->stream));
-  return MG_OK;
+  return check_faults(H);
 }
 
 mg_status mg_level_restrict(mg_hierarchy* H, int level, int order) {
@@ -1150,7 +1231,7 @@ mg_status mg_level_restrict(mg_hierarchy* H, int level, int order) {
   CKS(launch_ok(H, launch_restrict(H->L[level], H->L[level + 1], order, false, kFP64, H->stream, true),
                 "restriction"));
   CK(H, cudaStreamSynchronize(H->stream));
-  return MG_OK;
+  return check_faults(H);
 }
 
 mg_status mg_level_prolong(mg_hierarchy* H, int level, int order) {
@@ -1161,7 +1242,7 @@ mg_status mg_level_prolong(mg_hierarchy* H, int level, int order) {
   CKS(launch_ok(H, launch_prolong(H->L[level + 1], H->L[level], order, kFP64, false, H->stream),
                 "prolongation"));
   CK(H, cudaStreamSynchronize(H->stream));
-  return MG_OK;
+  return check_faults(H);
 }
 
 mg_status mg_timing_enable(mg_hierarchy* H, int enable) {

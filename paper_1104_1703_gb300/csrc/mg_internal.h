@@ -48,6 +48,10 @@ struct Geom {
   // exact when 2^(31+l) <= m d <= 2^(31+l) + 2^l).  Set by set_divisors().
   unsigned long long m_sz, m_P;
   int s_sz, s_P;
+  // Bounds-checked builds (MG_CHECKED) record the first list entry that
+  // fails slot_in_bounds here (device memory of the owning hierarchy, the
+  // site of the failing kernel); unused otherwise.
+  unsigned* fault;
   __host__ __device__ long long at(int q, int j, int k) const { return off0 + k * sz + (long long)j * P + q; }
   __host__ __device__ long long ncells() const { return (long long)nx * ny * nz; }
   __host__ __device__ int div_sz(unsigned n) const { return (int)(((unsigned long long)n * m_sz) >> s_sz); }
@@ -59,6 +63,15 @@ struct Geom {
     const unsigned rem = rel - (unsigned)(*k) * (unsigned)sz;
     *j = div_P(rem);
     *q = (int)(rem - (unsigned)(*j) * (unsigned)P);
+  }
+  // True iff `at` is the offset of a slot (q, j, k) with q < hx, j < ny and
+  // k < nz.  Then every stencil neighbour at +-1, +-P and +-sz lies inside
+  // the colour array [0, total), since off0 = sz + P and sz = (ny + 2) P.
+  __host__ __device__ bool slot_in_bounds(long long at) const {
+    if (at < off0 || at >= off0 + (long long)nz * sz) return false;
+    int q, j, k;
+    slot_of(at, &q, &j, &k);
+    return q < hx && j < ny && k < nz;
   }
   void set_divisors() {
     auto magic = [](unsigned long long d, unsigned long long* m, int* s) {
@@ -111,6 +124,16 @@ struct FineExtra {
   double* save[2];   // backup of the initial guess for the order switch
   const int8_t* mask;  // natural-layout mask (device)
 };
+
+// Multiprocessors of the current device, read once per device and cached;
+// launch grids are sized in multiples of it.
+int device_sms();
+
+// Every device and pinned-host allocation of the library goes through these
+// two.  mg_debug_fail_alloc (mg.h) can make the n-th of them fail as if the
+// device were out of memory, to show that each caller cleans up.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t host_malloc(void** p, size_t bytes);
 
 // Launch-count instrumentation.  Between capture_count_begin and
 // capture_count_end (one thread, around a stream capture) launches are

@@ -11,11 +11,14 @@
 //
 // The per-block partial sums, the only scratch this computation needs, live
 // in a file-scope __device__ array of fixed size.  Host code cannot use the
-// array's name as a device address, so its address is obtained with
-// cudaGetSymbolAddress once per device (on the first call made with that
-// device current) and passed to the kernels.
+// array's name as a device address, so every call obtains the address with
+// cudaGetSymbolAddress, with the caller's device current, and passes it to
+// the kernels.  The lookup allocates nothing and is cheap; doing it on every
+// call rather than caching it keeps the address right when the module is
+// loaded again at another address (after cudaDeviceReset, or in another
+// context of the same device).  The first call on a device also loads this
+// file's kernels and the array.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/mg.h"
 #include "mg_internal.h"
@@ -29,15 +32,11 @@ namespace {
 
 constexpr int kNoAllocMaxPartials = 4096;  // 32 KB of scratch on each device
 constexpr int kNoAllocThreads = 256;
-constexpr int kNoAllocMaxDevices = 64;
 
 // One partial sum of squares per block of the first kernel.  Every call on a
 // device uses the same array; each slot the second kernel reads is written by
 // the first kernel of the same call, so nothing needs clearing between calls.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
-
-std::mutex g_mutex;
-double* g_scratch[kNoAllocMaxDevices] = {};
 
 // Residual r^ = h^2 (Laplacian Phi - rho) of every active cell, with the
 // modified stencil of Section 3 at level 0 (ghost at theta = 1/2 through the
@@ -124,7 +123,7 @@ extern "C" mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* 
     return MG_ERR_INVALID_ARG;
   }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     set_thread_error("mg_residual_norm_noalloc: no usable current CUDA device");
     return MG_ERR_CUDA;
   }
@@ -134,19 +133,12 @@ extern "C" mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* 
       set_thread_error("mg_residual_norm_noalloc: a buffer is not device memory of the current GPU");
       return MG_ERR_INVALID_ARG;
     }
-  double* scratch;
-  {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-      if (e != cudaSuccess || !p) {
-        set_thread_error("mg_residual_norm_noalloc: cudaGetSymbolAddress of the scratch array failed");
-        return MG_ERR_CUDA;
-      }
-      g_scratch[dev] = (double*)p;
-    }
-    scratch = g_scratch[dev];
+  void* scratch = nullptr;
+  cudaError_t es = cudaGetSymbolAddress(&scratch, g_noalloc_partials);
+  if (es != cudaSuccess || !scratch) {
+    (void)cudaGetLastError();
+    set_thread_error("mg_residual_norm_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    return MG_ERR_CUDA;
   }
   const long long n = (long long)nx * ny * nz;
   long long blocks = (n + kNoAllocThreads - 1) / kNoAllocThreads;
@@ -155,8 +147,8 @@ extern "C" mg_status mg_residual_norm_noalloc(const int8_t* mask, const double* 
   const double h2 = h * h;
   count_launch(2);
   noalloc_resnorm_kernel<<<(int)blocks, kNoAllocThreads, 0, s>>>(mask, phi, rho, bx, by, bz, nx, ny, nz, h2,
-                                                                  scratch);
-  noalloc_finalize_kernel<<<1, kNoAllocThreads, 0, s>>>(scratch, (int)blocks, h2, norm_out);
+                                                                  (double*)scratch);
+  noalloc_finalize_kernel<<<1, kNoAllocThreads, 0, s>>>((const double*)scratch, (int)blocks, h2, norm_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_thread_error(cudaGetErrorString(e));

@@ -1,7 +1,8 @@
 // Host check of Geom::div_sz / div_P / slot_of (mg_internal.h) against
 // integer division, for the geometries of many grid shapes: every element
 // offset of small grids, and offsets next to every multiple of the divisor
-// plus random offsets for large ones.  Prints "ok" or the first mismatch.
+// plus random offsets for large ones; and of Geom::slot_in_bounds, the
+// checked build's bounds test.  Prints "ok" or the first mismatch.
 #include <cstdio>
 #include <cstdlib>
 
@@ -64,6 +65,33 @@ int main() {
           std::printf("mismatch %dx%dx%d n=%u\n", d[0], d[1], d[2], n);
           return 1;
         }
+      }
+    }
+  }
+  // the bounds test of the checked build (Geom::slot_in_bounds): true
+  // exactly on the slots (q < hx, j < ny, k < nz) of every offset of small
+  // grids, and every stencil neighbour of a slot lies inside the array
+  const int small[][3] = {{1, 1, 1}, {2, 3, 5}, {3, 1, 2}, {17, 12, 10}, {9, 16, 7}, {48, 32, 40}};
+  for (const auto& d : small) {
+    const Geom g = geom(d[0], d[1], d[2]);
+    for (long long at = -g.sz; at < g.total + g.sz; ++at) {
+      bool slot = false;
+      if (at >= g.off0) {
+        const long long rel = at - g.off0;
+        const long long k = rel / g.sz, r = rel % g.sz, j = r / g.P, q = r % g.P;
+        slot = k < g.nz && j < g.ny && q < g.hx;
+      }
+      if (g.slot_in_bounds(at) != slot) {
+        std::printf("bounds mismatch %dx%dx%d at=%lld\n", d[0], d[1], d[2], at);
+        return 1;
+      }
+      if (slot) {
+        const long long nb[6] = {at - 1, at + 1, at - g.P, at + g.P, at - g.sz, at + g.sz};
+        for (long long b : nb)
+          if (b < 0 || b >= g.total) {
+            std::printf("neighbour outside %dx%dx%d at=%lld\n", d[0], d[1], d[2], at);
+            return 1;
+          }
       }
     }
   }
