@@ -86,7 +86,7 @@ def test_checked_build_runs_the_small_parity_cases_clean():
     probe = subprocess.run([sys.executable, "-c",
                             "from paper_1104_1703_gb300 import binding as B; print(B.mg_checked_build())"],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    assert probe.returncode == 0 and probe.stdout.strip().endswith("1"), probe.stdout + probe.stderr
+    assert probe.returncode == 0 and probe.stdout.strip().endswith("True"), probe.stdout + probe.stderr
     sel = ("tests/test_gpu_parity.py::test_tiny_grids tests/test_gpu_parity.py::test_vcycle_parity "
            "tests/test_gpu_parity.py::test_solve_parity tests/test_gpu_parity.py::test_smoother_parity "
            "tests/test_gpu_parity.py::test_prolongation_parity tests/test_gpu_parity.py::test_restriction_parity "
