@@ -88,7 +88,12 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  one thread-block cluster; 0 = one launch per step (faster
  *                  on GB300: the replayed graph pipelines the launches, while
  *                  each cluster-wide step costs a barrier).  The results are
- *                  the same. */
+ *                  the same.
+ *  smoother_pass   mixed form: 1 = run each pair of FP32 Gauss-Seidel sweeps
+ *                  of the fine level (N_pre = N_post = 2 is one pair) as one
+ *                  temporal-blocked pass over the level (a z-wavefront over
+ *                  tiles staged in shared memory); 0 = four list half-sweeps.
+ *                  The results are bit-identical. */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -97,6 +102,7 @@ typedef struct {
   int precision;
   int inner_cycles;
   int coarse_cluster;
+  int smoother_pass;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -117,7 +123,7 @@ typedef struct {
 
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
- * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0. */
+ * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):
@@ -210,6 +216,11 @@ mg_status mg_solve(mg_hierarchy* hier, double tol, int max_cycles, mg_solve_info
 /* ||r|| and ||r(Phi = 0)|| (unscaled L2 over the active fine cells) for the
  * current solution.  Either output may be NULL.  Errors: CUDA. */
 mg_status mg_residual_norm(mg_hierarchy* hier, double* norm_out, double* norm_zero_out);
+
+/* 1 if the fine level's FP32 sweeps run as temporal-blocked passes (mixed
+ * form with option smoother_pass on a fine level larger than the one-CTA
+ * smoother's, and the GPU accepted the pass's tensor maps), else 0. */
+mg_status mg_get_smoother_pass(const mg_hierarchy* hier, int* active);
 
 /* Order-switch state: solves left in forced first order. */
 mg_status mg_get_hold(const mg_hierarchy* hier, int* hold);
@@ -436,6 +447,13 @@ int mg_checked_build(void);
  * disarms the hook.  It fires once.  The failing call returns MG_ERR_OOM and
  * releases everything it had allocated. */
 void mg_debug_fail_alloc(int nth);
+
+/* Test hook of the temporal-blocked smoothing pass (option smoother_pass):
+ * while on, passes captured or launched from now on make their first CTA
+ * wait on a barrier that nothing completes, so that its bounded wait runs out
+ * (after about a second); the CTA then leaves the pass and the solve or
+ * V-cycle returns MG_ERR_INTERNAL.  0 turns it off. */
+void mg_debug_stall_pass(int on);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ _d = ctypes.c_double
 class MGOptions(ctypes.Structure):
     _fields_ = [("n_pre", _i), ("n_post", _i), ("n_cycles", _i), ("coarse_sweeps", _i), ("hold_solves", _i),
                 ("eta", _d), ("order", _i), ("use_graphs", _i), ("precision", _i), ("inner_cycles", _i),
-                ("coarse_cluster", _i)]
+                ("coarse_cluster", _i), ("smoother_pass", _i)]
 
 
 class MGSolveInfo(ctypes.Structure):
@@ -68,6 +68,7 @@ SIGNATURES = {
     "mg_vcycle": (_i, [_vp, _vp]),
     "mg_solve": (_i, [_vp, _d, _i, _vp]),
     "mg_residual_norm": (_i, [_vp, _vp, _vp]),
+    "mg_get_smoother_pass": (_i, [_vp, _vp]),
     "mg_get_hold": (_i, [_vp, _vp]),
     "mg_set_hold": (_i, [_vp, _i]),
     "mg_last_error": (ctypes.c_char_p, [_vp]),
@@ -84,6 +85,7 @@ SIGNATURES = {
     "mg_probe_fp64_rate": (_i, [_i, _vp]),
     "mg_checked_build": (_i, []),
     "mg_debug_fail_alloc": (None, [_i]),
+    "mg_debug_stall_pass": (None, [_i]),
     "mg_timing_enable": (_i, [_vp, _i]),
     "mg_timing_read": (_i, [_vp, _vp, _vp]),
     "mg_batch_create": (_i, [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -272,6 +274,12 @@ def mg_residual_norm(h):
     return r.value, r0.value
 
 
+def mg_get_smoother_pass(h) -> bool:
+    v = _i()
+    _check(lib().mg_get_smoother_pass(h, ctypes.byref(v)), h)
+    return bool(v.value)
+
+
 def mg_get_hold(h):
     v = _i()
     _check(lib().mg_get_hold(h, ctypes.byref(v)), h)
@@ -361,6 +369,10 @@ def mg_debug_fail_alloc(nth: int):
     lib().mg_debug_fail_alloc(int(nth))
 
 
+def mg_debug_stall_pass(on: bool):
+    lib().mg_debug_stall_pass(1 if on else 0)
+
+
 def mg_timing_enable(h, enable=True):
     _check(lib().mg_timing_enable(h, 1 if enable else 0), h)
 
@@ -426,6 +438,10 @@ class Hierarchy:
 
     def residual_norm(self):
         return mg_residual_norm(self.handle)
+
+    @property
+    def smoother_pass(self):
+        return mg_get_smoother_pass(self.handle)
 
     @property
     def hold(self):

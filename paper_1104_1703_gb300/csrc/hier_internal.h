@@ -8,6 +8,7 @@
 
 #include "../../include/mg.h"
 #include "mg_internal.h"
+#include "pass_internal.h"
 
 namespace gbmg {
 
@@ -78,6 +79,13 @@ struct mg_hierarchy {
   size_t events_used = 0;
   long long timed_launches = 0;   // accumulated from graph replays
   double timed_ms = 0;
+  // temporal-blocked FP32 smoothing pass of level 0 (mixed form)
+  bool pass_on = false;
+  float* phi32_alt[2] = {nullptr, nullptr};  // the second FP32 correction buffer of level 0
+  uint32_t* pass_flags = nullptr;
+  uint32_t* pass_tiles = nullptr;
+  uint32_t* pass_ntiles = nullptr;
+  gbmg::PassMaps pass_maps;
 };
 
 namespace gbmg {

@@ -79,6 +79,12 @@ cudaError_t host_malloc(void** p, size_t bytes) {
 
 extern "C" void mg_debug_fail_alloc(int nth) { gbmg::g_fail_countdown.store(nth > 0 ? nth : 0); }
 
+namespace gbmg {
+static std::atomic<int> g_stall_pass{0};
+}  // namespace gbmg
+
+extern "C" void mg_debug_stall_pass(int on) { gbmg::g_stall_pass.store(on ? 1 : 0); }
+
 namespace {
 thread_local std::string t_last_error = "no error";
 }  // namespace
@@ -153,7 +159,7 @@ Geom make_geom(int nx, int ny, int nz) {
   g.ny = ny;
   g.nz = nz;
   g.hx = (nx + 1) / 2;
-  g.P = ((g.hx + 1) + 7) & ~7;
+  g.P = ((g.hx + 1) + 15) & ~15;  // multiple of 16: the byte arrays' rows are valid TMA strides
   g.sz = (long long)(ny + 2) * g.P;
   g.off0 = g.sz + g.P;
   g.total = (long long)(nz + 2) * g.sz;
@@ -165,7 +171,7 @@ bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
-         (o.coarse_cluster == 0 || o.coarse_cluster == 1);
+         (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1);
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -222,25 +228,78 @@ mg_status launch_ok(mg_hierarchy* H, cudaError_t e, const char* what) {
   return MG_OK;
 }
 
-mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec, bool update = false) {
-  if (l == 0 && H->timing) {
-    std::vector<TimedPair>& pool = H->cap_events ? *H->cap_events : H->events;
-    size_t& used = H->cap_events ? H->cap_events_used : H->events_used;
-    if (used == pool.size()) {
-      TimedPair p;
-      CK(H, cudaEventCreate(&p.a));
-      CK(H, cudaEventCreate(&p.b));
-      pool.push_back(p);
-    }
-    TimedPair& p = pool[used++];
-    // inside a capture the records become event nodes of the graph
-    const unsigned flags = H->cap_events ? cudaEventRecordExternal : cudaEventRecordDefault;
-    CK(H, cudaEventRecordWithFlags(p.a, H->cur, flags));
-    CKS(launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, update, H->cur), "half-sweep"));
-    CK(H, cudaEventRecordWithFlags(p.b, H->cur, flags));
-    return MG_OK;
+// Brackets the launches that `emit` enqueues with a timing event pair when
+// kernel timing is on (inside a capture the records become graph nodes).
+template <typename F>
+mg_status timed(mg_hierarchy* H, F emit) {
+  if (!H->timing) return emit();
+  std::vector<TimedPair>& pool = H->cap_events ? *H->cap_events : H->events;
+  size_t& used = H->cap_events ? H->cap_events_used : H->events_used;
+  if (used == pool.size()) {
+    TimedPair p;
+    CK(H, cudaEventCreate(&p.a));
+    CK(H, cudaEventCreate(&p.b));
+    pool.push_back(p);
   }
-  return launch_ok(H, launch_half_sweep(H->L[l], order, colour, prec, update, H->cur), "half-sweep");
+  TimedPair& p = pool[used++];
+  const unsigned flags = H->cap_events ? cudaEventRecordExternal : cudaEventRecordDefault;
+  CK(H, cudaEventRecordWithFlags(p.a, H->cur, flags));
+  CKS(emit());
+  CK(H, cudaEventRecordWithFlags(p.b, H->cur, flags));
+  return MG_OK;
+}
+
+mg_status half_sweep_on(mg_hierarchy* H, const LevelDev& L, int order, int colour, int prec, bool update) {
+  auto emit = [&]() { return launch_ok(H, launch_half_sweep(L, order, colour, prec, update, H->cur), "half-sweep"); };
+  if (L.level == 0) return timed(H, emit);
+  return emit();
+}
+
+mg_status half_sweep(mg_hierarchy* H, int l, int order, int colour, int prec, bool update = false) {
+  return half_sweep_on(H, H->L[l], order, colour, prec, update);
+}
+
+// Level 0 of the mixed form with the temporal-blocked pass: the FP32
+// correction alternates between two buffers (cur = 0: L[0].phi32, 1: the
+// second buffer); view0 is level 0 with the current one.
+LevelDev view0(const mg_hierarchy* H, int cur) {
+  LevelDev v = H->L[0];
+  if (cur)
+    for (int c = 0; c < 2; ++c) v.phi32[c] = H->phi32_alt[c];
+  return v;
+}
+
+// One temporal-blocked pass (two red-black sweeps) from buffer cur into the
+// other; with update, also Phi += e of the result.
+mg_status smooth_pass(mg_hierarchy* H, int& cur, bool update) {
+  PassArgs a;
+  a.g = H->L[0].g;
+  for (int c = 0; c < 2; ++c) {
+    a.out[c] = cur ? H->L[0].phi32[c] : H->phi32_alt[c];
+    a.phi64[c] = update ? H->L[0].phi[c] : nullptr;
+  }
+  a.tiles = H->pass_tiles;
+  a.ntiles = H->pass_ntiles;
+  a.err = H->err_flag + 2;
+  a.debug_stall = g_stall_pass.load();
+  const int input = cur;
+  CKS(timed(H, [&]() {
+    return launch_ok(H, launch_smooth_pass(H->pass_maps, input, a, H->cur), "temporal-blocked smoothing pass");
+  }));
+  cur ^= 1;
+  return MG_OK;
+}
+
+// `sweeps` FP32 sweeps of level 0: pairs as passes, a remaining single sweep
+// as two list half-sweeps on the current buffer.
+mg_status smooth0_fp32(mg_hierarchy* H, int order, int sweeps, int& cur, bool update_last) {
+  for (; sweeps >= 2; sweeps -= 2) CKS(smooth_pass(H, cur, update_last && sweeps == 2));
+  if (sweeps == 1) {
+    const LevelDev v = view0(H, cur);
+    CKS(half_sweep_on(H, v, order, 0, kFP32, update_last));
+    CKS(half_sweep_on(H, v, order, 1, kFP32, update_last));
+  }
+  return MG_OK;
 }
 
 // update_last: the last sweep also applies Phi += e (level 0, mixed form)
@@ -276,6 +335,22 @@ mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool up
                        "middle levels");
   }
   if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec, update_last);
+  if (l == 0 && prec == kFP32 && H->pass_on) {
+    // the same steps with the fine level's sweeps as temporal-blocked passes
+    int cur = 0;
+    CKS(smooth0_fp32(H, order, o.n_pre, cur, false));  // step 1
+    CKS(launch_ok(H, launch_restrict(view0(H, cur), H->L[1], order, o.n_pre >= 1, prec, H->cur),
+                  "residual/restriction"));  // steps 2-5
+    for (int c = 0; c < o.n_cycles; ++c) CKS(iteration(H, 1, order, prec));  // step 5
+    CKS(launch_ok(H, launch_prolong(H->L[1], view0(H, cur), order, prec, o.n_post >= 1, H->cur),
+                  "prolongation"));  // steps 6-7
+    CKS(smooth0_fp32(H, order, o.n_post, cur, update_last));  // step 8
+    if (cur)
+      for (int c = 0; c < 2; ++c)
+        CK(H, cudaMemcpyAsync(H->L[0].phi32[c], H->phi32_alt[c], sizeof(float) * H->L[0].g.total,
+                              cudaMemcpyDeviceToDevice, H->cur));
+    return MG_OK;
+  }
   CKS(smooth(H, l, order, o.n_pre, prec));                                  // step 1
   CKS(launch_ok(H, launch_restrict(H->L[l], H->L[l + 1], order, o.n_pre >= 1, prec, H->cur),
                 "residual/restriction"));                                    // steps 2-5
@@ -353,6 +428,8 @@ mg_status emit_cycle(mg_hierarchy* H, int order) {
     for (int i = 0; i < H->opt.inner_cycles; ++i)
       CKS(iteration(H, 0, order, kFP32, fused && i == H->opt.inner_cycles - 1));
     if (!fused) CKS(launch_ok(H, launch_refine_update(H->L[0], H->cur), "refinement update"));
+    if (H->pass_on)
+      CK(H, cudaMemcpyAsync(H->hscal + 6, H->err_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, H->cur));
     return emit_refine_residual(H);
   }
   CKS(iteration(H, 0, order));
@@ -419,6 +496,16 @@ mg_status run_cycle(mg_hierarchy* H, int order, double* r_out) {
   }
   if (!r_out) return MG_OK;
   CK(H, cudaStreamSynchronize(H->stream));
+  if (H->pass_on) {
+    int err = 0;
+    std::memcpy(&err, H->hscal + 6, sizeof(int));
+    if (err) {
+      CK(H, cudaMemsetAsync(H->err_flag + 2, 0, sizeof(int), H->stream));
+      CK(H, cudaStreamSynchronize(H->stream));
+      std::memset(H->hscal + 6, 0, sizeof(int));
+      return fail(H, MG_ERR_INTERNAL, "smoothing pass: a shared-memory copy did not complete in time");
+    }
+  }
   *r_out = std::sqrt(H->hscal[0]) / (H->h * H->h);
   if (H->opt.use_graphs && H->timing) {
     for (auto& p : H->graphs[order][1].events) {
@@ -474,6 +561,9 @@ mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
   // all in three launches
   CKS(launch_ok(H, launch_build_lists(H->list_jobs, H->n_list_jobs, H->list_blocks, H->list_scratch, s),
                 "active lists"));
+  if (H->pass_on)
+    CKS(launch_ok(H, launch_pass_tiles(H->L[0].g, H->L[0].code, H->pass_flags, H->pass_tiles, H->pass_ntiles, s),
+                  "pass tiles"));
   unsigned long long hc[2 * kMaxLevels];
   CK(H, cudaMemcpyAsync(hc, H->counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
   for (int l = 0; l < H->nlev; ++l)
@@ -574,6 +664,7 @@ void mg_default_options(mg_options* opt) {
   opt->precision = 0;
   opt->inner_cycles = 1;
   opt->coarse_cluster = 0;
+  opt->smoother_pass = 1;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -708,7 +799,10 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
         lblocks += nb;
       }
   }
-  const int n_zero = 4 * H->nlev + 4;
+  // the temporal-blocked FP32 pass needs a fine level larger than the
+  // one-CTA smoother's and a second FP32 correction buffer
+  const bool pass = mixed && o.smoother_pass == 1 && !small_level(H->L[0].g) && H->nlev >= 2;
+  const int n_zero = 4 * H->nlev + 4 + (mixed ? 2 * H->nlev : 0) + (pass ? 2 : 0);
   const int n_f32 = mixed ? 4 * (H->nlev - 1) : 0;
   const size_t o_lscr = A.reserve(sizeof(uint32_t) * ((size_t)lblocks + 1));
   const size_t o_ljobs = A.reserve(sizeof(ListJob) * ljobs.size());
@@ -721,6 +815,16 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     o_rhoh2[c] = A.reserve(sizeof(double) * g0.total);
     o_bc[c] = A.reserve(sizeof(double) * g0.total);
     o_save[c] = A.reserve(sizeof(double) * g0.total);
+  }
+  size_t o_alt[2] = {0, 0}, o_pflags = 0, o_ptiles = 0, o_pn = 0;
+  if (pass) {
+    int nq, nj, nk;
+    pass_tile_grid(g0, &nq, &nj, &nk);
+    const size_t ncand = (size_t)nq * nj * nk;
+    for (int c = 0; c < 2; ++c) o_alt[c] = A.reserve(sizeof(float) * g0.total);
+    o_pflags = A.reserve(sizeof(uint32_t) * ncand);
+    o_ptiles = A.reserve(sizeof(uint32_t) * ncand);
+    o_pn = A.reserve(sizeof(uint32_t));
   }
   size_t o_mask = A.reserve(g0.ncells());
   H->max_partials = residual_norm_blocks(g0);
@@ -782,6 +886,17 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->err_flag = (int*)(base + o_err);
   for (int l = 0; l < H->nlev; ++l) H->L[l].g.fault = (unsigned*)(H->err_flag + 1);
   H->counts = (unsigned long long*)(base + o_cnt);
+  if (pass) {
+    for (int c = 0; c < 2; ++c) H->phi32_alt[c] = (float*)(base + o_alt[c]);
+    H->pass_flags = (uint32_t*)(base + o_pflags);
+    H->pass_tiles = (uint32_t*)(base + o_ptiles);
+    H->pass_ntiles = (uint32_t*)(base + o_pn);
+    // the pass is used only where its tensor maps and shared-memory size
+    // are accepted; otherwise the list half-sweeps run (the same results)
+    H->pass_on = init_pass_kernel() == cudaSuccess &&
+                 make_pass_maps(&H->pass_maps, g0, H->L[0].phi32, H->phi32_alt, H->L[0].rhs32, H->L[0].code);
+    (void)cudaGetLastError();
+  }
 
   mg_status st = MG_OK;
   e = cudaMemsetAsync(H->arena, 0, A.used, H->stream);
@@ -806,7 +921,10 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       for (int c = 0; c < 2; ++c) {
         zjobs.push_back({H->L[l].phi[c], H->L[l].g.total});
         zjobs.push_back({H->L[l].rhs[c], H->L[l].g.total});
+        // FP32 corrections: cells a new mask makes inactive must read 0
+        if (mixed) zjobs.push_back({H->L[l].phi32[c], H->L[l].g.total / 2});
       }
+    for (int c = 0; c < 2 && pass; ++c) zjobs.push_back({H->phi32_alt[c], g0.total / 2});
     for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.rhoh2[c], g0.total});
     for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.bc[c], g0.total});  // last: skipped when already 0
     std::vector<F32Job> fjobs;
@@ -1116,6 +1234,12 @@ mg_status mg_solve(mg_hierarchy* H, double tol, int max_cycles, mg_solve_info* i
   if (st == MG_ERR_NOT_CONVERGED) return fail(H, st, "tolerance not reached within max_cycles");
   if (st == MG_ERR_DIVERGED) return fail(H, st, "non-finite residual norm");
   return st;
+}
+
+mg_status mg_get_smoother_pass(const mg_hierarchy* H, int* active) {
+  if (!H || !active) return fail(nullptr, MG_ERR_INVALID_ARG, "null argument");
+  *active = H->pass_on ? 1 : 0;
+  return MG_OK;
 }
 
 mg_status mg_get_hold(const mg_hierarchy* H, int* hold) {
