@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
               const long long at = g.at(q, j, k);
               const float v = src[c][idx];
               a.out[c][at] = v;
-              if (a.phi64 && (cds[c][(jj + kR) * kWQC + qq + kR + kCodeShift] & kActive2))
+              if (a.phi64[c] && (cds[c][(jj + kR) * kWQC + qq + kR + kCodeShift] & kActive2))
                 a.phi64[c][at] += widen_f32(v);
             }
           }
