@@ -27,12 +27,14 @@
 // right-hand side of both colours and the cell codes of both colours.  Each
 // is one TMA tile copy (cp.async.bulk.tensor) of the padded plane region into
 // shared memory, completed on an mbarrier; the next plane's copies are issued
-// a step ahead.  Planes sit in rings of shared-memory slots: 7 for the
-// correction (planes t-4 .. t+2 relative to S1's plane, the last one in
-// flight) and 5 for the right-hand side and codes.  Waits on the copies are
-// bounded by time: a copy that has not landed after a second makes every
-// thread of the CTA leave the pass, after waiting (again bounded) for its
-// copies in flight, with an error word set for the host.
+// two steps ahead.  Planes sit in rings of shared-memory slots (7 for the
+// black correction, 6 for the right-hand side and codes, 5 for the red
+// correction, which is never copied in).  One thread waits on each copy's
+// mbarrier and the others wait at the block barrier after it, so that no
+// warp spins on the copies.  The wait is bounded by time: a copy that has not
+// landed after a second makes every thread of the CTA leave the pass, after
+// thread 0 has waited (again bounded) for the CTA's copies in flight, with an
+// error word set for the host.
 //
 // Only tiles with an active cell are walked (a list built with the mask).
 // With the mixed form's last post-smoothing pass, the write-back also adds
@@ -52,15 +54,21 @@ constexpr int kWQ = kPassTQ + 2 * kR;           // float region width (slots)
 constexpr int kWJ = kPassTJ + 2 * kR;           // region height (rows)
 constexpr int kWQC = kPassCodeWidth;            // code region width (bytes), x start aligned to 16
 constexpr int kCodeShift = kPassCodeShift;      // code index of float region column 0
-constexpr int kPhiSlots = 7;
-constexpr int kBcSlots = 5;
+// Ring slots: a black plane's copy is issued two steps before S1 first reads
+// it and the plane stays until its write-back (7 slots); right-hand side and
+// codes likewise (6); red planes are written by S1 and read until S4 of the
+// plane above (5).
+constexpr int kAhead = 2;
+constexpr int kRedSlots = 5;
+constexpr int kPhiSlots = 5 + kAhead;
+constexpr int kBcSlots = 4 + kAhead;
 constexpr int kPlaneF = kWQ * kWJ;              // floats per plane region
 constexpr int kPlaneC = kWQC * kWJ;             // code bytes per plane region
 constexpr unsigned kPhiBytes = kPlaneF * 4;
 constexpr unsigned kBcBytes = 2 * kPlaneF * 4 + 2 * kPlaneC;
 
 struct __align__(128) PassSmem {
-  float red[kPhiSlots][kPlaneF];
+  float red[kRedSlots][kPlaneF];
   float black[kPhiSlots][kPlaneF];
   float b[kBcSlots][2][kPlaneF];
   uint8_t code[kBcSlots][2][kPlaneC];
@@ -207,32 +215,33 @@ __global__ void __launch_bounds__(kPassThreads, 2)
       issued_bc |= 1u << sl;
     };
     if (tid == 0) {
-      issue_phi(0);
-      issue_phi(1);
-      issue_phi(2);
-      issue_bc(1);
+      for (int r = 0; r < 2 + kAhead; ++r) issue_phi(r);
+      for (int r = 1; r < 1 + kAhead; ++r) issue_bc(r);
     }
     {
       // black planes 0 and 1 (plane 2 is waited for in step 0)
-      bool ok = true;
-      for (int r = 0; r < 2 && ok; ++r) ok = stall || mbar_wait_bounded(&S.bar_phi[r], (ph_phi >> r) & 1u, kLimitNs);
-      if (!ok) S.abort = 1;
+      if (tid == 0) {
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = stall || mbar_wait_bounded(&S.bar_phi[r], (ph_phi >> r) & 1u, kLimitNs);
+        if (!ok) S.abort = 1;
+        if (!stall) {
+          ph_phi ^= 3u;
+          issued_phi &= ~3u;
+        }
+      }
       __syncthreads();
       if (S.abort) goto abort;
-      if (!stall) {
-        ph_phi ^= 3u;
-        if (tid == 0) issued_phi &= ~3u;
-      }
     }
     for (int s = 0; s < nsteps; ++s) {
-      // prefetch: black plane s+3 (read by S1 of the next step), right-hand
-      // side and codes of plane s+2 (S1 of the next step)
+      // prefetch: black plane s+2+kAhead and the right-hand side and codes of
+      // plane s+1+kAhead (S1 reads them kAhead steps from now)
       if (tid == 0) {
-        if (s + 3 < kPassZ + 8) issue_phi(s + 3);
-        if (s + 2 < kPassZ + 7) issue_bc(s + 2);
+        if (s + 2 + kAhead < kPassZ + 8) issue_phi(s + 2 + kAhead);
+        if (s + 1 + kAhead < kPassZ + 7) issue_bc(s + 1 + kAhead);
       }
-      // wait: black plane s+2 and b/codes of plane s+1, which S1 needs now
-      {
+      // wait (thread 0; the others at the barrier): black plane s+2 and the
+      // right-hand side and codes of plane s+1, which S1 needs now
+      if (tid == 0) {
         const int sp = (s + 2) % kPhiSlots, sb = s % kBcSlots;
         bool ok;
         if (stall) {
@@ -241,46 +250,47 @@ __global__ void __launch_bounds__(kPassThreads, 2)
           ok = mbar_wait_bounded(&S.bar_phi[sp], (ph_phi >> sp) & 1u, kLimitNs) &&
                mbar_wait_bounded(&S.bar_bc[sb], (ph_bc >> sb) & 1u, kLimitNs);
         }
-        if (!ok) S.abort = 1;
-        __syncthreads();
-        if (S.abort) goto abort;
-        ph_phi ^= 1u << sp;
-        ph_bc ^= 1u << sb;
-        if (tid == 0) {
+        if (!ok) {
+          S.abort = 1;
+        } else {
+          ph_phi ^= 1u << sp;
+          ph_bc ^= 1u << sb;
           issued_phi &= ~(1u << sp);
           issued_bc &= ~(1u << sb);
         }
       }
+      __syncthreads();
+      if (S.abort) goto abort;
       {
         // S1: red on plane r1 = s+1
         const int r1 = s + 1;
         stage<3, true>(0, j0 - kR, pbase + r1, S.black[(r1 + kPhiSlots - 1) % kPhiSlots], S.black[r1 % kPhiSlots],
-                       S.black[(r1 + 1) % kPhiSlots], S.red[r1 % kPhiSlots], S.b[(r1 - 1) % kBcSlots][0],
+                       S.black[(r1 + 1) % kPhiSlots], S.red[r1 % kRedSlots], S.b[(r1 - 1) % kBcSlots][0],
                        S.code[(r1 - 1) % kBcSlots][0], S.tab);
         __syncthreads();
         if (s >= 2) {  // S2: black on plane s
           const int r2 = s;
-          stage<2, false>(1, j0 - kR, pbase + r2, S.red[(r2 + kPhiSlots - 1) % kPhiSlots], S.red[r2 % kPhiSlots],
-                          S.red[(r2 + 1) % kPhiSlots], S.black[r2 % kPhiSlots], S.b[(r2 - 1) % kBcSlots][1],
+          stage<2, false>(1, j0 - kR, pbase + r2, S.red[(r2 + kRedSlots - 1) % kRedSlots], S.red[r2 % kRedSlots],
+                          S.red[(r2 + 1) % kRedSlots], S.black[r2 % kPhiSlots], S.b[(r2 - 1) % kBcSlots][1],
                           S.code[(r2 - 1) % kBcSlots][1], S.tab);
         }
         __syncthreads();
         if (s >= 4) {  // S3: red on plane s-1
           const int r3 = s - 1;
           stage<1, false>(0, j0 - kR, pbase + r3, S.black[(r3 + kPhiSlots - 1) % kPhiSlots],
-                          S.black[r3 % kPhiSlots], S.black[(r3 + 1) % kPhiSlots], S.red[r3 % kPhiSlots],
+                          S.black[r3 % kPhiSlots], S.black[(r3 + 1) % kPhiSlots], S.red[r3 % kRedSlots],
                           S.b[(r3 - 1) % kBcSlots][0], S.code[(r3 - 1) % kBcSlots][0], S.tab);
         }
         __syncthreads();
         if (s >= 6) {  // S4: black on plane s-2, then the plane's write-back
           const int r4 = s - 2;
-          stage<0, false>(1, j0 - kR, pbase + r4, S.red[(r4 + kPhiSlots - 1) % kPhiSlots], S.red[r4 % kPhiSlots],
-                          S.red[(r4 + 1) % kPhiSlots], S.black[r4 % kPhiSlots], S.b[(r4 - 1) % kBcSlots][1],
+          stage<0, false>(1, j0 - kR, pbase + r4, S.red[(r4 + kRedSlots - 1) % kRedSlots], S.red[r4 % kRedSlots],
+                          S.red[(r4 + 1) % kRedSlots], S.black[r4 % kPhiSlots], S.b[(r4 - 1) % kBcSlots][1],
                           S.code[(r4 - 1) % kBcSlots][1], S.tab);
           __syncthreads();
           const int k = pbase + r4;
           if (k < g.nz) {
-            const float* src[2] = {S.red[r4 % kPhiSlots], S.black[r4 % kPhiSlots]};
+            const float* src[2] = {S.red[r4 % kRedSlots], S.black[r4 % kPhiSlots]};
             const uint8_t* cds[2] = {S.code[(r4 - 1) % kBcSlots][0], S.code[(r4 - 1) % kBcSlots][1]};
             for (int e = tid; e < 2 * kPassTQ * kPassTJ; e += kPassThreads) {
               const int c = e / (kPassTQ * kPassTJ);
