@@ -130,33 +130,55 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// One stage of the wavefront: colour c's Gauss-Seidel update on plane region
-// `p` (relative plane index rp, global plane k) over the ring of width `ring`
-// around the tile.  `o_*` are the other colour's planes rp-1, rp, rp+1; `self`
+// One stage of the wavefront: colour c's Gauss-Seidel update on one plane
+// region, rows [J0, J1) and quads [Q0, Q1) of 4 slots (columns 4 Q .. 4 Q + 3).
+// `om`, `o0`, `op` are the other colour's planes below, at and above; `self`
 // is this colour's plane; b and code the plane's right-hand side and codes.
-// S1 (write_all) also writes 0 to the inactive red cells of its region, so
-// that stale values of the reused slot are never read.
-template <int RING, bool WRITE_ALL>
+// A thread takes one quad of one row at a time: its 4 values of the other
+// colour in the row, the rows above and below and the planes below and
+// above are 128-bit shared loads, plus the two scalars on either side; the
+// codes are one 32-bit load.  Every update is the list kernel's
+//   ((o[q] + o[q + dx]) + (o[row - 1] + o[row + 1])) + (o[plane - 1] + o[plane + 1])
+// then (s - b) * (1 / D), in the same order.  Each slot of the quad is written,
+// 0 where the cell is inactive (those hold 0 anyway, and S1 thereby clears
+// the stale red values of a reused slot).  A stage's quads span the whole
+// region width (ring 4 in x), wider than its ring; the values it computes
+// beyond its ring read stale or outside neighbours and are wrong, but each
+// ring's values are read only by later stages inside their own, narrower
+// rings, and S1 reads black values no later stage has touched, so no wrong
+// value reaches the tile.
+template <int J0, int J1, int Q0, int Q1>
 __device__ __forceinline__ void stage(int c, int j_base, int k, const float* __restrict__ om,
                                       const float* __restrict__ o0, const float* __restrict__ op, float* self,
                                       const float* __restrict__ b, const uint8_t* __restrict__ code,
                                       const float* tab) {
-  constexpr int W = kPassTQ + 2 * RING;
-  constexpr int H = kPassTJ + 2 * RING;
-  constexpr int N = W * H;
-  for (int e = threadIdx.x; e < N; e += kPassThreads) {
-    const int jj = kR - RING + e / W;
-    const int qq = kR - RING + e % W;
-    const int idx = jj * kWQ + qq;
-    const uint8_t cd = code[jj * kWQC + qq + kCodeShift];
-    if (!(cd & kActive2)) {
-      if (WRITE_ALL) self[idx] = 0.0f;
-      continue;
-    }
-    const int j = j_base + jj;
-    const int dx = ((c ^ j ^ k) & 1) ? 1 : -1;
-    const float s = ((o0[idx] + o0[idx + dx]) + (o0[idx - kWQ] + o0[idx + kWQ])) + (om[idx] + op[idx]);
-    self[idx] = (s - b[idx]) * tab[__popc((unsigned)cd >> kGhostShift)];
+  constexpr int NQ = Q1 - Q0;
+  constexpr int N = (J1 - J0) * NQ;
+  const int par = (c ^ j_base ^ k) & 1;  // row jj has dx = +1 iff (par ^ jj) & 1
+  for (int t = threadIdx.x; t < N; t += kPassThreads) {
+    const int jj = J0 + t / NQ;
+    const int idx = jj * kWQ + 4 * (Q0 + t % NQ);
+    const float4 v = *reinterpret_cast<const float4*>(o0 + idx);
+    const float vl = o0[idx - 1], vr = o0[idx + 4];
+    const float4 ym = *reinterpret_cast<const float4*>(o0 + idx - kWQ);
+    const float4 yp = *reinterpret_cast<const float4*>(o0 + idx + kWQ);
+    const float4 zm = *reinterpret_cast<const float4*>(om + idx);
+    const float4 zp = *reinterpret_cast<const float4*>(op + idx);
+    const float4 bb = *reinterpret_cast<const float4*>(b + idx);
+    const unsigned cd = *reinterpret_cast<const unsigned*>(code + jj * kWQC + (idx - jj * kWQ) + kCodeShift);
+    const bool plus = (par ^ jj) & 1;
+    const float x0 = plus ? v.y : vl, x1 = plus ? v.z : v.x, x2 = plus ? v.w : v.y, x3 = plus ? vr : v.z;
+    const float s0 = ((v.x + x0) + (ym.x + yp.x)) + (zm.x + zp.x);
+    const float s1 = ((v.y + x1) + (ym.y + yp.y)) + (zm.y + zp.y);
+    const float s2 = ((v.z + x2) + (ym.z + yp.z)) + (zm.z + zp.z);
+    const float s3 = ((v.w + x3) + (ym.w + yp.w)) + (zm.w + zp.w);
+    const unsigned c0 = cd & 0xffu, c1 = (cd >> 8) & 0xffu, c2 = (cd >> 16) & 0xffu, c3 = cd >> 24;
+    float4 out;
+    out.x = (c0 & kActive2) ? (s0 - bb.x) * tab[__popc(c0 >> kGhostShift)] : 0.0f;
+    out.y = (c1 & kActive2) ? (s1 - bb.y) * tab[__popc(c1 >> kGhostShift)] : 0.0f;
+    out.z = (c2 & kActive2) ? (s2 - bb.z) * tab[__popc(c2 >> kGhostShift)] : 0.0f;
+    out.w = (c3 & kActive2) ? (s3 - bb.w) * tab[__popc(c3 >> kGhostShift)] : 0.0f;
+    *reinterpret_cast<float4*>(self + idx) = out;
   }
 }
 
@@ -264,27 +286,27 @@ __global__ void __launch_bounds__(kPassThreads, 2)
       {
         // S1: red on plane r1 = s+1
         const int r1 = s + 1;
-        stage<3, true>(0, j0 - kR, pbase + r1, S.black[(r1 + kPhiSlots - 1) % kPhiSlots], S.black[r1 % kPhiSlots],
+        stage<1, kWJ - 1, 0, kWQ / 4>(0, j0 - kR, pbase + r1, S.black[(r1 + kPhiSlots - 1) % kPhiSlots], S.black[r1 % kPhiSlots],
                        S.black[(r1 + 1) % kPhiSlots], S.red[r1 % kRedSlots], S.b[(r1 - 1) % kBcSlots][0],
                        S.code[(r1 - 1) % kBcSlots][0], S.tab);
         __syncthreads();
         if (s >= 2) {  // S2: black on plane s
           const int r2 = s;
-          stage<2, false>(1, j0 - kR, pbase + r2, S.red[(r2 + kRedSlots - 1) % kRedSlots], S.red[r2 % kRedSlots],
+          stage<2, kWJ - 2, 0, kWQ / 4>(1, j0 - kR, pbase + r2, S.red[(r2 + kRedSlots - 1) % kRedSlots], S.red[r2 % kRedSlots],
                           S.red[(r2 + 1) % kRedSlots], S.black[r2 % kPhiSlots], S.b[(r2 - 1) % kBcSlots][1],
                           S.code[(r2 - 1) % kBcSlots][1], S.tab);
         }
         __syncthreads();
         if (s >= 4) {  // S3: red on plane s-1
           const int r3 = s - 1;
-          stage<1, false>(0, j0 - kR, pbase + r3, S.black[(r3 + kPhiSlots - 1) % kPhiSlots],
+          stage<3, kWJ - 3, 0, kWQ / 4>(0, j0 - kR, pbase + r3, S.black[(r3 + kPhiSlots - 1) % kPhiSlots],
                           S.black[r3 % kPhiSlots], S.black[(r3 + 1) % kPhiSlots], S.red[r3 % kRedSlots],
                           S.b[(r3 - 1) % kBcSlots][0], S.code[(r3 - 1) % kBcSlots][0], S.tab);
         }
         __syncthreads();
         if (s >= 6) {  // S4: black on plane s-2, then the plane's write-back
           const int r4 = s - 2;
-          stage<0, false>(1, j0 - kR, pbase + r4, S.red[(r4 + kRedSlots - 1) % kRedSlots], S.red[r4 % kRedSlots],
+          stage<4, kWJ - 4, 1, kWQ / 4 - 1>(1, j0 - kR, pbase + r4, S.red[(r4 + kRedSlots - 1) % kRedSlots], S.red[r4 % kRedSlots],
                           S.red[(r4 + 1) % kRedSlots], S.black[r4 % kPhiSlots], S.b[(r4 - 1) % kBcSlots][1],
                           S.code[(r4 - 1) % kBcSlots][1], S.tab);
           __syncthreads();
@@ -292,18 +314,27 @@ __global__ void __launch_bounds__(kPassThreads, 2)
           if (k < g.nz) {
             const float* src[2] = {S.red[r4 % kRedSlots], S.black[r4 % kPhiSlots]};
             const uint8_t* cds[2] = {S.code[(r4 - 1) % kBcSlots][0], S.code[(r4 - 1) % kBcSlots][1]};
-            for (int e = tid; e < 2 * kPassTQ * kPassTJ; e += kPassThreads) {
-              const int c = e / (kPassTQ * kPassTJ);
-              const int rem = e - c * (kPassTQ * kPassTJ);
-              const int jj = rem / kPassTQ, qq = rem - jj * kPassTQ;
+            constexpr int NQ = kPassTQ / 4;
+            for (int e = tid; e < 2 * kPassTJ * NQ; e += kPassThreads) {
+              const int c = e / (kPassTJ * NQ);
+              const int rem = e - c * (kPassTJ * NQ);
+              const int jj = rem / NQ, qq = 4 * (rem - jj * NQ);
               const int q = q0 + qq, j = j0 + jj;
-              if (q < 0 || q >= g.hx || j >= g.ny) continue;
+              // quads are 4-aligned and the pitch is a multiple of 16, so a
+              // quad lies inside the row or wholly in its padding (whose
+              // values are 0: nothing there is active)
+              if (q >= g.P || j >= g.ny) continue;
               const int idx = (jj + kR) * kWQ + qq + kR;
               const long long at = g.at(q, j, k);
-              const float v = src[c][idx];
-              a.out[c][at] = v;
-              if (a.phi64[c] && (cds[c][(jj + kR) * kWQC + qq + kR + kCodeShift] & kActive2))
-                a.phi64[c][at] += widen_f32(v);
+              const float4 v = *reinterpret_cast<const float4*>(src[c] + idx);
+              *reinterpret_cast<float4*>(a.out[c] + at) = v;
+              if (a.phi64[c]) {
+                const unsigned cd = *reinterpret_cast<const unsigned*>(cds[c] + (jj + kR) * kWQC + qq + kR + kCodeShift);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if ((cd >> (8 * u)) & kActive2) a.phi64[c][at + u] += widen_f32(vv[u]);
+              }
             }
           }
         }
