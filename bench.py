@@ -77,6 +77,10 @@ def parse():
                    help="profiling runs: time the headline form only (no second form, e2e or CPU leg)")
     p.add_argument("--precision", type=int, default=1, choices=[0, 1],
                    help="form timed for the headline: 1 = FP32 V-cycles in FP64 refinement, 0 = FP64")
+    p.add_argument("--smoother-pass", type=int, default=0, choices=[0, 1],
+                   help="mixed form: 1 = fine-level FP32 sweep pairs as temporal-blocked passes (the headline "
+                        "otherwise runs the faster list half-sweeps and times the pass beside it)")
+    p.add_argument("--no-pass-probe", action="store_true", help="skip timing the temporal-blocked pass")
     return p.parse_args()
 
 
@@ -298,12 +302,13 @@ class Form:
     """One solver form (precision 0 = FP64 method, 1 = FP32 V-cycles inside
     FP64 iterative refinement) on the resident workload."""
 
-    def __init__(self, B, precision, mask_d, rho_d, h, stream, inner_cycles=1, **extra):
+    def __init__(self, B, precision, mask_d, rho_d, h, stream, inner_cycles=1, smoother_pass=0, **extra):
         self.B = B
         self.precision = precision
         opts = dict(extra, precision=precision)
         if precision == 1:
             opts["inner_cycles"] = inner_cycles
+            opts["smoother_pass"] = smoother_pass
         self.H = B.Hierarchy(mask_d, h, stream=stream, **opts)
         self.n_active = self.H.level_info(0)[1]
         # the fine level's FP32 sweep pairs run as temporal-blocked passes
@@ -434,6 +439,13 @@ def roofline(st, n_active, precision, peaks, fp64_rate=None, pass_on=False):
             "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
             "traffic": profiled_traffic("gs_list_fp32_level0_sphere_union_256.md"),
             "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
+
+
+def peaks_of():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 BATCH_PATCHES = 96
@@ -594,12 +606,12 @@ def run_ours(args):
         # tolerance (same workload, untimed here; the chosen form is then
         # timed from scratch below)
         for ic in range(1, 9):
-            f = Form(B, 1, mask_d, rho_d, w["h"], stream.cuda_stream, ic)
+            f = Form(B, 1, mask_d, rho_d, w["h"], stream.cuda_stream, ic, args.smoother_pass)
             probe = argparse.Namespace(steps=3, warmup=1)
             ic_ms[ic] = 1e3 * time_form(f, probe, mask_d, rho_d, stream, world, device)["elapsed"] / 3
             del f
         args.inner_cycles = min(ic_ms, key=ic_ms.get)
-    main = Form(B, args.precision, mask_d, rho_d, w["h"], stream.cuda_stream, args.inner_cycles)
+    main = Form(B, args.precision, mask_d, rho_d, w["h"], stream.cuda_stream, args.inner_cycles, args.smoother_pass)
     n_active = main.n_active
 
     # clocks are sampled through the headline form's timed passes (steps
@@ -626,7 +638,8 @@ def run_ours(args):
                   flush=True)
         return
 
-    other = Form(B, 1 - args.precision, mask_d, rho_d, w["h"], stream.cuda_stream, args.inner_cycles)
+    other = Form(B, 1 - args.precision, mask_d, rho_d, w["h"], stream.cuda_stream, args.inner_cycles,
+                 args.smoother_pass)
     st_other = time_form(other, args, mask_d, rho_d, stream, world, device)
     st_other_k = time_form(other, args, mask_d, rho_d, stream, world, device, timing=True)
 
@@ -644,17 +657,25 @@ def run_ours(args):
     fp64_rate = B.mg_probe_fp64_rate(4096)
     main_pass, other_pass = main.pass_on, other.pass_on
     del main, other
+    pass_probe = None
+    if not args.no_pass_probe and not args.smoother_pass:
+        # the mixed form with the temporal-blocked smoothing pass, same inner
+        # cycles (bit-identical results), timed beside the headline
+        fp = Form(B, 1, mask_d, rho_d, w["h"], stream.cuda_stream, args.inner_cycles, 1)
+        probe = argparse.Namespace(steps=min(args.steps, 5), warmup=args.warmup)
+        st_p = time_form(fp, probe, mask_d, rho_d, stream, world, device)
+        st_pk = time_form(fp, probe, mask_d, rho_d, stream, world, device, timing=True)
+        pass_probe = {"time_to_tol_ms": 1e3 * st_p["elapsed"] / probe.steps, "steps": probe.steps,
+                      "active": fp.pass_on,
+                      "roofline": roofline(st_pk, n_active, 1, peaks_of(), fp64_rate, fp.pass_on)}
+        del fp
     wcyc = None if args.no_wcycles else run_wcycles(args, B, device, stream, world, mask_d, rho_d, w["h"])
     batched = None if args.no_batch else run_batched(args, B, device, stream, world)
     holes = None if args.no_holes else run_holes(args, B, device, stream, world)
 
     if rank != 0:
         return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = peaks_of()
     ms = lambda st: 1e3 * st["elapsed"] / args.steps  # noqa: E731
     line = {
         "metric": METRIC, "value": st_main["updates"] / st_main["elapsed"], "unit": UNIT, "n_gpus": world,
@@ -687,6 +708,8 @@ def run_ours(args):
         line["holes_512"] = holes
     if wcyc is not None:
         line["w_cycles"] = wcyc
+    if pass_probe is not None:
+        line["smoother_pass_probe"] = pass_probe
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"], line["error_vs_oracle"] = cpu_baseline(args.size, solutions)
     print(json.dumps(line), flush=True)

@@ -664,7 +664,7 @@ void mg_default_options(mg_options* opt) {
   opt->precision = 0;
   opt->inner_cycles = 1;
   opt->coarse_cluster = 0;
-  opt->smoother_pass = 1;
+  opt->smoother_pass = 0;
 }
 
 const char* mg_status_string(mg_status st) {

@@ -41,7 +41,7 @@ CASES = _cases()
 
 def _solve(oracle, w, **opts):
     H = B.Hierarchy(w["mask"], w["h"], precision=1, **opts)
-    assert H.smoother_pass == (opts.get("smoother_pass", 1) == 1)
+    assert H.smoother_pass == (opts.get("smoother_pass", 0) == 1)
     H.set_rhs(w["rho"])
     if "phi_c" in w:
         H.set_dirichlet(*oracle.dirichlet_from_coarse(w["mask"], w["phi_c"], w["origin"]))
