@@ -406,6 +406,49 @@ mg_status mg_batch_launches_per_cycle(const mg_batch* batch, long long* launches
 const char* mg_batch_last_error(const mg_batch* batch);
 
 /* ---------------------------------------------------------------------------
+ * Learned initial guess (no counterpart in the paper)
+ *
+ * A 3D U-Net that predicts the fine solution Phi of one AMR patch from three
+ * input channels (the right-hand side, the mask and the Dirichlet values),
+ * used as the initial guess of mg_solve, whose stopping test and order switch
+ * (Sections 4 and 5.2) stay the judge: a poor guess costs cycles, never
+ * accuracy.  Architecture, for L levels and c base channels (level l: c 2^l
+ * channels, grid n / 2^l): down path of two 3x3x3 convolutions with bias and
+ * ReLU per level, 2x2x2 mean pooling between levels; up path of nearest
+ * upsampling by 2, concatenation after the level's down output and two
+ * 3x3x3 convolutions with ReLU; a 1x1x1 head to one channel times the active
+ * mask.  Weights and activations are BF16 and every convolution accumulates
+ * in FP32 on the tensor cores (tcgen05 with TMEM accumulators).
+ * Parameters are ordered, per convolution down0.0, down0.1, ..., down(L-1).1,
+ * up0.0, up0.1, ..., up(L-2).1 and then the head: the weights
+ * [cout][cin][3][3][3] followed by the bias [cout] (head: [c], then [1]).
+ * Tensors at the C ABI are FP32 in natural layout [channel][z][y][x].
+ * ------------------------------------------------------------------------- */
+
+typedef struct mg_unet mg_unet; /* opaque, library-owned */
+
+/* levels 1..6, base a multiple of 16 with base * 2^(levels-1) <= 128, grid
+ * nx*ny*nz with each size 1..1024 and divisible by 2^(levels-1).  All
+ * parameters start at 0 (set them with mg_unet_set_params).  cuda_stream as
+ * in mg_create_hierarchy.  Errors: INVALID_ARG, OOM, CUDA. */
+mg_status mg_unet_create(int levels, int base, int nx, int ny, int nz, void* cuda_stream, mg_unet** out);
+mg_status mg_unet_destroy(mg_unet* net);
+mg_status mg_unet_num_params(const mg_unet* net, long long* n);
+/* All parameters in the order above, FP64 (rounded to FP32 masters and BF16
+ * working copies on the device).  Errors: INVALID_ARG, CUDA. */
+mg_status mg_unet_set_params(mg_unet* net, const double* params, mg_mem where);
+mg_status mg_unet_get_params(mg_unet* net, double* params, mg_mem where);
+/* Forward pass: x [3][nz][ny][nx] input channels (FP32); pred (nullable)
+ * receives [nz][ny][nx] (FP32).  Errors: INVALID_ARG, CUDA, INTERNAL (a
+ * kernel's bounded wait ran out). */
+mg_status mg_unet_forward(mg_unet* net, const float* x, mg_mem where, float* pred, mg_mem pred_where);
+/* The ReLU output of convolution `layer` (parameter order) after the last
+ * forward pass, [c][d][h][w] FP32; dims4 = {c, d, h, w}.  For verification. */
+mg_status mg_unet_layer_info(const mg_unet* net, int layer, int* dims4);
+mg_status mg_unet_layer_output(mg_unet* net, int layer, float* out, mg_mem where);
+const char* mg_unet_last_error(const mg_unet* net);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation
  * ------------------------------------------------------------------------- */
 

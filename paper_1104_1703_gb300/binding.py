@@ -98,6 +98,15 @@ SIGNATURES = {
     "mg_batch_autotune": (_i, [_vp, _i, _d, _i, _i, _vp]),
     "mg_batch_launches_per_cycle": (_i, [_vp, _vp]),
     "mg_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "mg_unet_create": (_i, [_i, _i, _i, _i, _i, _vp, _vp]),
+    "mg_unet_destroy": (_i, [_vp]),
+    "mg_unet_num_params": (_i, [_vp, _vp]),
+    "mg_unet_set_params": (_i, [_vp, _vp, _i]),
+    "mg_unet_get_params": (_i, [_vp, _vp, _i]),
+    "mg_unet_forward": (_i, [_vp, _vp, _i, _vp, _i]),
+    "mg_unet_layer_info": (_i, [_vp, _i, _vp]),
+    "mg_unet_layer_output": (_i, [_vp, _i, _vp, _i]),
+    "mg_unet_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 _LIB = None
@@ -629,3 +638,84 @@ class Batch:
 
     def launches_per_cycle(self):
         return mg_batch_launches_per_cycle(self.handle)
+
+
+# --------------------------------------------------------------------------
+# Learned initial guess (3D U-Net)
+# --------------------------------------------------------------------------
+
+def mg_unet_last_error(n=None) -> str:
+    return lib().mg_unet_last_error(n).decode()
+
+
+def _check_unet(st, n=None):
+    if st != MG_OK:
+        raise MGError(st, mg_unet_last_error(n))
+
+
+def _in_f32(a, shape, name):
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError("%s: expected a contiguous float32 tensor of shape %s" % (name, shape))
+        return _vp(a.data_ptr()), (MG_MEM_DEVICE if a.is_cuda else MG_MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if arr.shape != tuple(shape):
+        raise ValueError("%s: expected shape %s, got %s" % (name, tuple(shape), arr.shape))
+    return arr.ctypes.data_as(_vp), MG_MEM_HOST, arr
+
+
+class UNet:
+    """Owns one network handle (the C ABI's mg_unet_*)."""
+
+    def __init__(self, levels, base, shape, stream="auto"):
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        if stream == "auto":
+            stream = _default_stream()
+        out = _vp()
+        _check_unet(lib().mg_unet_create(int(levels), int(base), nx, ny, nz, stream, ctypes.byref(out)))
+        self.handle = out
+
+    def close(self):
+        if self.handle:
+            lib().mg_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        v = ctypes.c_longlong()
+        _check_unet(lib().mg_unet_num_params(self.handle, ctypes.byref(v)), self.handle)
+        return v.value
+
+    def set_params(self, flat):
+        arr = np.ascontiguousarray(flat, dtype=np.float64)
+        if arr.size != self.num_params():
+            raise ValueError("expected %d parameters" % self.num_params())
+        _check_unet(lib().mg_unet_set_params(self.handle, arr.ctypes.data_as(_vp), MG_MEM_HOST), self.handle)
+
+    def get_params(self):
+        out = np.zeros(self.num_params())
+        _check_unet(lib().mg_unet_get_params(self.handle, out.ctypes.data_as(_vp), MG_MEM_HOST), self.handle)
+        return out
+
+    def forward(self, x, out=None):
+        p, where, keep = _in_f32(x, (3,) + self.shape, "x")
+        if out is None:
+            out = np.zeros(self.shape, dtype=np.float32)
+        po, wo, keep_o = _in_f32(out, self.shape, "pred")
+        _check_unet(lib().mg_unet_forward(self.handle, p, where, po, wo), self.handle)
+        return out
+
+    def layer_output(self, layer):
+        dims = (_i * 4)()
+        _check_unet(lib().mg_unet_layer_info(self.handle, int(layer), dims), self.handle)
+        out = np.zeros(tuple(dims[:4]), dtype=np.float32)
+        _check_unet(lib().mg_unet_layer_output(self.handle, int(layer), out.ctypes.data_as(_vp), MG_MEM_HOST),
+                    self.handle)
+        return out

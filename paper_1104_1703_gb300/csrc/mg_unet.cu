@@ -1,0 +1,492 @@
+// Host driver of the learned initial guess's network (mg_unet_* in mg.h): a
+// 3D U-Net with BF16 weights and activations and FP32 accumulation, whose
+// convolutions run on the tcgen05 kernel of kernels_unet.cu.
+//
+// Architecture (levels L, base channels c; level l has c_l = c 2^l channels
+// and grid size n / 2^l):
+//   down path, l = 0 .. L-1: input (level 0: the three feature channels,
+//     padded to 16; level l > 0: the 2x2x2 mean of level l-1's output), then
+//     two 3x3x3 convolutions (zero padding, bias) each followed by ReLU;
+//   up path, l = L-2 .. 0: the level below's output upsampled by 2 (nearest)
+//     and concatenated after level l's down output (skip first), then two
+//     3x3x3 convolutions with ReLU;
+//   head: a 1x1x1 convolution to one channel, times the active mask.
+// The concatenation is one buffer per level: level l's second down
+// convolution writes its channels [0, c_l) and the upsampling its channels
+// [c_l, c_l + c_{l+1}), so no copy is made.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+#include "unet_internal.h"
+
+namespace gbmg {
+void set_thread_error(const char* msg);        // mg_capi.cu
+bool is_device_ptr(const void* p, int device);  // mg_capi.cu
+}  // namespace gbmg
+
+using namespace gbmg;
+
+namespace {
+
+constexpr int kMaxNetLevels = 6;
+
+struct Tensor {
+  __nv_bfloat16* p = nullptr;
+  int stride = 0;  // channels per voxel of the buffer
+  int off = 0;     // first channel of the tensor
+  int c = 0;       // channels of the tensor
+  int W = 0, H = 0, D = 0;
+  long long voxels() const { return (long long)W * H * D; }
+};
+
+struct Conv {
+  int cin = 0, cin_pad = 0, cout = 0, level = 0;
+  float* w = nullptr;   // FP32 master weights [cout][cin][27]
+  float* b = nullptr;   // [cout]
+  __nv_bfloat16* wf = nullptr;  // packed forward weights
+  Tensor in, out;
+  CUtensorMap map_in;
+  ConvArgs args;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+}  // namespace
+
+struct mg_unet {
+  int L = 0, base = 0, nx = 0, ny = 0, nz = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error = "no error";
+  char* arena = nullptr;
+  int* err = nullptr;
+  // tensors
+  Tensor x0;                           // level-0 input, 16 channels
+  Tensor d0[kMaxNetLevels];            // first down convolution
+  Tensor d1[kMaxNetLevels];            // second down convolution (a channel range of cat[l] for l < L-1)
+  Tensor pool[kMaxNetLevels];          // pooled input of level l >= 1
+  Tensor cat[kMaxNetLevels];           // skip + upsampled, l < L-1
+  Tensor u0[kMaxNetLevels], u1[kMaxNetLevels];
+  float* xin = nullptr;                // FP32 input channels [3][V0] (staging)
+  float* pred = nullptr;               // FP32 prediction [V0]
+  float* head_w = nullptr;             // [c_0]
+  float* head_b = nullptr;             // [1]
+  float* nat = nullptr;                // FP32 staging for layer read-back
+  size_t nat_elems = 0;
+  std::vector<Conv> convs;             // parameter order: down0.0, down0.1, ..., down(L-1).1, up0.0, up0.1, ..., up(L-2).1
+  long long n_params = 0;
+};
+
+namespace {
+
+thread_local std::string t_unet_error;
+
+mg_status ufail(mg_unet* N, mg_status st, const std::string& msg) {
+  if (N) N->last_error = msg;
+  set_thread_error(msg.c_str());
+  return st;
+}
+
+mg_status ucuda(mg_unet* N, cudaError_t e, const char* what) {
+  return ufail(N, e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define UCK(N, call)                                      \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ucuda((N), e_, #call);  \
+  } while (0)
+
+#define UCKS(call)                \
+  do {                            \
+    mg_status s_ = (call);        \
+    if (s_ != MG_OK) return s_;   \
+  } while (0)
+
+struct UGuard {
+  int prev = -1;
+  explicit UGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~UGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+struct Reserve {
+  size_t used = 0;
+  size_t take(size_t bytes) {
+    const size_t o = (used + 255) & ~(size_t)255;
+    used = o + bytes;
+    return o;
+  }
+};
+
+// Names the conv layers in parameter order.
+std::string conv_name(const mg_unet* N, int i) {
+  if (i < 2 * N->L) return "down" + std::to_string(i / 2) + "." + std::to_string(i % 2);
+  const int j = i - 2 * N->L;
+  return "up" + std::to_string(j / 2) + "." + std::to_string(j % 2);
+}
+
+mg_status setup_conv(mg_unet* N, Conv& C) {
+  int bx, by, bz;
+  conv_tile_box(C.in.W, C.in.H, C.in.D, &bx, &by, &bz);
+  const int kc = conv_kc(C.cin_pad);
+  if (!make_conv_input_map(&C.map_in, C.in.p, C.in.W, C.in.H, C.in.D, C.cin_pad, bx, by, bz, kc))
+    return ufail(N, MG_ERR_CUDA, "tensor map of a convolution input was refused");
+  ConvArgs& a = C.args;
+  std::memset(&a, 0, sizeof(a));
+  a.W = C.in.W;
+  a.H = C.in.H;
+  a.D = C.in.D;
+  a.cin = C.cin_pad;
+  a.cout = C.cout;
+  a.kc = kc;
+  a.bx = bx;
+  a.by = by;
+  a.bz = bz;
+  a.ntx = (a.W + bx - 1) / bx;
+  a.nty = (a.H + by - 1) / by;
+  a.ntz = (a.D + bz - 1) / bz;
+  a.w = C.wf;
+  a.bias = C.b;
+  a.relu = 1;
+  a.out = C.out.p;
+  a.out_stride = C.out.stride;
+  a.out_off = C.out.off;
+  a.err = N->err;
+  C.smem = conv_smem_bytes(a.cin, a.cout, a.kc);
+  UCK(N, init_conv_kernel(C.smem));
+  C.grid = conv_grid(a, C.smem);
+  return MG_OK;
+}
+
+mg_status check_err(mg_unet* N) {
+  int e = 0;
+  UCK(N, cudaStreamSynchronize(N->stream));
+  UCK(N, cudaMemcpy(&e, N->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    UCK(N, cudaMemset(N->err, 0, sizeof(int)));
+    return ufail(N, MG_ERR_INTERNAL, "network kernel: a wait on an asynchronous copy or MMA did not complete in time");
+  }
+  return MG_OK;
+}
+
+mg_status forward(mg_unet* N) {
+  cudaStream_t s = N->stream;
+  const int L = N->L;
+  for (int l = 0; l < L; ++l) {
+    if (l > 0) {
+      const Tensor& src = N->d1[l - 1];
+      const Tensor& dst = N->pool[l];
+      UCK(N, launch_avg_pool(src.p, src.stride, src.off, dst.W, dst.H, dst.D, dst.c, dst.p, dst.stride, dst.off, s));
+    }
+    for (int j = 0; j < 2; ++j) {
+      Conv& C = N->convs[2 * l + j];
+      UCK(N, launch_conv(C.map_in, C.args, C.grid, s));
+    }
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const Tensor& prev = l == L - 2 ? N->d1[L - 1] : N->u1[l + 1];
+    const Tensor& cat = N->cat[l];
+    UCK(N, launch_upsample(prev.p, prev.stride, prev.off, prev.W, prev.H, prev.D, prev.c, cat.p, cat.stride,
+                           N->d1[l].c, s));
+    for (int j = 0; j < 2; ++j) {
+      Conv& C = N->convs[2 * L + 2 * l + j];
+      UCK(N, launch_conv(C.map_in, C.args, C.grid, s));
+    }
+  }
+  const Tensor& top = L >= 2 ? N->u1[0] : N->d1[0];
+  UCK(N, launch_head(top.p, top.c, N->head_w, N->head_b, N->x0.p, N->x0.voxels(), N->pred, s));
+  return MG_OK;
+}
+
+void destroy_unet(mg_unet* N) {
+  if (!N) return;
+  UGuard g(N->device);
+  if (N->stream) cudaStreamSynchronize(N->stream);
+  if (N->arena) cudaFree(N->arena);
+  if (N->own_stream && N->stream) cudaStreamDestroy(N->stream);
+  delete N;
+}
+
+// copy `bytes` between a caller buffer and device memory
+mg_status copy_io(mg_unet* N, void* dst, const void* src, size_t bytes, bool to_device, mg_mem where) {
+  if (where == MG_MEM_DEVICE) {
+    const void* user = to_device ? src : dst;
+    if (!is_device_ptr(user, N->device))
+      return ufail(N, MG_ERR_INVALID_ARG, "an MG_MEM_DEVICE buffer is not device memory of the network's GPU");
+    UCK(N, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, N->stream));
+    return MG_OK;
+  }
+  UCK(N, cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, N->stream));
+  UCK(N, cudaStreamSynchronize(N->stream));
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_unet_create(int levels, int base, int nx, int ny, int nz, void* cuda_stream, mg_unet** out) {
+  if (out) *out = nullptr;
+  if (!out) return ufail(nullptr, MG_ERR_INVALID_ARG, "null output");
+  if (levels < 1 || levels > kMaxNetLevels || base < 16 || base % 16 || base << (levels - 1) > 128)
+    return ufail(nullptr, MG_ERR_INVALID_ARG, "levels must be 1..6 and base a multiple of 16 with base 2^(levels-1) <= 128");
+  const int div = 1 << (levels - 1);
+  if (nx < 1 || ny < 1 || nz < 1 || nx % div || ny % div || nz % div || nx > 1024 || ny > 1024 || nz > 1024)
+    return ufail(nullptr, MG_ERR_INVALID_ARG, "dimensions must be 1..1024 and divisible by 2^(levels-1)");
+  mg_unet* N = new mg_unet();
+  N->L = levels;
+  N->base = base;
+  N->nx = nx;
+  N->ny = ny;
+  N->nz = nz;
+  if (cudaGetDevice(&N->device) != cudaSuccess) {
+    delete N;
+    return ufail(nullptr, MG_ERR_CUDA, "no CUDA device");
+  }
+  if (cuda_stream) {
+    N->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreate(&N->stream) != cudaSuccess) {
+      delete N;
+      return ufail(nullptr, MG_ERR_CUDA, "cudaStreamCreate");
+    }
+    N->own_stream = true;
+  }
+  const int L = levels;
+  std::vector<int> ch(L);
+  for (int l = 0; l < L; ++l) ch[l] = base << l;
+  // tensors and their arena offsets
+  Reserve R;
+  struct Pending {
+    Tensor* t;
+    size_t off;
+  };
+  std::vector<Pending> pend;
+  auto tensor = [&](Tensor& t, int level, int stride, int off, int c, bool alloc) {
+    t.W = nx >> level;
+    t.H = ny >> level;
+    t.D = nz >> level;
+    t.stride = stride;
+    t.off = off;
+    t.c = c;
+    if (alloc) pend.push_back({&t, R.take(sizeof(__nv_bfloat16) * (size_t)t.voxels() * stride)});
+  };
+  tensor(N->x0, 0, 16, 0, 16, true);
+  for (int l = 0; l < L; ++l) {
+    if (l > 0) tensor(N->pool[l], l, ch[l - 1], 0, ch[l - 1], true);
+    tensor(N->d0[l], l, ch[l], 0, ch[l], true);
+    if (l < L - 1) {
+      tensor(N->cat[l], l, ch[l] + ch[l + 1], 0, ch[l] + ch[l + 1], true);
+      tensor(N->d1[l], l, ch[l] + ch[l + 1], 0, ch[l], false);  // shares cat[l]'s buffer
+    } else {
+      tensor(N->d1[l], l, ch[l], 0, ch[l], true);
+    }
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    tensor(N->u0[l], l, ch[l], 0, ch[l], true);
+    tensor(N->u1[l], l, ch[l], 0, ch[l], true);
+  }
+  const long long V0 = (long long)nx * ny * nz;
+  const size_t o_xin = R.take(sizeof(float) * 3 * V0);
+  const size_t o_pred = R.take(sizeof(float) * V0);
+  N->nat_elems = (size_t)V0 * (size_t)(ch[0] + (L > 1 ? ch[1] : 0) + 16);
+  const size_t o_nat = R.take(sizeof(float) * N->nat_elems);
+  const size_t o_err = R.take(sizeof(int) * 4);
+  // convolutions
+  struct ConvPlan {
+    int cin, cout, level;
+  };
+  std::vector<ConvPlan> plan;
+  for (int l = 0; l < L; ++l) {
+    plan.push_back({l == 0 ? 3 : ch[l - 1], ch[l], l});
+    plan.push_back({ch[l], ch[l], l});
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    plan.push_back({ch[l] + ch[l + 1], ch[l], l});
+    plan.push_back({ch[l], ch[l], l});
+  }
+  N->convs.resize(plan.size());
+  std::vector<size_t> o_w(plan.size()), o_b(plan.size()), o_wf(plan.size());
+  N->n_params = 0;
+  for (size_t i = 0; i < plan.size(); ++i) {
+    Conv& C = N->convs[i];
+    C.cin = plan[i].cin;
+    C.cin_pad = (C.cin + 15) / 16 * 16;
+    C.cout = plan[i].cout;
+    C.level = plan[i].level;
+    o_w[i] = R.take(sizeof(float) * (size_t)C.cout * C.cin * 27);
+    o_b[i] = R.take(sizeof(float) * C.cout);
+    o_wf[i] = R.take(sizeof(__nv_bfloat16) * 27 * (size_t)C.cout * C.cin_pad);
+    N->n_params += (long long)C.cout * C.cin * 27 + C.cout;
+  }
+  const size_t o_hw = R.take(sizeof(float) * ch[0]);
+  const size_t o_hb = R.take(sizeof(float));
+  N->n_params += ch[0] + 1;
+
+  cudaError_t e = dev_malloc((void**)&N->arena, R.used);
+  if (e != cudaSuccess) {
+    N->arena = nullptr;
+    mg_status st = ucuda(nullptr, e, "cudaMalloc(network arena)");
+    destroy_unet(N);
+    return st;
+  }
+  char* base_p = N->arena;
+  for (auto& p : pend) p.t->p = (__nv_bfloat16*)(base_p + p.off);
+  for (int l = 0; l < L - 1; ++l) N->d1[l].p = N->cat[l].p;
+  N->xin = (float*)(base_p + o_xin);
+  N->pred = (float*)(base_p + o_pred);
+  N->nat = (float*)(base_p + o_nat);
+  N->err = (int*)(base_p + o_err);
+  N->head_w = (float*)(base_p + o_hw);
+  N->head_b = (float*)(base_p + o_hb);
+  mg_status st = MG_OK;
+  if (cudaMemsetAsync(N->arena, 0, R.used, N->stream) != cudaSuccess) st = ufail(N, MG_ERR_CUDA, "arena reset");
+  for (size_t i = 0; i < plan.size() && st == MG_OK; ++i) {
+    Conv& C = N->convs[i];
+    C.w = (float*)(base_p + o_w[i]);
+    C.b = (float*)(base_p + o_b[i]);
+    C.wf = (__nv_bfloat16*)(base_p + o_wf[i]);
+    const int l = C.level;
+    const bool down = (int)i < 2 * L;
+    const int j = (int)i % 2;
+    if (down) {
+      C.in = j == 0 ? (l == 0 ? N->x0 : N->pool[l]) : N->d0[l];
+      C.out = j == 0 ? N->d0[l] : N->d1[l];
+    } else {
+      C.in = j == 0 ? N->cat[l] : N->u0[l];
+      C.out = j == 0 ? N->u0[l] : N->u1[l];
+    }
+    st = setup_conv(N, C);
+  }
+  if (st == MG_OK && cudaStreamSynchronize(N->stream) != cudaSuccess) st = ufail(N, MG_ERR_CUDA, "network setup");
+  if (st != MG_OK) {
+    std::string msg = N->last_error;
+    destroy_unet(N);
+    set_thread_error(msg.c_str());
+    return st;
+  }
+  *out = N;
+  return MG_OK;
+}
+
+mg_status mg_unet_destroy(mg_unet* N) {
+  destroy_unet(N);
+  return MG_OK;
+}
+
+mg_status mg_unet_num_params(const mg_unet* N, long long* n) {
+  if (!N || !n) return ufail(nullptr, MG_ERR_INVALID_ARG, "null argument");
+  *n = N->n_params;
+  return MG_OK;
+}
+
+mg_status mg_unet_set_params(mg_unet* N, const double* p, mg_mem where) {
+  if (!N || !p) return ufail(N, MG_ERR_INVALID_ARG, "null argument");
+  UGuard g(N->device);
+  std::vector<double> h((size_t)N->n_params);
+  if (where == MG_MEM_DEVICE) {
+    if (!is_device_ptr(p, N->device))
+      return ufail(N, MG_ERR_INVALID_ARG, "an MG_MEM_DEVICE buffer is not device memory of the network's GPU");
+    UCK(N, cudaMemcpy(h.data(), p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h.data(), p, sizeof(double) * h.size());
+  }
+  size_t k = 0;
+  std::vector<float> f;
+  for (Conv& C : N->convs) {
+    const size_t nw = (size_t)C.cout * C.cin * 27;
+    f.assign(h.begin() + k, h.begin() + k + nw);
+    k += nw;
+    UCK(N, cudaMemcpy(C.w, f.data(), sizeof(float) * nw, cudaMemcpyHostToDevice));
+    f.assign(h.begin() + k, h.begin() + k + C.cout);
+    k += C.cout;
+    UCK(N, cudaMemcpy(C.b, f.data(), sizeof(float) * C.cout, cudaMemcpyHostToDevice));
+    UCK(N, launch_pack_weights(C.w, C.cout, C.cin, C.cin_pad, false, C.wf, N->stream));
+  }
+  const int c0 = N->base;
+  f.assign(h.begin() + k, h.begin() + k + c0);
+  k += c0;
+  UCK(N, cudaMemcpy(N->head_w, f.data(), sizeof(float) * c0, cudaMemcpyHostToDevice));
+  const float hb = (float)h[k];
+  UCK(N, cudaMemcpy(N->head_b, &hb, sizeof(float), cudaMemcpyHostToDevice));
+  UCK(N, cudaStreamSynchronize(N->stream));
+  return MG_OK;
+}
+
+mg_status mg_unet_get_params(mg_unet* N, double* p, mg_mem where) {
+  if (!N || !p) return ufail(N, MG_ERR_INVALID_ARG, "null argument");
+  UGuard g(N->device);
+  UCK(N, cudaStreamSynchronize(N->stream));
+  std::vector<double> h;
+  h.reserve((size_t)N->n_params);
+  std::vector<float> f;
+  for (Conv& C : N->convs) {
+    f.resize((size_t)C.cout * C.cin * 27);
+    UCK(N, cudaMemcpy(f.data(), C.w, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+    h.insert(h.end(), f.begin(), f.end());
+    f.resize(C.cout);
+    UCK(N, cudaMemcpy(f.data(), C.b, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+    h.insert(h.end(), f.begin(), f.end());
+  }
+  f.resize(N->base + 1);
+  UCK(N, cudaMemcpy(f.data(), N->head_w, sizeof(float) * N->base, cudaMemcpyDeviceToHost));
+  UCK(N, cudaMemcpy(f.data() + N->base, N->head_b, sizeof(float), cudaMemcpyDeviceToHost));
+  h.insert(h.end(), f.begin(), f.end());
+  if (where == MG_MEM_DEVICE) {
+    if (!is_device_ptr(p, N->device))
+      return ufail(N, MG_ERR_INVALID_ARG, "an MG_MEM_DEVICE buffer is not device memory of the network's GPU");
+    UCK(N, cudaMemcpy(p, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(p, h.data(), sizeof(double) * h.size());
+  }
+  return MG_OK;
+}
+
+mg_status mg_unet_forward(mg_unet* N, const float* x, mg_mem where, float* pred, mg_mem pred_where) {
+  if (!N || !x) return ufail(N, MG_ERR_INVALID_ARG, "null argument");
+  UGuard g(N->device);
+  const long long V0 = N->x0.voxels();
+  UCKS(copy_io(N, N->xin, x, sizeof(float) * 3 * V0, true, where));
+  UCK(N, launch_input_to_bf16(N->xin, V0, N->x0.p, N->stream));
+  UCKS(forward(N));
+  UCKS(check_err(N));
+  if (pred) UCKS(copy_io(N, pred, N->pred, sizeof(float) * V0, false, pred_where));
+  return MG_OK;
+}
+
+mg_status mg_unet_layer_output(mg_unet* N, int layer, float* out, mg_mem where) {
+  if (!N || !out) return ufail(N, MG_ERR_INVALID_ARG, "null argument");
+  if (layer < 0 || layer >= (int)N->convs.size()) return ufail(N, MG_ERR_INVALID_ARG, "layer out of range");
+  UGuard g(N->device);
+  const Tensor& t = N->convs[layer].out;
+  const size_t n = (size_t)t.c * t.voxels();
+  if (n > N->nat_elems) return ufail(N, MG_ERR_INTERNAL, "read-back staging too small");
+  UCK(N, launch_tensor_to_natural(t.p, t.stride, t.off, t.c, t.voxels(), N->nat, N->stream));
+  return copy_io(N, out, N->nat, sizeof(float) * n, false, where);
+}
+
+mg_status mg_unet_layer_info(const mg_unet* N, int layer, int* dims4) {
+  if (!N || !dims4) return ufail(nullptr, MG_ERR_INVALID_ARG, "null argument");
+  if (layer < 0 || layer >= (int)N->convs.size()) return ufail(nullptr, MG_ERR_INVALID_ARG, "layer out of range");
+  const Tensor& t = N->convs[layer].out;
+  dims4[0] = t.c;
+  dims4[1] = t.D;
+  dims4[2] = t.H;
+  dims4[3] = t.W;
+  return MG_OK;
+}
+
+const char* mg_unet_last_error(const mg_unet* N) { return N ? N->last_error.c_str() : mg_last_error(nullptr); }
+
+}  // extern "C"

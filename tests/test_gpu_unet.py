@@ -1,0 +1,127 @@
+"""The learned initial guess's network on the GPU (mg_unet_*: tcgen05
+convolutions, BF16 weights and activations, FP32 accumulation) against its
+FP64 definition in oracle/unet_oracle.py.
+
+Tolerances, from the arithmetic.  The network rounds its weights and every
+activation to BF16 (relative error at most 2^-9 per value) and accumulates
+in FP32 (K <= 27 x 192 products; relative error well below 1e-4 of the sum
+of magnitudes).  So
+  - per layer: the oracle's convolution applied to the network's own BF16
+    input and BF16-rounded weights, then ReLU, matches the layer's output to
+    |got - want| <= 2^-8 |want| + 2e-4 max|want| (one output rounding plus
+    the accumulation);
+  - end to end: the oracle's forward pass on BF16-rounded weights and input
+    differs from the network's by the BF16 roundings of the intermediate
+    activations, each of relative size 2^-9 and propagated through at most
+    4 levels x 4 convolutions: relative L2 error <= 2e-2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import unet_oracle as U  # noqa: E402
+from paper_1104_1703_gb300 import binding as B  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), as float64."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def flat(P):
+    return np.concatenate([P[k].ravel() for k in P])
+
+
+def _params(levels, base, seed):
+    P = U.init_params(seed, levels=levels, base=base)
+    rng = np.random.default_rng(seed + 1)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = rng.normal(0.0, 0.1, P[k].shape)
+    return P
+
+
+def _input(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(3, n, n, n))
+    x[1] = np.where(rng.random((n, n, n)) < 0.7, 1.0, -1.0)
+    return x.astype(np.float32)
+
+
+def _pool(t):
+    c, d, h, w = t.shape
+    return t.reshape(c, d // 2, 2, h // 2, 2, w // 2, 2).sum(axis=(2, 4, 6)) * 0.125
+
+
+def _names(levels):
+    return ["down%d.%d" % (l, j) for l in range(levels) for j in range(2)] + \
+           ["up%d.%d" % (l, j) for l in range(levels - 1) for j in range(2)]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("levels,n", [(1, 16), (2, 16), (3, 16), (4, 16), (2, 24), (3, 32)])
+def test_each_convolution_matches_the_oracle(dev, levels, n):
+    P = _params(levels, 16, 11 + levels)
+    x = _input(n, 5 + n)
+    net = B.UNet(levels, 16, (n, n, n))
+    net.set_params(flat(P))
+    net.forward(x)
+    names = _names(levels)
+    out = {name: net.layer_output(i).astype(np.float64) for i, name in enumerate(names)}
+    for i, name in enumerate(names):
+        l, j = int(name[-3]), int(name[-1])
+        if name.startswith("down"):
+            if j == 1:
+                inp = out["down%d.0" % l]
+            elif l == 0:
+                inp = bf16(x)
+            else:
+                inp = bf16(_pool(out["down%d.1" % (l - 1)]))
+        else:
+            if j == 1:
+                inp = out["up%d.0" % l]
+            else:
+                below = out["down%d.1" % (levels - 1)] if l == levels - 2 else out["up%d.1" % (l + 1)]
+                inp = np.concatenate([out["down%d.1" % l], U.upsample2(below)], axis=0)
+        want = U.relu(U.conv3d(inp, bf16(P[name + ".w"]), P[name + ".b"]))
+        got = out[name]
+        assert got.shape == want.shape, name
+        bound = 2.0 ** -8 * np.abs(want) + 2e-4 * np.abs(want).max()
+        bad = np.abs(got - want) > bound
+        assert not bad.any(), (name, int(bad.sum()), float(np.abs(got - want).max()), float(np.abs(want).max()))
+
+
+@pytest.mark.parametrize("levels,n", [(2, 16), (4, 32)])
+def test_forward_matches_the_oracle_end_to_end(dev, levels, n):
+    P = _params(levels, 16, 21)
+    x = _input(n, 9)
+    net = B.UNet(levels, 16, (n, n, n))
+    net.set_params(flat(P))
+    pred = net.forward(x).astype(np.float64)
+    Pb = {k: (bf16(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in P.items()}
+    ref, _ = U.forward(Pb, bf16(x))
+    ref = ref[0]
+    assert not pred[x[1] <= 0].any()
+    err = np.linalg.norm(pred - ref) / np.linalg.norm(ref)
+    assert err < 2e-2, err
+
+
+def test_params_round_trip(dev):
+    P = _params(3, 16, 4)
+    net = B.UNet(3, 16, (16, 16, 16))
+    f = flat(P)
+    net.set_params(f)
+    back = net.get_params()
+    assert back.shape == f.shape
+    np.testing.assert_allclose(back, f.astype(np.float32).astype(np.float64), rtol=0, atol=0)
