@@ -164,8 +164,16 @@ mg_status setup_conv(mg_unet* N, Conv& C) {
   a.out_off = C.out.off;
   a.err = N->err;
   C.smem = conv_smem_bytes(a.cin, a.cout, a.kc);
-  UCK(N, init_conv_kernel(C.smem));
-  C.grid = conv_grid(a, C.smem);
+  return MG_OK;
+}
+
+// The kernel's shared-memory limit is one attribute for all convolutions:
+// set it to the largest need, then size each launch grid.
+mg_status finish_convs(mg_unet* N) {
+  size_t most = 0;
+  for (const Conv& C : N->convs) most = C.smem > most ? C.smem : most;
+  UCK(N, init_conv_kernel(most));
+  for (Conv& C : N->convs) C.grid = conv_grid(C.args, C.smem);
   return MG_OK;
 }
 
@@ -369,6 +377,7 @@ mg_status mg_unet_create(int levels, int base, int nx, int ny, int nz, void* cud
     }
     st = setup_conv(N, C);
   }
+  if (st == MG_OK) st = finish_convs(N);
   if (st == MG_OK && cudaStreamSynchronize(N->stream) != cudaSuccess) st = ufail(N, MG_ERR_CUDA, "network setup");
   if (st != MG_OK) {
     std::string msg = N->last_error;
