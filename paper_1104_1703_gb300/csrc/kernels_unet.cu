@@ -282,10 +282,17 @@ cudaError_t init_conv_kernel(size_t smem_bytes) {
   return cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
+// The output tile's box: powers of two with bx * by * bz = 128 exactly (the
+// copy of a tile must deliver the 128 rows the MMA and the barrier's byte
+// count expect; rows beyond the grid read 0 and are not stored).
 void conv_tile_box(int W, int H, int D, int* bx, int* by, int* bz) {
-  *bx = W < 128 ? W : 128;
-  const int rest = 128 / *bx;
-  *by = H < rest ? H : rest;
+  auto pow2_at_most = [](int n, int cap) {
+    int p = 1;
+    while (2 * p <= n && 2 * p <= cap) p *= 2;
+    return p;
+  };
+  *bx = pow2_at_most(W, 128);
+  *by = pow2_at_most(H, 128 / *bx);
   *bz = 128 / (*bx * *by);
   (void)D;
 }
