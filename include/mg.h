@@ -442,6 +442,23 @@ mg_status mg_unet_get_params(mg_unet* net, double* params, mg_mem where);
  * receives [nz][ny][nx] (FP32).  Errors: INVALID_ARG, CUDA, INTERNAL (a
  * kernel's bounded wait ran out). */
 mg_status mg_unet_forward(mg_unet* net, const float* x, mg_mem where, float* pred, mg_mem pred_where);
+/* Backward pass after mg_unet_forward: g_pred [nz][ny][nx] (FP32) is
+ * dL/dpred; the gradient of every parameter (order above) is computed on the
+ * GPU (weight gradients as tcgen05 GEMMs over the voxels) and kept in the
+ * network; mg_unet_get_grads copies it out (FP64).  Errors: INVALID_ARG,
+ * CUDA, INTERNAL. */
+mg_status mg_unet_backward(mg_unet* net, const float* g_pred, mg_mem where);
+mg_status mg_unet_get_grads(mg_unet* net, double* grads, mg_mem where);
+/* One Adam update (Kingma & Ba, Algorithm 1, with bias correction) of every
+ * parameter from the current gradients; FP32 master parameters, then the
+ * BF16 working weights are rounded again.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_unet_adam_step(mg_unet* net, double lr, double beta1, double beta2, double eps);
+/* One training step on one sample: forward pass on x [3][nz][ny][nx], loss
+ * sum over active cells of (pred - y)^2 / sum of y^2 there (y [nz][ny][nx],
+ * active = x channel 1 > 0), backward pass and one Adam update (beta1 0.9,
+ * beta2 0.999, eps 1e-8).  loss (nullable) receives the loss before the
+ * update.  Errors: INVALID_ARG, CUDA, INTERNAL. */
+mg_status mg_unet_train_step(mg_unet* net, const float* x, const float* y, mg_mem where, double lr, double* loss);
 /* The ReLU output of convolution `layer` (parameter order) after the last
  * forward pass, [c][d][h][w] FP32; dims4 = {c, d, h, w}.  For verification. */
 mg_status mg_unet_layer_info(const mg_unet* net, int layer, int* dims4);

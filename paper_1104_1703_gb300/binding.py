@@ -104,6 +104,10 @@ SIGNATURES = {
     "mg_unet_set_params": (_i, [_vp, _vp, _i]),
     "mg_unet_get_params": (_i, [_vp, _vp, _i]),
     "mg_unet_forward": (_i, [_vp, _vp, _i, _vp, _i]),
+    "mg_unet_backward": (_i, [_vp, _vp, _i]),
+    "mg_unet_get_grads": (_i, [_vp, _vp, _i]),
+    "mg_unet_adam_step": (_i, [_vp, _d, _d, _d, _d]),
+    "mg_unet_train_step": (_i, [_vp, _vp, _vp, _i, _d, _vp]),
     "mg_unet_layer_info": (_i, [_vp, _i, _vp]),
     "mg_unet_layer_output": (_i, [_vp, _i, _vp, _i]),
     "mg_unet_last_error": (ctypes.c_char_p, [_vp]),
@@ -711,6 +715,28 @@ class UNet:
         po, wo, keep_o = _in_f32(out, self.shape, "pred")
         _check_unet(lib().mg_unet_forward(self.handle, p, where, po, wo), self.handle)
         return out
+
+    def backward(self, g_pred):
+        p, where, keep = _in_f32(g_pred, self.shape, "g_pred")
+        _check_unet(lib().mg_unet_backward(self.handle, p, where), self.handle)
+
+    def get_grads(self):
+        out = np.zeros(self.num_params())
+        _check_unet(lib().mg_unet_get_grads(self.handle, out.ctypes.data_as(_vp), MG_MEM_HOST), self.handle)
+        return out
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check_unet(lib().mg_unet_adam_step(self.handle, float(lr), float(beta1), float(beta2), float(eps)),
+                    self.handle)
+
+    def train_step(self, x, y, lr=1e-3):
+        px, wx, kx = _in_f32(x, (3,) + self.shape, "x")
+        py, wy, ky = _in_f32(y, self.shape, "y")
+        if wx != wy:
+            raise ValueError("x and y must both be host arrays or both CUDA tensors")
+        loss = _d()
+        _check_unet(lib().mg_unet_train_step(self.handle, px, py, wx, float(lr), ctypes.byref(loss)), self.handle)
+        return loss.value
 
     def layer_output(self, layer):
         dims = (_i * 4)()

@@ -157,10 +157,19 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(const void* base, uint32_t 
          (((uint64_t)(sbo >> 4) & 0x3fffull) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor of an operand in the canonical MN-major
+// layout without swizzle: core matrices of 8 K-rows x 16 bytes (8 M or N
+// elements) stored as 128 contiguous bytes; `lbo` is the byte distance
+// between core matrices adjacent along K, `sbo` along M (or N).
+__device__ __forceinline__ uint64_t smem_desc_mnmajor(const void* base, uint32_t lbo, uint32_t sbo) {
+  return smem_desc_kmajor(base, lbo, sbo);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
-// both operands K-major, tile M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// tile M x N; operands K-major unless mn_major (then both MN-major).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool mn_major = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (1u << 15) | (1u << 16) : 0u) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 }  // namespace

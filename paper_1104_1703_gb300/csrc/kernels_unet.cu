@@ -48,6 +48,17 @@ struct ConvSmemHeader {
 
 __device__ __forceinline__ int conv_units(const ConvArgs& a) { return 27 * (a.cin / (8 * a.kc)); }
 
+}  // namespace
+
+// TMEM columns of a convolution CTA: two FP32 accumulators of cout columns,
+// rounded up to the power of two the allocator takes.
+__host__ __device__ uint32_t conv_tmem_cols(int cout) {
+  const int c = 2 * cout;
+  return c <= 32 ? 32u : (c <= 64 ? 64u : (c <= 128 ? 128u : (c <= 256 ? 256u : 512u)));
+}
+
+namespace {
+
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv_kernel(const __grid_constant__ CUtensorMap map, ConvArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -61,7 +72,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const int units = conv_units(a);
   const int upt = a.cin / (8 * a.kc);
   const uint32_t acc_cols = (uint32_t)a.cout;
-  const uint32_t tcols = acc_cols * 2 <= 32 ? 32u : (acc_cols * 2 <= 64 ? 64u : (acc_cols * 2 <= 128 ? 128u : 256u));
+  const uint32_t tcols = conv_tmem_cols(a.cout);
   if (threadIdx.x == 0) {
     for (int i = 0; i < kConvStages; ++i) {
       mbar_init(&S.full[i], 1);
@@ -273,10 +284,7 @@ size_t conv_smem_bytes(int cin, int cout, int kc) {
   return 1024 + (size_t)kConvStages * ((size_t)kc * 2048 + (size_t)kc * cout * 16) + 32768;
 }
 
-uint32_t conv_tmem_cols(int cout) {
-  const int c = 2 * cout;
-  return c <= 32 ? 32u : (c <= 64 ? 64u : (c <= 128 ? 128u : 256u));
-}
+
 
 cudaError_t init_conv_kernel(size_t smem_bytes) {
   return cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -481,6 +489,401 @@ cudaError_t launch_tensor_to_natural(const __nv_bfloat16* t, int stride, int off
                                      cudaStream_t s) {
   count_launch();
   tensor_to_natural_kernel<<<ew_grid((long long)c * V), 256, 0, s>>>(t, stride, off, c, V, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gbmg
+
+// ---------------------------------------------------------------------------
+// Backward pass: weight gradients on the tensor cores, and the element-wise
+// and reduction kernels
+// ---------------------------------------------------------------------------
+//
+// Weight gradient of a convolution: dW[o][i][tap] = sum over voxels v of
+// g[v][o] x[v + offset(tap)][i], with g the gradient of the pre-activation
+// and x the layer's input (zero outside the grid).  As a GEMM: rows (tap, i)
+// of the tap-major row space (27 x cin rows), columns o, K = the voxels.  A
+// CTA takes 128 rows and a range of voxel tiles: per tile, the 16 channel
+// octets of its rows are 16 TMA copies of the input tile shifted by each
+// octet's tap (box 8 channels x the tile), landing as [octet][voxel][8],
+// and g's tile is one copy, [o-octet][voxel][8]; both are the canonical
+// MN-major layout (8 voxels x 8 channels per 128-byte core matrix, 128 bytes
+// apart along K = voxels, 2048 bytes apart along M or N), so the MMA reads
+// them as they land.  The 128 x cout FP32 accumulator stays in TMEM over the
+// CTA's voxel range and is written once as the CTA's partial sum; a second
+// kernel adds the partials in a fixed order.
+
+namespace gbmg {
+
+namespace {
+
+constexpr int kWgStages = 3;
+
+struct WgSmemHeader {
+  unsigned long long full[kWgStages];
+  unsigned long long empty[kWgStages];
+  unsigned long long accf;
+  uint32_t tmem;
+  int abort;
+  int consumed;
+};
+
+__global__ void __launch_bounds__(kConvThreads, 1)
+    wgrad_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_g, WgradArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  WgSmemHeader& S = *reinterpret_cast<WgSmemHeader*>(smem_raw);
+  const unsigned a_bytes = 16u * 2048u;
+  const unsigned b_bytes = (unsigned)a.cout * 256u;
+  unsigned char* stage_a = smem_raw + 1024;
+  unsigned char* stage_b = stage_a + kWgStages * a_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mb = blockIdx.x % a.nmblk, sp = blockIdx.x / a.nmblk;
+  const int T = a.ntx * a.nty * a.ntz;
+  const int t_lo = (int)((long long)T * sp / a.nsplit), t_hi = (int)((long long)T * (sp + 1) / a.nsplit);
+  const uint32_t tcols = a.cout <= 32 ? 32u : (a.cout <= 64 ? 64u : 128u);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWgStages; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], 1);
+    }
+    mbar_init(&S.accf, 1);
+    S.abort = 0;
+    S.consumed = 0;
+    mbar_init_fence();
+  }
+  if (warp == 1) tmem_alloc(&S.tmem, tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  volatile int* abort = &S.abort;
+  const int octets = a.cin / 8;
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int t = t_lo; t < t_hi; ++t, ++it) {
+        const int st = it % kWgStages, n = it / kWgStages;
+        if (n > 0 && !mbar_wait_bounded(&S.empty[st], (n - 1) & 1, kConvLimitNs, abort)) {
+          atomicExch(a.err, 1);
+          *abort = 1;
+          break;
+        }
+        const int tx = t % a.ntx, r = t / a.ntx, ty = r % a.nty, tz = r / a.nty;
+        const int x0 = tx * a.bx, y0 = ty * a.by, z0 = tz * a.bz;
+        fence_proxy_async();
+        mbar_expect_tx(&S.full[st], a_bytes + b_bytes);
+        for (int g = 0; g < 16; ++g) {
+          int R = mb * 16 + g;  // row octet in the tap-major row space
+          if (R >= 27 * octets) R = 27 * octets - 1;  // padding rows: any valid octet (their sums are not used)
+          const int tap = R / octets, ic = R % octets;
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          tma_load_5d(stage_a + st * a_bytes + g * 2048, &map_x, 0, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, ic,
+                      &S.full[st]);
+        }
+        tma_load_5d(stage_b + st * b_bytes, &map_g, 0, x0, y0, z0, 0, &S.full[st]);
+      }
+      if (*abort) {
+        for (int j = S.consumed; j < it; ++j) mbar_wait_bounded(&S.full[j % kWgStages], (j / kWgStages) & 1, kConvLimitNs);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(kConvTileM, a.cout, true);
+      int it = 0;
+      bool issued = false;
+      for (int t = t_lo; t < t_hi && !*abort; ++t, ++it) {
+        const int st = it % kWgStages;
+        if (!mbar_wait_bounded(&S.full[st], (it / kWgStages) & 1, kConvLimitNs, abort)) {
+          atomicExch(a.err, 1);
+          *abort = 1;
+          break;
+        }
+        S.consumed = it + 1;
+        tc_fence_after();
+        const unsigned char* A = stage_a + st * a_bytes;
+        const unsigned char* Bm = stage_b + st * b_bytes;
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint64_t ad = smem_desc_mnmajor(A + ks * 256, 128, 2048);
+          const uint64_t bd = smem_desc_mnmajor(Bm + ks * 256, 128, 2048);
+          tc_mma_f16(tmem, ad, bd, idesc, (t > t_lo || ks > 0) ? 1u : 0u);
+        }
+        tc_commit(&S.empty[st]);
+        issued = true;
+      }
+      if (!*abort) tc_commit(&S.accf);
+      else if (issued)
+        for (int j = (it > kWgStages ? it - kWgStages : 0); j < it; ++j)
+          mbar_wait_bounded(&S.empty[j % kWgStages], (j / kWgStages) & 1, kConvLimitNs);
+    }
+  } else {
+    const int q = warp & 3;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(&S.accf, 0, kConvLimitNs, abort) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      __syncwarp();
+      tc_fence_after();
+      const int row = mb * 128 + 32 * q + lane;
+      float* dst = a.partial + ((size_t)sp * a.nmblk * 128 + row) * a.cout;
+      for (int c0 = 0; c0 < a.cout; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dst[c0 + i] = v[i];
+      }
+    } else if (lane == 0) {
+      if (!*abort) atomicExch(a.err, 1);
+      *abort = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, tcols);
+}
+
+// dW[o][i][tap] (+)= sum over splits of partial[split][tap * cin_pad + i][o],
+// in split order; i < cin (the real input channels).
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nsplit, int rows, int cin_pad, int cin,
+                                    int cout, float* __restrict__ dw) {
+  const long long n = (long long)cout * cin * 27;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int tap = (int)(e % 27);
+    const long long r = e / 27;
+    const int i = (int)(r % cin), o = (int)(r / cin);
+    const size_t row = (size_t)tap * cin_pad + i;
+    float acc = 0.0f;
+    for (int s = 0; s < nsplit; ++s) acc += partial[((size_t)s * rows + row) * cout + o];
+    dw[e] = acc;
+  }
+}
+
+// Per-block partial sums over voxels of g[v][o] (bias gradient), one row of
+// partials per block; then a fixed-order reduction.
+__global__ void channel_sum_kernel(const __nv_bfloat16* __restrict__ g, int c, long long V, float* __restrict__ part) {
+  extern __shared__ float sh[];
+  for (int o = threadIdx.x; o < c; o += blockDim.x) sh[o] = 0.0f;
+  __syncthreads();
+  const long long per = (V + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(V, lo + per);
+  // each thread owns one channel and a stride of voxels
+  const int lanes = blockDim.x / c;
+  const int o = threadIdx.x % c, l = threadIdx.x / c;
+  float acc = 0.0f;
+  if (l < lanes)
+    for (long long v = lo + l; v < hi; v += lanes) acc += __bfloat162float(g[v * c + o]);
+  if (l < lanes) atomicAdd(&sh[o], acc);  // within the block only
+  __syncthreads();
+  for (int k = threadIdx.x; k < c; k += blockDim.x) part[(size_t)blockIdx.x * c + k] = sh[k];
+}
+
+__global__ void partial_rows_sum_kernel(const float* __restrict__ part, int nrows, int c, float* __restrict__ out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int r = 0; r < nrows; ++r) acc += part[(size_t)r * c + k];
+    out[k] = acc;
+  }
+}
+
+// Head backward.  g_pred (FP32, dL/dpred), act = input channel 1 > 0:
+// gz[v][i] = (top[v][i] > 0) w[i] g act (BF16), and per-block partial sums
+// of g act top[v][i] (head weights) and g act (head bias).
+__global__ void head_backward_kernel(const float* __restrict__ gp, const __nv_bfloat16* __restrict__ x0,
+                                     const __nv_bfloat16* __restrict__ top, int c, const float* __restrict__ w,
+                                     long long V, __nv_bfloat16* __restrict__ gz, float* __restrict__ part) {
+  extern __shared__ float sh[];  // [c + 1]
+  for (int k = threadIdx.x; k <= c; k += blockDim.x) sh[k] = 0.0f;
+  __syncthreads();
+  float acc_b = 0.0f;
+  float acc_w[64];
+  for (int i = 0; i < c && i < 64; ++i) acc_w[i] = 0.0f;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const float g = __bfloat162float(x0[v * 16 + 1]) > 0.0f ? gp[v] : 0.0f;
+    acc_b += g;
+    for (int i = 0; i < c; ++i) {
+      const float t = __bfloat162float(top[v * c + i]);
+      acc_w[i] += g * t;
+      gz[v * c + i] = __float2bfloat16_rn(t > 0.0f ? w[i] * g : 0.0f);
+    }
+  }
+  for (int i = 0; i < c; ++i) atomicAdd(&sh[i], acc_w[i]);
+  atomicAdd(&sh[c], acc_b);
+  __syncthreads();
+  for (int k = threadIdx.x; k <= c; k += blockDim.x) part[(size_t)blockIdx.x * (c + 1) + k] = sh[k];
+}
+
+// Gradient through nearest upsampling: dst[v][i] = sum over the 8 children of
+// src[child][so + i] (src at twice the size), FP32 sum rounded to BF16.
+__global__ void upsample_backward_kernel(const __nv_bfloat16* __restrict__ src, int ss, int so, int W, int H, int D,
+                                         int c, __nv_bfloat16* __restrict__ dst) {
+  const long long n = (long long)W * H * D * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % c);
+    const long long v = e / c;
+    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((long long)W * H));
+    float acc = 0.0f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const long long vs = ((long long)(2 * z + dz) * (2 * H) + (2 * y + dy)) * (2 * W) + (2 * x + dx);
+          acc += __bfloat162float(src[vs * ss + so + i]);
+        }
+    dst[e] = __float2bfloat16_rn(acc);
+  }
+}
+
+// Gradient of a down level's second convolution output that feeds both the
+// concatenation (skip, already masked) and the pooling of the level below:
+// gz[v][i] = skip[v][i] + (act[v][i] > 0) gpool[parent][i] / 8.
+__global__ void skip_pool_combine_kernel(const __nv_bfloat16* __restrict__ skip, int ss,
+                                         const __nv_bfloat16* __restrict__ act, int as,
+                                         const __nv_bfloat16* __restrict__ gpool, int W, int H, int D, int c,
+                                         __nv_bfloat16* __restrict__ gz) {
+  const long long n = (long long)W * H * D * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % c);
+    const long long v = e / c;
+    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((long long)W * H));
+    const long long vp = ((long long)(z >> 1) * (H / 2) + (y >> 1)) * (W / 2) + (x >> 1);
+    const float a = __bfloat162float(act[v * as + i]);
+    const float gpv = a > 0.0f ? 0.125f * __bfloat162float(gpool[vp * c + i]) : 0.0f;
+    gz[e] = __float2bfloat16_rn(__bfloat162float(skip[v * ss + i]) + gpv);
+  }
+}
+
+// Loss and its gradient (relative squared error over the active cells):
+// per-block partials of sum act y^2 and sum act (p - y)^2 ...
+__global__ void loss_partials_kernel(const float* __restrict__ p, const float* __restrict__ y,
+                                     const __nv_bfloat16* __restrict__ x0, long long V, double* __restrict__ part) {
+  double den = 0.0, num = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    if (!(__bfloat162float(x0[v * 16 + 1]) > 0.0f)) continue;
+    const double yy = y[v], d = (double)p[v] - yy;
+    den += yy * yy;
+    num += d * d;
+  }
+  __shared__ double sd[256], sn[256];
+  sd[threadIdx.x] = den;
+  sn[threadIdx.x] = num;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sd[0];
+    part[2 * blockIdx.x + 1] = sn[0];
+  }
+}
+
+// ... summed in a fixed order: out[0] = den, out[1] = num
+__global__ void loss_finalize_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double d = 0.0, n = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      d += part[2 * b];
+      n += part[2 * b + 1];
+    }
+    out[0] = d;
+    out[1] = n;
+  }
+}
+
+// g[v] = 2 act (p - y) / den
+__global__ void loss_grad_kernel(const float* __restrict__ p, const float* __restrict__ y,
+                                 const __nv_bfloat16* __restrict__ x0, long long V, const double* __restrict__ sums,
+                                 float* __restrict__ g) {
+  const double den = sums[0];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const bool act = __bfloat162float(x0[v * 16 + 1]) > 0.0f;
+    g[v] = act && den > 0.0 ? (float)(2.0 * ((double)p[v] - (double)y[v]) / den) : 0.0f;
+  }
+}
+
+// Adam (Kingma & Ba, Algorithm 1) on the flat FP32 parameters; bc1 = 1 -
+// beta1^t, bc2 = 1 - beta2^t.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float gg = g[e];
+    const float mm = b1 * m[e] + (1.0f - b1) * gg;
+    const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+  }
+}
+
+}  // namespace
+
+size_t wgrad_smem_bytes(int cout) { return 1024 + (size_t)kWgStages * (16 * 2048 + (size_t)cout * 256); }
+
+cudaError_t init_wgrad_kernel(size_t smem_bytes) {
+  return cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+cudaError_t launch_wgrad(const CUtensorMap& mx, const CUtensorMap& mg, const WgradArgs& a, cudaStream_t s) {
+  count_launch();
+  wgrad_kernel<<<a.nmblk * a.nsplit, kConvThreads, wgrad_smem_bytes(a.cout), s>>>(mx, mg, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad_reduce(const float* partial, int nsplit, int rows, int cin_pad, int cin, int cout, float* dw,
+                                cudaStream_t s) {
+  count_launch();
+  wgrad_reduce_kernel<<<ew_grid((long long)cout * cin * 27), 256, 0, s>>>(partial, nsplit, rows, cin_pad, cin, cout, dw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bias_grad(const __nv_bfloat16* g, int c, long long V, float* part, int nblocks, float* db,
+                             cudaStream_t s) {
+  count_launch(2);
+  channel_sum_kernel<<<nblocks, 256, sizeof(float) * c, s>>>(g, c, V, part);
+  partial_rows_sum_kernel<<<1, 256, 0, s>>>(part, nblocks, c, db);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head_backward(const float* gp, const __nv_bfloat16* x0, const __nv_bfloat16* top, int c,
+                                 const float* w, long long V, __nv_bfloat16* gz, float* part, int nblocks, float* dwb,
+                                 cudaStream_t s) {
+  count_launch(2);
+  head_backward_kernel<<<nblocks, 256, sizeof(float) * (c + 1), s>>>(gp, x0, top, c, w, V, gz, part);
+  partial_rows_sum_kernel<<<1, 256, 0, s>>>(part, nblocks, c + 1, dwb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample_backward(const __nv_bfloat16* src, int ss, int so, int W, int H, int D, int c,
+                                     __nv_bfloat16* dst, cudaStream_t s) {
+  count_launch();
+  upsample_backward_kernel<<<ew_grid((long long)W * H * D * c), 256, 0, s>>>(src, ss, so, W, H, D, c, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skip_pool_combine(const __nv_bfloat16* skip, int ss, const __nv_bfloat16* act, int as,
+                                     const __nv_bfloat16* gpool, int W, int H, int D, int c, __nv_bfloat16* gz,
+                                     cudaStream_t s) {
+  count_launch();
+  skip_pool_combine_kernel<<<ew_grid((long long)W * H * D * c), 256, 0, s>>>(skip, ss, act, as, gpool, W, H, D, c, gz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const float* p, const float* y, const __nv_bfloat16* x0, long long V, double* part, int nblocks,
+                        double* sums, float* g, cudaStream_t s) {
+  count_launch(3);
+  loss_partials_kernel<<<nblocks, 256, 0, s>>>(p, y, x0, V, part);
+  loss_finalize_kernel<<<1, 32, 0, s>>>(part, nblocks, sums);
+  loss_grad_kernel<<<ew_grid(V), 256, 0, s>>>(p, y, x0, V, sums, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t s) {
+  count_launch();
+  adam_kernel<<<ew_grid(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
   return cudaGetLastError();
 }
 

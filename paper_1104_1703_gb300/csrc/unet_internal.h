@@ -24,7 +24,7 @@ constexpr int kConvTileM = 128;    // voxels per output tile (the MMA's M)
 // unit is one tap and `kc` 8-channel chunks of the input.
 struct ConvArgs {
   int W, H, D;           // spatial size of input and output
-  int cin, cout;         // channels, multiples of 16; cout <= 128
+  int cin, cout;         // channels, multiples of 16; cout <= 256
   int kc;                // 8-channel chunks per unit (even, divides cin / 8, <= 8)
   int bx, by, bz;        // the output tile's box (bx * by * bz = 128)
   int ntx, nty, ntz;     // tiles per axis
@@ -41,7 +41,7 @@ struct ConvArgs {
 };
 
 size_t conv_smem_bytes(int cin, int cout, int kc);
-uint32_t conv_tmem_cols(int cout);
+__host__ __device__ uint32_t conv_tmem_cols(int cout);
 int conv_kc(int cin);
 cudaError_t init_conv_kernel(size_t smem_bytes);
 // `map` describes the input tensor: dims (8, W, H, D, cin / 8), box
@@ -59,6 +59,42 @@ int conv_grid(const ConvArgs& a, size_t smem_bytes);
 // channels exchanged, [27][cout / 8][cin_pad][8].
 cudaError_t launch_pack_weights(const float* w, int cout, int cin, int cin_pad, bool backward, __nv_bfloat16* out,
                                 cudaStream_t s);
+
+// Weight gradient of one convolution (see kernels_unet.cu): CTA
+// (mblock, split) sums the voxel tiles [T split / nsplit, T (split+1) /
+// nsplit) into partial[split][mblock * 128 + row][o], rows (tap, i) of the
+// tap-major row space of cin (padded) input channels.
+struct WgradArgs {
+  int W, H, D;
+  int cin;     // padded input channels (the input tensor's channels), multiple of 16
+  int cout;    // output channels, multiple of 16, <= 128
+  int bx, by, bz, ntx, nty, ntz;
+  int nmblk;   // ceil(27 cin / 128)
+  int nsplit;  // <= the number of voxel tiles
+  float* partial;
+  int* err;
+};
+size_t wgrad_smem_bytes(int cout);
+cudaError_t init_wgrad_kernel(size_t smem_bytes);
+// mx: the input tensor with box (8, bx, by, bz, 1); mg: the gradient tensor
+// (cout channels) with box (8, bx, by, bz, cout / 8)
+cudaError_t launch_wgrad(const CUtensorMap& mx, const CUtensorMap& mg, const WgradArgs& a, cudaStream_t s);
+cudaError_t launch_wgrad_reduce(const float* partial, int nsplit, int rows, int cin_pad, int cin, int cout, float* dw,
+                                cudaStream_t s);
+cudaError_t launch_bias_grad(const __nv_bfloat16* g, int c, long long V, float* part, int nblocks, float* db,
+                             cudaStream_t s);
+cudaError_t launch_head_backward(const float* gp, const __nv_bfloat16* x0, const __nv_bfloat16* top, int c,
+                                 const float* w, long long V, __nv_bfloat16* gz, float* part, int nblocks, float* dwb,
+                                 cudaStream_t s);
+cudaError_t launch_upsample_backward(const __nv_bfloat16* src, int ss, int so, int W, int H, int D, int c,
+                                     __nv_bfloat16* dst, cudaStream_t s);
+cudaError_t launch_skip_pool_combine(const __nv_bfloat16* skip, int ss, const __nv_bfloat16* act, int as,
+                                     const __nv_bfloat16* gpool, int W, int H, int D, int c, __nv_bfloat16* gz,
+                                     cudaStream_t s);
+cudaError_t launch_loss(const float* p, const float* y, const __nv_bfloat16* x0, long long V, double* part, int nblocks,
+                        double* sums, float* g, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t s);
 
 cudaError_t launch_input_to_bf16(const float* x, long long V, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_avg_pool(const __nv_bfloat16* src, int ss, int so, int W, int H, int D, int c, __nv_bfloat16* dst,

@@ -125,3 +125,69 @@ def test_params_round_trip(dev):
     back = net.get_params()
     assert back.shape == f.shape
     np.testing.assert_allclose(back, f.astype(np.float32).astype(np.float64), rtol=0, atol=0)
+
+
+def _grad_case(levels, n, seed):
+    P = _params(levels, 16, seed)
+    x = _input(n, seed + 2)
+    g = np.random.default_rng(seed + 3).normal(size=(n, n, n)).astype(np.float32)
+    net = B.UNet(levels, 16, (n, n, n))
+    net.set_params(flat(P))
+    net.forward(x)
+    net.backward(g)
+    G = net.get_grads()
+    Pb = {k: (bf16(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in P.items()}
+    _, cache = U.forward(Pb, bf16(x))
+    Gr = U.backward(Pb, cache, g[None].astype(np.float64))
+    return P, net, G, Gr
+
+
+@pytest.mark.parametrize("levels,n", [(1, 16), (2, 16), (3, 16), (4, 32)])
+def test_gradients_match_the_oracle(dev, levels, n):
+    P, net, G, Gr = _grad_case(levels, n, 40 + levels)
+    ref = flat({k: Gr[k] for k in P})
+    assert G.shape == ref.shape
+    err = np.linalg.norm(G - ref) / np.linalg.norm(ref)
+    assert err < 3e-2, err
+    k0 = 0
+    for k in P:
+        size = P[k].size
+        got, want = G[k0:k0 + size], Gr[k].ravel()
+        k0 += size
+        if k.endswith(".w"):
+            e = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert e < 1e-1, (k, e)
+
+
+def test_adam_step_matches_the_oracle(dev):
+    P, net, G, _ = _grad_case(2, 16, 50)
+    theta0 = net.get_params()
+    net.adam_step(lr=1e-3)
+    theta1 = net.get_params()
+    Q = {}
+    k0 = 0
+    for k in P:
+        Q[k] = theta0[k0:k0 + P[k].size].reshape(P[k].shape).copy()
+        k0 += P[k].size
+    Gd, k0 = {}, 0
+    for k in P:
+        Gd[k] = G[k0:k0 + P[k].size].reshape(P[k].shape)
+        k0 += P[k].size
+    U.adam_step(Q, Gd, {}, lr=1e-3)
+    want = flat(Q)
+    np.testing.assert_allclose(theta1 - theta0, want - theta0, rtol=1e-4, atol=1e-9)
+
+
+def test_training_reduces_the_loss_on_a_fixed_sample(dev):
+    n = 16
+    P = _params(2, 16, 60)
+    rng = np.random.default_rng(61)
+    x = _input(n, 62)
+    y = (rng.normal(size=(n, n, n)) * (x[1] > 0)).astype(np.float32)
+    net = B.UNet(2, 16, (n, n, n))
+    net.set_params(flat(P))
+    pred = net.forward(x).astype(np.float64)
+    loss_ref, _ = U.loss_and_grad(pred, y.astype(np.float64), x[1])
+    losses = [net.train_step(x, y, lr=3e-3) for _ in range(40)]
+    assert losses[0] == pytest.approx(loss_ref, rel=1e-5)
+    assert losses[-1] < 0.6 * losses[0], losses
