@@ -463,6 +463,9 @@ mg_status mg_unet_train_step(mg_unet* net, const float* x, const float* y, mg_me
  * forward pass, [c][d][h][w] FP32; dims4 = {c, d, h, w}.  For verification. */
 mg_status mg_unet_layer_info(const mg_unet* net, int layer, int* dims4);
 mg_status mg_unet_layer_output(mg_unet* net, int layer, float* out, mg_mem where);
+/* The gradient of the loss w.r.t. convolution `layer`'s pre-activation after
+ * the last backward pass, same shape as its output.  For verification. */
+mg_status mg_unet_layer_grad(mg_unet* net, int layer, float* out, mg_mem where);
 const char* mg_unet_last_error(const mg_unet* net);
 
 /* ---------------------------------------------------------------------------

@@ -110,6 +110,7 @@ SIGNATURES = {
     "mg_unet_train_step": (_i, [_vp, _vp, _vp, _i, _d, _vp]),
     "mg_unet_layer_info": (_i, [_vp, _i, _vp]),
     "mg_unet_layer_output": (_i, [_vp, _i, _vp, _i]),
+    "mg_unet_layer_grad": (_i, [_vp, _i, _vp, _i]),
     "mg_unet_last_error": (ctypes.c_char_p, [_vp]),
 }
 
@@ -737,6 +738,14 @@ class UNet:
         loss = _d()
         _check_unet(lib().mg_unet_train_step(self.handle, px, py, wx, float(lr), ctypes.byref(loss)), self.handle)
         return loss.value
+
+    def layer_grad(self, layer):
+        dims = (_i * 4)()
+        _check_unet(lib().mg_unet_layer_info(self.handle, int(layer), dims), self.handle)
+        out = np.zeros(tuple(dims[:4]), dtype=np.float32)
+        _check_unet(lib().mg_unet_layer_grad(self.handle, int(layer), out.ctypes.data_as(_vp), MG_MEM_HOST),
+                    self.handle)
+        return out
 
     def layer_output(self, layer):
         dims = (_i * 4)()

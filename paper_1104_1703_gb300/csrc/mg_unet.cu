@@ -740,6 +740,17 @@ mg_status mg_unet_layer_output(mg_unet* N, int layer, float* out, mg_mem where) 
   return copy_io(N, out, N->nat, sizeof(float) * n, false, where);
 }
 
+mg_status mg_unet_layer_grad(mg_unet* N, int layer, float* out, mg_mem where) {
+  if (!N || !out) return ufail(N, MG_ERR_INVALID_ARG, "null argument");
+  if (layer < 0 || layer >= (int)N->convs.size()) return ufail(N, MG_ERR_INVALID_ARG, "layer out of range");
+  UGuard g(N->device);
+  const Tensor& t = N->convs[layer].gz;
+  const size_t n = (size_t)t.c * t.voxels();
+  if (n > N->nat_elems) return ufail(N, MG_ERR_INTERNAL, "read-back staging too small");
+  UCK(N, launch_tensor_to_natural(t.p, t.stride, t.off, t.c, t.voxels(), N->nat, N->stream));
+  return copy_io(N, out, N->nat, sizeof(float) * n, false, where);
+}
+
 mg_status mg_unet_layer_info(const mg_unet* N, int layer, int* dims4) {
   if (!N || !dims4) return ufail(nullptr, MG_ERR_INVALID_ARG, "null argument");
   if (layer < 0 || layer >= (int)N->convs.size()) return ufail(nullptr, MG_ERR_INVALID_ARG, "layer out of range");

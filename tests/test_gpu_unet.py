@@ -136,31 +136,111 @@ def _grad_case(levels, n, seed):
     net.forward(x)
     net.backward(g)
     G = net.get_grads()
+    return P, x, g, net, G
+
+
+def _own_cache(levels, P, x, net):
+    """The oracle's forward cache rebuilt from the network's own BF16
+    activations (each layer's input and its ReLU output, whose sign gives the
+    same mask as the pre-activation)."""
+    names = _names(levels)
+    out = {nm: net.layer_output(i).astype(np.float64) for i, nm in enumerate(names)}
+    cache = {"x": bf16(x), "act": (x[1:2] > 0).astype(np.float64)}
+    for nm in names:
+        l, j = int(nm[-3]), int(nm[-1])
+        if nm.startswith("down"):
+            inp = out["down%d.0" % l] if j == 1 else (bf16(x) if l == 0 else bf16(_pool(out["down%d.1" % (l - 1)])))
+        elif j == 1:
+            inp = out["up%d.0" % l]
+        else:
+            below = out["down%d.1" % (levels - 1)] if l == levels - 2 else out["up%d.1" % (l + 1)]
+            inp = np.concatenate([out["down%d.1" % l], U.upsample2(below)], axis=0)
+        cache[nm + ".in"] = inp
+        cache[nm + ".z"] = out[nm]
+    cache["head.in"] = out["up0.1" if levels > 1 else "down0.1"]
+    return cache, out
+
+
+def _split(P, G):
+    d, k0 = {}, 0
+    for k in P:
+        d[k] = G[k0:k0 + P[k].size].reshape(P[k].shape)
+        k0 += P[k].size
+    return d
+
+
+@pytest.mark.parametrize("levels,n", [(2, 16), (3, 16)])
+def test_each_backward_step_matches_the_oracle(dev, levels, n):
+    """Per layer, on the network's own tensors: the weight and bias
+    gradients are the oracle's convolution backward of the layer's input and
+    pre-activation gradient (FP32 sums of BF16 products: relative 1e-5), the
+    pre-activation gradient of the layer below is its backward-data output
+    times the ReLU mask (one BF16 rounding), and the head, upsampling and
+    pooling gradients likewise."""
+    P, x, g, net, G = _grad_case(levels, n, 70 + levels)
     Pb = {k: (bf16(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in P.items()}
-    _, cache = U.forward(Pb, bf16(x))
-    Gr = U.backward(Pb, cache, g[None].astype(np.float64))
-    return P, net, G, Gr
+    cache, out = _own_cache(levels, P, x, net)
+    names = _names(levels)
+    gz = {nm: net.layer_grad(i).astype(np.float64) for i, nm in enumerate(names)}
+    Gd = _split(P, G)
+
+    def close(got, want, what):
+        bound = 2.0 ** -8 * np.abs(want) + 2e-3 * np.abs(want).max()
+        assert not (np.abs(got - want) > bound).any(), (what, float(np.abs(got - want).max()))
+
+    top = cache["head.in"]
+    w_h = P["head.w"].ravel()
+    close(gz["up0.1"], (top > 0) * w_h[:, None, None, None] * (g * (x[1] > 0))[None], "head")
+    for nm in names:
+        l, j = int(nm[-3]), int(nm[-1])
+        gx, gw, gb = U.conv3d_backward(cache[nm + ".in"], Pb[nm + ".w"], gz[nm])
+        assert np.linalg.norm(Gd[nm + ".w"] - gw) <= 1e-5 * np.linalg.norm(gw), nm
+        assert np.linalg.norm(Gd[nm + ".b"] - gb) <= 1e-5 * np.linalg.norm(gb) + 1e-12, nm
+        if j == 1:
+            lower = nm[:-1] + "0"
+            close(gz[lower], gx * (out[lower] > 0), nm + " backward data")
+        elif nm.startswith("up"):
+            gcat = gx * (cache[nm + ".in"] > 0)
+            c = out["down%d.1" % l].shape[0]
+            below = "down%d.1" % (levels - 1) if l == levels - 2 else "up%d.1" % (l + 1)
+            close(gz[below], U.upsample2_backward(gcat[c:]), nm + " upsampling backward")
+            gx1, _, _ = U.conv3d_backward(cache["down%d.0.in" % (l + 1)], Pb["down%d.0.w" % (l + 1)],
+                                          gz["down%d.0" % (l + 1)])
+            close(gz["down%d.1" % l], gcat[:c] + U.avg_pool2_backward(gx1) * (out["down%d.1" % l] > 0),
+                  nm + " skip and pooling backward")
 
 
 @pytest.mark.parametrize("levels,n", [(1, 16), (2, 16), (3, 16), (4, 32)])
-def test_gradients_match_the_oracle(dev, levels, n):
-    P, net, G, Gr = _grad_case(levels, n, 40 + levels)
+def test_gradients_match_the_oracle_on_the_networks_activations(dev, levels, n):
+    """The whole gradient against the oracle's backward pass on the
+    network's own forward activations: the remaining differences are the
+    BF16 roundings of the gradient tensors (relative L2 <= 2e-2)."""
+    P, x, g, net, G = _grad_case(levels, n, 40 + levels)
+    Pb = {k: (bf16(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in P.items()}
+    cache, _ = _own_cache(levels, P, x, net)
+    Gr = U.backward(Pb, cache, g[None].astype(np.float64))
     ref = flat({k: Gr[k] for k in P})
-    assert G.shape == ref.shape
     err = np.linalg.norm(G - ref) / np.linalg.norm(ref)
-    assert err < 3e-2, err
-    k0 = 0
-    for k in P:
-        size = P[k].size
-        got, want = G[k0:k0 + size], Gr[k].ravel()
-        k0 += size
-        if k.endswith(".w"):
-            e = np.linalg.norm(got - want) / np.linalg.norm(want)
-            assert e < 1e-1, (k, e)
+    assert err < 2e-2, err
+
+
+@pytest.mark.parametrize("levels,n", [(2, 16), (4, 32)])
+def test_gradients_near_the_fp64_network(dev, levels, n):
+    """Against the oracle's own FP64 forward and backward: about 1% of the
+    ReLU masks differ between BF16 and FP64 activations, and gradient sums
+    that mostly cancel magnify that to several per cent; the gradient keeps
+    its direction."""
+    P, x, g, net, G = _grad_case(levels, n, 40 + levels)
+    Pb = {k: (bf16(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in P.items()}
+    _, cache = U.forward(Pb, bf16(x))
+    Gr = U.backward(Pb, cache, g[None].astype(np.float64))
+    ref = flat({k: Gr[k] for k in P})
+    assert np.linalg.norm(G - ref) / np.linalg.norm(ref) < 0.2
+    assert np.dot(G, ref) / np.dot(ref, ref) > 0.9
 
 
 def test_adam_step_matches_the_oracle(dev):
-    P, net, G, _ = _grad_case(2, 16, 50)
+    P, _, _, net, G = _grad_case(2, 16, 50)
     theta0 = net.get_params()
     net.adam_step(lr=1e-3)
     theta1 = net.get_params()
