@@ -266,13 +266,12 @@ def test_adam_step_matches_the_oracle(dev):
 def test_training_reduces_the_loss_on_a_fixed_sample(dev):
     n = 16
     P = _params(2, 16, 60)
-    rng = np.random.default_rng(61)
     x = _input(n, 62)
-    y = (rng.normal(size=(n, n, n)) * (x[1] > 0)).astype(np.float32)
+    y = (x[0] * (x[1] > 0)).astype(np.float32)  # a target the convolutions can represent
     net = B.UNet(2, 16, (n, n, n))
     net.set_params(flat(P))
     pred = net.forward(x).astype(np.float64)
     loss_ref, _ = U.loss_and_grad(pred, y.astype(np.float64), x[1])
-    losses = [net.train_step(x, y, lr=3e-3) for _ in range(40)]
+    losses = [net.train_step(x, y, lr=1e-3) for _ in range(60)]
     assert losses[0] == pytest.approx(loss_ref, rel=1e-5)
-    assert losses[-1] < 0.6 * losses[0], losses
+    assert losses[-1] < 0.3 * losses[0], losses
