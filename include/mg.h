@@ -187,6 +187,16 @@ mg_status mg_set_dirichlet(mg_hierarchy* hier, const double* bx, const double* b
 mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* hier, const double* phi_c, mg_mem where, int cnx,
                                        int cny, int cnz, int ox, int oy, int oz);
 
+/* The values mg_set_dirichlet_from_coarse would fold, as face arrays in
+ * mg_set_dirichlet's layout: each boundary face of the hierarchy's active
+ * domain gets the coarse potential trilinearly interpolated at its centre
+ * (Section 1 one-way interface); every other face is 0.  bx, by, bz are
+ * device buffers of the hierarchy's GPU ((nx+1) ny nz, nx (ny+1) nz,
+ * nx ny (nz+1) doubles).  Errors: INVALID_ARG (including a boundary face
+ * outside the coarse cell centres), CUDA. */
+mg_status mg_faces_from_coarse(mg_hierarchy* hier, const double* phi_c, mg_mem where, int cnx, int cny, int cnz, int ox,
+                               int oy, int oz, double* bx, double* by, double* bz);
+
 /* Initial guess (NULL = 0) and read-back of the fine solution, nx*ny*nz.
  * Errors: INVALID_ARG, CUDA. */
 mg_status mg_set_solution(mg_hierarchy* hier, const double* phi, mg_mem where);
@@ -459,6 +469,28 @@ mg_status mg_unet_adam_step(mg_unet* net, double lr, double beta1, double beta2,
  * beta2 0.999, eps 1e-8).  loss (nullable) receives the loss before the
  * update.  Errors: INVALID_ARG, CUDA, INTERNAL. */
 mg_status mg_unet_train_step(mg_unet* net, const float* x, const float* y, mg_mem where, double lr, double* loss);
+/* The network's input channels for one patch of the network's grid size,
+ * from device buffers: mask (int8), rho (double) and the Dirichlet face
+ * arrays bx, by, bz of mg_set_dirichlet's layout (nullable = 0); h the cell
+ * size.  Channel 0 is h^2 n^2 rho / s on active cells (n the largest grid
+ * size), channel 1 is +1 on active and -1 on inactive cells, channel 2 the
+ * mean Dirichlet value over the cell's boundary faces / s (0 without
+ * boundary faces), with s the root of the mean square of channel 0's
+ * numerator over active cells plus that of the boundary-face values (so
+ * scaling rho and the boundary values together leaves the channels alone).
+ * x (nullable) receives [3][nz][ny][nx] FP32, scale (nullable, host) s. */
+mg_status mg_unet_features(mg_unet* net, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                           const double* bz, double h, float* x, mg_mem where, double* scale);
+/* The learned initial guess: phi (device, [nz][ny][nx] doubles) = s times
+ * the network's prediction from the patch's input channels.  Enqueued on the
+ * network's stream.  Errors: INVALID_ARG, CUDA. */
+mg_status mg_unet_predict(mg_unet* net, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                          const double* bz, double h, double* phi);
+/* One training step on a solved patch: target phi / s (phi device, the
+ * patch's solution), then as mg_unet_train_step.  Errors: INVALID_ARG, CUDA,
+ * INTERNAL. */
+mg_status mg_unet_train_patch(mg_unet* net, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                              const double* bz, double h, const double* phi, double lr, double* loss);
 /* The ReLU output of convolution `layer` (parameter order) after the last
  * forward pass, [c][d][h][w] FP32; dims4 = {c, d, h, w}.  For verification. */
 mg_status mg_unet_layer_info(const mg_unet* net, int layer, int* dims4);
@@ -467,6 +499,19 @@ mg_status mg_unet_layer_output(mg_unet* net, int layer, float* out, mg_mem where
  * the last backward pass, same shape as its output.  For verification. */
 mg_status mg_unet_layer_grad(mg_unet* net, int layer, float* out, mg_mem where);
 const char* mg_unet_last_error(const mg_unet* net);
+
+/* Synthetic AMR patch on the GPU (input synthesis for training and
+ * evaluating the learned guess; no part of the method): the blob-patch
+ * recipe, a mask from white noise (SplitMix64 stream of `seed`, Box-Muller)
+ * smoothed by a periodic Gaussian of corr_cells cells and thresholded at 0,
+ * rho ~ U[-1, 1], and a coarse potential of 6 random low Fourier modes on
+ * ((nz+1)/2+2) x ((ny+1)/2+2) x ((nx+1)/2+2) cells (origin -2 in fine-cell
+ * units).  Device buffers: scratch 2 nx ny nz + 8 corr_cells + 2 floats,
+ * mask nx ny nz int8, rho nx ny nz doubles, phi_c the coarse grid.  Sizes
+ * 1..2048, corr_cells in (0, 64].  Enqueued on cuda_stream.
+ * Errors (mg_last_error(NULL)): INVALID_ARG, CUDA. */
+mg_status mg_generate_blob_patch(unsigned long long seed, int nx, int ny, int nz, double corr_cells, float* scratch,
+                                 int8_t* mask, double* rho, double* phi_c, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation

@@ -104,6 +104,11 @@ SIGNATURES = {
     "mg_unet_set_params": (_i, [_vp, _vp, _i]),
     "mg_unet_get_params": (_i, [_vp, _vp, _i]),
     "mg_unet_forward": (_i, [_vp, _vp, _i, _vp, _i]),
+    "mg_unet_features": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _i, _vp]),
+    "mg_unet_predict": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "mg_unet_train_patch": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp]),
+    "mg_faces_from_coarse": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "mg_generate_blob_patch": (_i, [ctypes.c_ulonglong, _i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp]),
     "mg_unet_backward": (_i, [_vp, _vp, _i]),
     "mg_unet_get_grads": (_i, [_vp, _vp, _i]),
     "mg_unet_adam_step": (_i, [_vp, _d, _d, _d, _d]),
@@ -399,6 +404,9 @@ def mg_timing_read(h):
 
 class Hierarchy:
     """Owns one handle; methods forward to the functions above."""
+
+    def faces_from_coarse(self, phi_c, origin, bx, by, bz):
+        mg_faces_from_coarse(self.handle, phi_c, origin, bx, by, bz)
 
     def __init__(self, mask, h, options=None, stream="auto", **opts):
         if options is None and opts:
@@ -739,6 +747,41 @@ class UNet:
         _check_unet(lib().mg_unet_train_step(self.handle, px, py, wx, float(lr), ctypes.byref(loss)), self.handle)
         return loss.value
 
+    @staticmethod
+    def _dev(a, name):
+        if a is None:
+            return None
+        if not (_is_torch(a) and a.is_cuda and a.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA tensor" % name)
+        return _vp(a.data_ptr())
+
+    def features(self, mask, rho, faces, h):
+        """(x [3][nz][ny][nx] float32 numpy, scale s) of a patch given as CUDA
+        tensors (faces a (bx, by, bz) tuple, entries may be None)."""
+        x = np.zeros((3,) + self.shape, dtype=np.float32)
+        s = _d()
+        bx, by, bz = faces
+        _check_unet(lib().mg_unet_features(self.handle, self._dev(mask, "mask"), self._dev(rho, "rho"),
+                                           self._dev(bx, "bx"), self._dev(by, "by"), self._dev(bz, "bz"), float(h),
+                                           x.ctypes.data_as(_vp), MG_MEM_HOST, ctypes.byref(s)), self.handle)
+        return x, s.value
+
+    def predict(self, mask, rho, faces, h, phi_out):
+        """Writes the learned guess into phi_out (a float64 CUDA tensor)."""
+        bx, by, bz = faces
+        _check_unet(lib().mg_unet_predict(self.handle, self._dev(mask, "mask"), self._dev(rho, "rho"),
+                                          self._dev(bx, "bx"), self._dev(by, "by"), self._dev(bz, "bz"), float(h),
+                                          self._dev(phi_out, "phi")), self.handle)
+        return phi_out
+
+    def train_patch(self, mask, rho, faces, h, phi, lr=1e-3):
+        bx, by, bz = faces
+        loss = _d()
+        _check_unet(lib().mg_unet_train_patch(self.handle, self._dev(mask, "mask"), self._dev(rho, "rho"),
+                                              self._dev(bx, "bx"), self._dev(by, "by"), self._dev(bz, "bz"), float(h),
+                                              self._dev(phi, "phi"), float(lr), ctypes.byref(loss)), self.handle)
+        return loss.value
+
     def layer_grad(self, layer):
         dims = (_i * 4)()
         _check_unet(lib().mg_unet_layer_info(self.handle, int(layer), dims), self.handle)
@@ -754,3 +797,28 @@ class UNet:
         _check_unet(lib().mg_unet_layer_output(self.handle, int(layer), out.ctypes.data_as(_vp), MG_MEM_HOST),
                     self.handle)
         return out
+
+
+def mg_faces_from_coarse(h, phi_c, origin, bx, by, bz):
+    """Writes the interpolated Dirichlet values of hierarchy h's boundary
+    faces into the CUDA tensors bx, by, bz."""
+    cz, cy, cx = phi_c.shape
+    p, where, keep = _in(phi_c, np.float64, (cz, cy, cx), "phi_c")
+    for name, a in (("bx", bx), ("by", by), ("bz", bz)):
+        if not (_is_torch(a) and a.is_cuda and a.is_contiguous() and a.dtype == __import__("torch").float64):
+            raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    _check(lib().mg_faces_from_coarse(h, p, where, cx, cy, cz, int(origin[0]), int(origin[1]), int(origin[2]),
+                                      _vp(bx.data_ptr()), _vp(by.data_ptr()), _vp(bz.data_ptr())), h)
+
+
+def mg_generate_blob_patch(seed, shape, scratch, mask, rho, phi_c, corr_cells=8.0, stream=None):
+    """Fills the CUDA tensors mask (int8), rho (float64) and phi_c (float64,
+    the coarse grid) with the synthetic patch of `seed`; scratch is a float32
+    CUDA tensor of at least 2 V + 8 corr_cells + 2 elements."""
+    nz, ny, nx = shape
+    if stream is None:
+        stream = _default_stream()
+    st = lib().mg_generate_blob_patch(int(seed) & 0xFFFFFFFFFFFFFFFF, nx, ny, nz, float(corr_cells),
+                                      _vp(scratch.data_ptr()), _vp(mask.data_ptr()), _vp(rho.data_ptr()),
+                                      _vp(phi_c.data_ptr()), stream)
+    _check(st)

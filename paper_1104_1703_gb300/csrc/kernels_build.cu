@@ -289,6 +289,41 @@ __global__ void fold_coarse_kernel(LevelDev L, FineExtra F, const double* __rest
   }
 }
 
+// The same interpolated values as face arrays (mg_set_dirichlet's layout):
+// each ghost face of an active cell gets the coarse potential sampled at its
+// centre (a ghost face has one active cell, so one thread writes it); the
+// arrays were zeroed before.
+__global__ void faces_from_coarse_kernel(LevelDev L, const double* __restrict__ pc, int cnx, int cny, int cnz, int ox,
+                                         int oy, int oz, double* __restrict__ bx, double* __restrict__ by,
+                                         double* __restrict__ bz, int* err_flag) {
+  const Geom g = L.g;
+  const long long n = g.ncells();
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    natural_coords(idx, g.nx, g.ny, i, j, k);
+    const int c = colour_of(i, j, k);
+    const uint8_t code = L.code[c][g.at(i >> 1, j, k)];
+    if (!(code & kActive2)) continue;
+    const int gh = code >> kGhostShift;
+    if (!gh) continue;
+    const double x = i + 0.5, y = j + 0.5, z = k + 0.5;
+    const double fx[6] = {(double)i, (double)(i + 1), x, x, x, x};
+    const double fy[6] = {y, y, (double)j, (double)(j + 1), y, y};
+    const double fz[6] = {z, z, z, z, (double)k, (double)(k + 1)};
+    const long long nx1 = g.nx + 1, ny1 = g.ny + 1;
+    double* const dst[6] = {bx + ((long long)k * g.ny + j) * nx1 + i, bx + ((long long)k * g.ny + j) * nx1 + i + 1,
+                            by + ((long long)k * ny1 + j) * g.nx + i, by + ((long long)k * ny1 + j + 1) * g.nx + i,
+                            bz + ((long long)k * g.ny + j) * g.nx + i, bz + ((long long)(k + 1) * g.ny + j) * g.nx + i};
+    for (int d = 0; d < 6; ++d) {
+      if (!(gh & (1 << d))) continue;
+      double v;
+      if (coarse_sample(pc, cnx, cny, cnz, ox, oy, oz, fx[d], fy[d], fz[d], v)) *dst[d] = v;
+      else atomicExch(err_flag, 1);
+    }
+  }
+}
+
 // b = h^2 rho - bc over whole colour arrays (halo and padding stay 0).
 __global__ void combine_rhs_kernel(long long total, const double* __restrict__ r0, const double* __restrict__ r1,
                                    const double* __restrict__ b0, const double* __restrict__ b1, double* __restrict__ o0,
@@ -528,6 +563,14 @@ cudaError_t launch_fold_coarse(const LevelDev& L0, const FineExtra& F, const dou
   count_launch();
   fold_coarse_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0, F, pc, cnx, cny, cnz, ox, oy, oz,
                                                                    err_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces_from_coarse(const LevelDev& L0, const double* pc, int cnx, int cny, int cnz, int ox, int oy,
+                                    int oz, double* bx, double* by, double* bz, int* err_flag, cudaStream_t s) {
+  count_launch();
+  faces_from_coarse_kernel<<<grid_for(L0.g.ncells()), kThreads, 0, s>>>(L0, pc, cnx, cny, cnz, ox, oy, oz, bx, by, bz,
+                                                                         err_flag);
   return cudaGetLastError();
 }
 

@@ -888,3 +888,148 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
 }
 
 }  // namespace gbmg
+
+// ---------------------------------------------------------------------------
+// The network's input channels from one patch's data (device buffers in the
+// C ABI's natural layout), and the scale that maps its output back to Phi
+// ---------------------------------------------------------------------------
+
+namespace gbmg {
+
+namespace {
+
+struct CellFaces {
+  int n;        // ghost faces
+  double sum;   // sum of their Dirichlet values
+  double sq;    // sum of their squares
+};
+
+__device__ __forceinline__ CellFaces ghost_faces(const int8_t* __restrict__ mask, const double* __restrict__ bx,
+                                                 const double* __restrict__ by, const double* __restrict__ bz, int nx,
+                                                 int ny, int nz, long long v) {
+  const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((long long)nx * ny));
+  const long long sy = nx, sz = (long long)nx * ny;
+  const bool in[6] = {i > 0, i + 1 < nx, j > 0, j + 1 < ny, k > 0, k + 1 < nz};
+  const long long off[6] = {-1, 1, -sy, sy, -sz, sz};
+  const long long nx1 = nx + 1, ny1 = ny + 1;
+  const long long fi[6] = {((long long)k * ny + j) * nx1 + i, ((long long)k * ny + j) * nx1 + i + 1,
+                           ((long long)k * ny1 + j) * nx + i, ((long long)k * ny1 + j + 1) * nx + i,
+                           ((long long)k * ny + j) * nx + i, ((long long)(k + 1) * ny + j) * nx + i};
+  const double* fb[6] = {bx, bx, by, by, bz, bz};
+  CellFaces r = {0, 0.0, 0.0};
+  for (int d = 0; d < 6; ++d) {
+    if (in[d] && mask[v + off[d]] > 0) continue;
+    const double f = fb[d] ? fb[d][fi[d]] : 0.0;
+    r.n += 1;
+    r.sum += f;
+    r.sq += f * f;
+  }
+  return r;
+}
+
+// per-block partial sums: [0] sum of src^2 over active cells, [1] active
+// cells, [2] sum of ghost-face values squared, [3] ghost faces
+__global__ void features_partials_kernel(const int8_t* __restrict__ mask, const double* __restrict__ rho,
+                                         const double* __restrict__ bx, const double* __restrict__ by,
+                                         const double* __restrict__ bz, int nx, int ny, int nz, double h2n2,
+                                         double* __restrict__ part) {
+  const long long V = (long long)nx * ny * nz;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    if (mask[v] <= 0) continue;
+    const double src = h2n2 * rho[v];
+    a[0] += src * src;
+    a[1] += 1.0;
+    const CellFaces f = ghost_faces(mask, bx, by, bz, nx, ny, nz, v);
+    a[2] += f.sq;
+    a[3] += f.n;
+  }
+  __shared__ double sh[4][256];
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// s = sqrt(mean src^2 + mean face^2) (1 when that is not positive), in a
+// fixed order over the blocks
+__global__ void features_scale_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ s_out) {
+  if (threadIdx.x || blockIdx.x) return;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nblocks; ++b)
+    for (int q = 0; q < 4; ++q) a[q] += part[4 * b + q];
+  const double ms = (a[1] > 0 ? a[0] / a[1] : 0.0) + (a[3] > 0 ? a[2] / a[3] : 0.0);
+  const double s = sqrt(ms);
+  *s_out = s > 0.0 ? s : 1.0;
+}
+
+// xin[0] = src / s on active cells; xin[1] = +1 active, -1 inactive; xin[2] =
+// mean ghost-face value / s where the cell has ghost faces
+__global__ void features_write_kernel(const int8_t* __restrict__ mask, const double* __restrict__ rho,
+                                      const double* __restrict__ bx, const double* __restrict__ by,
+                                      const double* __restrict__ bz, int nx, int ny, int nz, double h2n2,
+                                      const double* __restrict__ s_dev, float* __restrict__ xin) {
+  const long long V = (long long)nx * ny * nz;
+  const double s = *s_dev;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const bool act = mask[v] > 0;
+    double f0 = 0.0, f2 = 0.0;
+    if (act) {
+      f0 = h2n2 * rho[v] / s;
+      const CellFaces f = ghost_faces(mask, bx, by, bz, nx, ny, nz, v);
+      if (f.n) f2 = f.sum / f.n / s;
+    }
+    xin[v] = (float)f0;
+    xin[V + v] = act ? 1.0f : -1.0f;
+    xin[2 * V + v] = (float)f2;
+  }
+}
+
+// phi[v] = s pred[v] (FP64)
+__global__ void scale_prediction_kernel(const float* __restrict__ pred, long long V, const double* __restrict__ s_dev,
+                                        double* __restrict__ phi) {
+  const double s = *s_dev;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
+    phi[v] = s * (double)pred[v];
+}
+
+// y[v] = phi[v] / s (the training target of a solved patch)
+__global__ void scale_target_kernel(const double* __restrict__ phi, long long V, const double* __restrict__ s_dev,
+                                    float* __restrict__ y) {
+  const double s = *s_dev;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
+    y[v] = (float)(phi[v] / s);
+}
+
+}  // namespace
+
+cudaError_t launch_features(const int8_t* mask, const double* rho, const double* bx, const double* by,
+                            const double* bz, int nx, int ny, int nz, double h, double* part, int nblocks,
+                            double* s_dev, float* xin, cudaStream_t s) {
+  const int n = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
+  const double h2n2 = h * h * (double)n * (double)n;
+  count_launch(3);
+  features_partials_kernel<<<nblocks, 256, 0, s>>>(mask, rho, bx, by, bz, nx, ny, nz, h2n2, part);
+  features_scale_kernel<<<1, 32, 0, s>>>(part, nblocks, s_dev);
+  features_write_kernel<<<ew_grid((long long)nx * ny * nz), 256, 0, s>>>(mask, rho, bx, by, bz, nx, ny, nz, h2n2, s_dev,
+                                                                        xin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_prediction(const float* pred, long long V, const double* s_dev, double* phi, cudaStream_t s) {
+  count_launch();
+  scale_prediction_kernel<<<ew_grid(V), 256, 0, s>>>(pred, V, s_dev, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_target(const double* phi, long long V, const double* s_dev, float* y, cudaStream_t s) {
+  count_launch();
+  scale_target_kernel<<<ew_grid(V), 256, 0, s>>>(phi, V, s_dev, y);
+  return cudaGetLastError();
+}
+
+}  // namespace gbmg

@@ -1078,6 +1078,35 @@ mg_status mg_set_dirichlet_from_coarse(mg_hierarchy* H, const double* phi_c, mg_
   return MG_OK;
 }
 
+mg_status mg_faces_from_coarse(mg_hierarchy* H, const double* phi_c, mg_mem where, int cnx, int cny, int cnz, int ox,
+                               int oy, int oz, double* bx, double* by, double* bz) {
+  if (!H || !phi_c || !bx || !by || !bz) return fail(H, MG_ERR_INVALID_ARG, "null argument");
+  if (cnx < 2 || cny < 2 || cnz < 2 || cnx > 4096 || cny > 4096 || cnz > 4096)
+    return fail(H, MG_ERR_INVALID_ARG, "coarse dimensions must be in 2..4096");
+  DeviceGuard guard(H->device);
+  for (const void* p : {(const void*)bx, (const void*)by, (const void*)bz})
+    if (!is_device_ptr(p, H->device))
+      return fail(H, MG_ERR_INVALID_ARG, "face arrays must be device memory of the hierarchy's GPU");
+  const Geom& g = H->L[0].g;
+  const size_t bytes = sizeof(double) * (size_t)cnx * cny * cnz;
+  if (where == MG_MEM_HOST) CKS(ensure_staging(H, bytes));
+  const void* src;
+  CKS(device_view(H, phi_c, where, bytes, 0, &src));
+  CK(H, cudaMemsetAsync(bx, 0, sizeof(double) * (size_t)(g.nx + 1) * g.ny * g.nz, H->stream));
+  CK(H, cudaMemsetAsync(by, 0, sizeof(double) * (size_t)g.nx * (g.ny + 1) * g.nz, H->stream));
+  CK(H, cudaMemsetAsync(bz, 0, sizeof(double) * (size_t)g.nx * g.ny * (g.nz + 1), H->stream));
+  CK(H, cudaMemsetAsync(H->err_flag, 0, sizeof(int), H->stream));
+  CKS(launch_ok(H, launch_faces_from_coarse(H->L[0], (const double*)src, cnx, cny, cnz, ox, oy, oz, bx, by, bz,
+                                            H->err_flag, H->stream),
+                "coarse interpolation"));
+  int err = 0;
+  CK(H, cudaMemcpyAsync(H->hscal, H->err_flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  CK(H, cudaStreamSynchronize(H->stream));
+  std::memcpy(&err, H->hscal, sizeof(int));
+  if (err) return fail(H, MG_ERR_INVALID_ARG, "a boundary face lies outside the coarse cell centres");
+  return MG_OK;
+}
+
 mg_status mg_set_solution(mg_hierarchy* H, const double* phi, mg_mem where) {
   if (!H) return fail(H, MG_ERR_INVALID_ARG, "null hierarchy");
   DeviceGuard guard(H->device);

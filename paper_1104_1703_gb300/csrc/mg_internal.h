@@ -191,6 +191,10 @@ cudaError_t launch_fold_faces(const LevelDev& L0, const FineExtra& F, const doub
 cudaError_t launch_fold_coarse(const LevelDev& L0, const FineExtra& F, const double* pc, int cnx, int cny,
                                int cnz, int ox, int oy, int oz, int* err_flag, cudaStream_t s);
 cudaError_t launch_combine_rhs(const LevelDev& L0, const FineExtra& F, cudaStream_t s);
+// The interpolated values as face arrays (zeroed by the caller; only ghost
+// faces of active cells are written).
+cudaError_t launch_faces_from_coarse(const LevelDev& L0, const double* pc, int cnx, int cny, int cnz, int ox, int oy,
+                                    int oz, double* bx, double* by, double* bz, int* err_flag, cudaStream_t s);
 // h^2 rho into F.rhoh2 and the folded b into L0.rhs in one pass.
 cudaError_t launch_set_rhs(const LevelDev& L0, const FineExtra& F, const double* rho, double h2, bool bc_zero,
                            cudaStream_t s);

@@ -109,6 +109,8 @@ struct mg_unet {
   double* loss_part = nullptr;         // loss partial sums and the two totals
   double* loss_sums = nullptr;
   int loss_blocks = 0;
+  double* feat_part = nullptr;         // feature partial sums
+  double* feat_scale = nullptr;        // the patch's scale s
 };
 
 namespace {
@@ -530,6 +532,7 @@ mg_status mg_unet_create(int levels, int base, int nx, int ny, int nz, void* cud
   const size_t o_red = R.take(sizeof(float) * (size_t)N->red_blocks * (128 + 1));
   N->loss_blocks = 512;
   const size_t o_lp = R.take(sizeof(double) * (2 * (size_t)N->loss_blocks + 2));
+  const size_t o_fp = R.take(sizeof(double) * (4 * (size_t)N->loss_blocks + 2));
 
   cudaError_t e = dev_malloc((void**)&N->arena, R.used);
   if (e != cudaSuccess) {
@@ -558,6 +561,8 @@ mg_status mg_unet_create(int levels, int base, int nx, int ny, int nz, void* cud
   N->red_partial = (float*)(base_p + o_red);
   N->loss_part = (double*)(base_p + o_lp);
   N->loss_sums = N->loss_part + 2 * N->loss_blocks;
+  N->feat_part = (double*)(base_p + o_fp);
+  N->feat_scale = N->feat_part + 4 * N->loss_blocks;
   mg_status st = MG_OK;
   if (cudaMemsetAsync(N->arena, 0, R.used, N->stream) != cudaSuccess) st = ufail(N, MG_ERR_CUDA, "arena reset");
   for (size_t i = 0; i < plan.size(); ++i) {
@@ -725,6 +730,60 @@ mg_status mg_unet_train_step(mg_unet* N, const float* x, const float* y, mg_mem 
     UCKS(check_err(N));
     *loss = sums[0] > 0 ? sums[1] / sums[0] : 0.0;
     return MG_OK;
+  }
+  return MG_OK;
+}
+
+static mg_status patch_inputs(mg_unet* N, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                              const double* bz, double h) {
+  if (!mask || !rho || !(h > 0)) return ufail(N, MG_ERR_INVALID_ARG, "null mask or rho, or h <= 0");
+  for (const void* p : {(const void*)mask, (const void*)rho, (const void*)bx, (const void*)by, (const void*)bz})
+    if (p && !is_device_ptr(p, N->device))
+      return ufail(N, MG_ERR_INVALID_ARG, "patch buffers must be device memory of the network's GPU");
+  UCK(N, launch_features(mask, rho, bx, by, bz, N->nx, N->ny, N->nz, h, N->feat_part, N->loss_blocks, N->feat_scale,
+                         N->xin, N->stream));
+  UCK(N, launch_input_to_bf16(N->xin, N->x0.voxels(), N->x0.p, N->stream));
+  return MG_OK;
+}
+
+mg_status mg_unet_features(mg_unet* N, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                           const double* bz, double h, float* x, mg_mem where, double* scale) {
+  if (!N) return ufail(N, MG_ERR_INVALID_ARG, "null network");
+  UGuard g(N->device);
+  UCKS(patch_inputs(N, mask, rho, bx, by, bz, h));
+  if (x) UCKS(copy_io(N, x, N->xin, sizeof(float) * 3 * N->x0.voxels(), false, where));
+  if (scale) UCK(N, cudaMemcpy(scale, N->feat_scale, sizeof(double), cudaMemcpyDeviceToHost));
+  return MG_OK;
+}
+
+mg_status mg_unet_predict(mg_unet* N, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                          const double* bz, double h, double* phi) {
+  if (!N || !phi) return ufail(N, MG_ERR_INVALID_ARG, "null network or output");
+  UGuard g(N->device);
+  if (!is_device_ptr(phi, N->device)) return ufail(N, MG_ERR_INVALID_ARG, "phi must be device memory");
+  UCKS(patch_inputs(N, mask, rho, bx, by, bz, h));
+  UCKS(forward(N));
+  UCK(N, launch_scale_prediction(N->pred, N->x0.voxels(), N->feat_scale, phi, N->stream));
+  return MG_OK;
+}
+
+mg_status mg_unet_train_patch(mg_unet* N, const int8_t* mask, const double* rho, const double* bx, const double* by,
+                              const double* bz, double h, const double* phi, double lr, double* loss) {
+  if (!N || !phi) return ufail(N, MG_ERR_INVALID_ARG, "null network or target");
+  UGuard g(N->device);
+  if (!is_device_ptr(phi, N->device)) return ufail(N, MG_ERR_INVALID_ARG, "phi must be device memory");
+  const long long V0 = N->x0.voxels();
+  UCKS(patch_inputs(N, mask, rho, bx, by, bz, h));
+  UCK(N, launch_scale_target(phi, V0, N->feat_scale, N->target, N->stream));
+  UCKS(forward(N));
+  UCK(N, launch_loss(N->pred, N->target, N->x0.p, V0, N->loss_part, N->loss_blocks, N->loss_sums, N->gpred, N->stream));
+  UCKS(backward(N));
+  UCKS(mg_unet_adam_step(N, lr, 0.9, 0.999, 1e-8));
+  if (loss) {
+    double sums[2];
+    UCK(N, cudaMemcpyAsync(sums, N->loss_sums, sizeof(sums), cudaMemcpyDeviceToHost, N->stream));
+    UCKS(check_err(N));
+    *loss = sums[0] > 0 ? sums[1] / sums[0] : 0.0;
   }
   return MG_OK;
 }

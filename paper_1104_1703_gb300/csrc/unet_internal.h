@@ -96,6 +96,14 @@ cudaError_t launch_loss(const float* p, const float* y, const __nv_bfloat16* x0,
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, cudaStream_t s);
 
+// The three input channels (FP32 [3][V]) of a patch and its scale s (device
+// scalar), from device mask, rho and face arrays (faces nullable = 0).
+cudaError_t launch_features(const int8_t* mask, const double* rho, const double* bx, const double* by,
+                            const double* bz, int nx, int ny, int nz, double h, double* part, int nblocks,
+                            double* s_dev, float* xin, cudaStream_t s);
+cudaError_t launch_scale_prediction(const float* pred, long long V, const double* s_dev, double* phi, cudaStream_t s);
+cudaError_t launch_scale_target(const double* phi, long long V, const double* s_dev, float* y, cudaStream_t s);
+
 cudaError_t launch_input_to_bf16(const float* x, long long V, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_avg_pool(const __nv_bfloat16* src, int ss, int so, int W, int H, int D, int c, __nv_bfloat16* dst,
                             int ds, int dofs, cudaStream_t s);
