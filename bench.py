@@ -81,6 +81,9 @@ def parse():
                    help="mixed form: 1 = fine-level FP32 sweep pairs as temporal-blocked passes (the headline "
                         "otherwise runs the faster list half-sweeps and times the pass beside it)")
     p.add_argument("--no-pass-probe", action="store_true", help="skip timing the temporal-blocked pass")
+    p.add_argument("--no-learned", action="store_true", help="skip training and evaluating the learned guess")
+    p.add_argument("--learned-train", type=int, default=4096, help="method-generated training solves (128^3)")
+    p.add_argument("--learned-eval", type=int, default=512, help="held-out patches evaluated (128^3)")
     return p.parse_args()
 
 
@@ -560,6 +563,23 @@ def run_holes(args, B, device, stream, world):
     return out
 
 
+def run_learned(args):
+    """The learned initial guess (a 4-level 3D U-Net, 16 base channels, BF16
+    weights and activations, FP32 accumulation, tcgen05 convolutions):
+    trained on --learned-train solves at 128^3 that the method generates
+    (blob patches with one-way-interface boundary values, solved to 1e-10;
+    one Adam step per solve), then evaluated on --learned-eval held-out
+    patches: V-cycles and wall time to 1e-8 of the mixed form from the
+    learned guess (inference inside the timed region) against the mixed form
+    and the plain FP64 method from a zero guess."""
+    from paper_1104_1703_gb300 import learned as Lg
+    s, losses, records = Lg.run(n=128, levels=4, base=16, n_train=args.learned_train, n_eval=args.learned_eval)
+    s["workload"] = ("blob patches 128^3 (white noise smoothed over 8 cells, thresholded; rho ~ U[-1,1]; Dirichlet "
+                     "values interpolated from a half-resolution coarse potential), GPU-generated from seeds")
+    s["tol"] = 1e-8
+    return s
+
+
 def run_wcycles(args, B, device, stream, world, mask_d, rho_d, h):
     """The multigrid schedules of Section 5.3 on the headline workload: the
     plain FP64 method with N_cycles = 1 (V), 2 and 3 (W) coarse iterations
@@ -672,6 +692,7 @@ def run_ours(args):
     wcyc = None if args.no_wcycles else run_wcycles(args, B, device, stream, world, mask_d, rho_d, w["h"])
     batched = None if args.no_batch else run_batched(args, B, device, stream, world)
     holes = None if args.no_holes else run_holes(args, B, device, stream, world)
+    learned = None if args.no_learned else run_learned(args)
 
     if rank != 0:
         return
@@ -710,6 +731,8 @@ def run_ours(args):
         line["w_cycles"] = wcyc
     if pass_probe is not None:
         line["smoother_pass_probe"] = pass_probe
+    if learned is not None:
+        line["learned_guess"] = learned
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"], line["error_vs_oracle"] = cpu_baseline(args.size, solutions)
     print(json.dumps(line), flush=True)

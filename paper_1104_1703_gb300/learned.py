@@ -114,18 +114,28 @@ def train(net: B.UNet, patches: Patches, seeds, lr: float = 1e-3, lr_end: float 
     return losses
 
 
-def evaluate(net: B.UNet, patches: Patches, seeds, tol: float = 1e-8, max_cycles: int = 200):
+def evaluate(net: B.UNet, patches: Patches, seeds, tol: float = 1e-8, max_cycles: int = 200, fp64: "Patches" = None):
     """For each patch: the solve to tol from a zero guess and from the
     learned guess (the guess's inference inside the timed region), timed
-    with CUDA events on the library's stream.  Returns per-patch records."""
+    with CUDA events on the library's stream; with `fp64` (Patches of the
+    plain FP64 method) also the FP64 solve from a zero guess.  Returns
+    per-patch records."""
     import torch
     out = []
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     stream = torch.cuda.current_stream()
     for seed in seeds:
         if not patches.setup(seed):
             continue
         H = patches.H
+        rec = {"seed": int(seed)}
+        if fp64 is not None:
+            fp64.setup(seed)
+            torch.cuda.synchronize()
+            ev[4].record(stream)
+            fp64.H.set_solution(None)
+            st2, i2 = fp64.H.solve(tol, max_cycles)
+            ev[5].record(stream)
         torch.cuda.synchronize()
         ev[0].record(stream)
         H.set_solution(None)
@@ -137,9 +147,12 @@ def evaluate(net: B.UNet, patches: Patches, seeds, tol: float = 1e-8, max_cycles
         st1, i1 = H.solve(tol, max_cycles)
         ev[3].record(stream)
         torch.cuda.synchronize()
-        out.append({"seed": int(seed), "status": (st0, st1), "cycles_zero": i0["cycles"], "cycles_learned": i1["cycles"],
+        rec.update({"status": (st0, st1), "cycles_zero": i0["cycles"], "cycles_learned": i1["cycles"],
                     "ms_zero": ev[0].elapsed_time(ev[1]), "ms_learned": ev[2].elapsed_time(ev[3]),
                     "rel_init_learned": i1["r_init"] / i1["r_zero"], "order": (i0["order"], i1["order"])})
+        if fp64 is not None:
+            rec.update({"status_fp64": st2, "cycles_fp64": i2["cycles"], "ms_fp64": ev[4].elapsed_time(ev[5])})
+        out.append(rec)
     return out
 
 
@@ -159,7 +172,12 @@ def summary(records, inner_cycles: int = 1):
             "ms_zero_mean": float(mz.mean()), "ms_learned_mean": float(ml.mean()),
             "wall_time_ratio_learned_over_zero": float(ml.mean() / mz.mean()),
             "initial_rel_residual_learned_median": float(np.median([r["rel_init_learned"] for r in records])),
-            "all_converged": all(r["status"] == (0, 0) for r in records)}
+            "all_converged": all(r["status"] == (0, 0) for r in records) and
+                             all(r.get("status_fp64", 0) == 0 for r in records),
+            **({"cycles_fp64_mean": float(np.mean([r["cycles_fp64"] for r in records])),
+                "ms_fp64_mean": float(np.mean([r["ms_fp64"] for r in records])),
+                "wall_time_ratio_learned_over_fp64": float(ml.mean() / np.mean([r["ms_fp64"] for r in records]))}
+               if "ms_fp64" in records[0] else {})}
 
 
 def run(n: int = 128, levels: int = 4, base: int = 16, n_train: int = 4096, n_eval: int = 512, lr: float = 1e-3,
@@ -177,7 +195,8 @@ def run(n: int = 128, levels: int = 4, base: int = 16, n_train: int = 4096, n_ev
     losses = train(net, patches, [base_seed + i for i in range(n_train)], lr, lr_end, log_every=log_every)
     torch.cuda.synchronize()
     t_train = time.time() - t0
-    records = evaluate(net, patches, [base_seed + 500000 + i for i in range(n_eval)])
+    fp64 = Patches(n, device, precision=0)
+    records = evaluate(net, patches, [base_seed + 500000 + i for i in range(n_eval)], fp64=fp64)
     s = summary(records, inner_cycles)
     s.update({"grid": [n, n, n], "levels": levels, "base_channels": base, "train_patches": len(losses),
               "train_seconds": t_train, "loss_first_64": float(np.mean(losses[:64])) if losses else None,
