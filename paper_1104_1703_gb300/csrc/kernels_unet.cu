@@ -37,16 +37,64 @@ namespace {
 constexpr unsigned long long kConvLimitNs = 1000000000ull;
 
 struct ConvSmemHeader {
-  unsigned long long full[kConvStages];
-  unsigned long long empty[kConvStages];
+  unsigned long long full[kConvMaxStages];
+  unsigned long long empty[kConvMaxStages];
   unsigned long long accf[2];
   unsigned long long acce[2];
+  unsigned long long wbar;
   uint32_t tmem;
   int abort;
   int consumed;  // units the MMA thread has waited for (the copies still in flight at an abort are after it)
 };
 
-__device__ __forceinline__ int conv_units(const ConvArgs& a) { return 27 * (a.cin / (8 * a.kc)); }
+}  // namespace
+
+// Shared-memory layout of one convolution launch: per pipeline unit the
+// input bytes (a halo row box of 16 channels, or one tap's tile of kc
+// chunks) and the weight bytes staged with it (0 when the layer's weights
+// are resident: w_bytes, loaded once per CTA).
+__host__ __device__ ConvLayout conv_layout(const ConvArgs& a) {
+  ConvLayout l;
+  const unsigned wall = 27u * (unsigned)a.cin * (unsigned)a.cout * 2u;
+  l.w_load = a.wres ? wall : 0u;
+  l.w_bytes = a.wres ? (wall + 1023u) / 1024u * 1024u : 0u;
+  if (a.halo) {
+    l.a_bytes = 2u * 9u * 130u * 16u;
+    l.b_bytes = 0;
+    l.units = a.cin / 16;
+  } else {
+    l.a_bytes = (unsigned)a.kc * 2048u;
+    l.b_bytes = a.wres ? 0u : (unsigned)a.kc * (unsigned)a.cout * 16u;
+    l.units = 27 * (a.cin / (8 * a.kc));
+  }
+  return l;
+}
+
+size_t conv_smem_bytes(const ConvArgs& a) {
+  const ConvLayout l = conv_layout(a);
+  return 1024 + (size_t)l.w_bytes + (size_t)a.stages * (l.a_bytes + l.b_bytes);
+}
+
+// Pipeline depth, resident weights and the halo path of a convolution: a
+// tile that is one full row of 128 voxels takes its input once with a halo
+// (box 130 x 3 x 3, every tap a view of it; this needs the weights
+// resident); weights up to 72 KB stay resident; as many stages as fit in
+// about 110 KB (two CTAs per multiprocessor) or, for halo stages, 220 KB.
+void conv_plan(ConvArgs& a) {
+  const unsigned wall = 27u * (unsigned)a.cin * (unsigned)a.cout * 2u;
+  a.wres = wall <= 72u * 1024u ? 1 : 0;
+  a.halo = (a.bx == 128 && a.wres) ? 1 : 0;
+  a.stages = 1;
+  const ConvLayout l = conv_layout(a);
+  const size_t per = l.a_bytes + l.b_bytes;
+  const size_t budget = per > 12 * 1024 ? 220 * 1024 : 110 * 1024;
+  long long n = ((long long)budget - 1024 - (long long)l.w_bytes) / (long long)per;
+  if (n > kConvMaxStages) n = kConvMaxStages;
+  if (n < 2) n = 2;
+  a.stages = (int)n;
+}
+
+namespace {
 
 }  // namespace
 
@@ -63,18 +111,19 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     conv_kernel(const __grid_constant__ CUtensorMap map, ConvArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   ConvSmemHeader& S = *reinterpret_cast<ConvSmemHeader*>(smem_raw);
-  unsigned char* stage_a = smem_raw + 1024;
-  const unsigned a_bytes = (unsigned)a.kc * 2048u;
-  const unsigned b_bytes = (unsigned)a.kc * (unsigned)a.cout * 16u;
-  unsigned char* stage_b = stage_a + kConvStages * a_bytes;
+  const ConvLayout lay = conv_layout(a);
+  unsigned char* wres = smem_raw + 1024;  // resident weights (when lay.w_bytes > 0)
+  unsigned char* stage_a = wres + lay.w_bytes;
+  unsigned char* stage_b = stage_a + a.stages * lay.a_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = a.ntx * a.nty * a.ntz;
-  const int units = conv_units(a);
+  const int units = lay.units;
   const int upt = a.cin / (8 * a.kc);
+  const int NS = a.stages;
   const uint32_t acc_cols = (uint32_t)a.cout;
   const uint32_t tcols = conv_tmem_cols(a.cout);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kConvStages; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], 1);
     }
@@ -82,6 +131,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       mbar_init(&S.accf[i], 1);
       mbar_init(&S.acce[i], 128);
     }
+    mbar_init(&S.wbar, 1);
     S.abort = 0;
     S.consumed = 0;
     mbar_init_fence();
@@ -96,45 +146,62 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---- copies ----
+      if (lay.w_bytes) {  // the whole layer's weights, once per CTA
+        mbar_expect_tx(&S.wbar, lay.w_load);
+        bulk_load(wres, a.w, lay.w_load, &S.wbar);
+      }
       int it = 0;
       const bool stall = a.debug_stall && blockIdx.x == 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
         const int tx = t % a.ntx, r = t / a.ntx, ty = r % a.nty, tz = r / a.nty;
         const int x0 = tx * a.bx, y0 = ty * a.by, z0 = tz * a.bz;
         for (int u = 0; u < units; ++u, ++it) {
-          const int st = it % kConvStages, n = it / kConvStages;
+          const int st = it % NS, n = it / NS;
           if (n > 0 && !mbar_wait_bounded(&S.empty[st], (n - 1) & 1, kConvLimitNs, abort)) {
             atomicExch(a.err, 1);
             *abort = 1;
             break;
           }
-          if (stall && it >= kConvStages) {  // stop issuing: the MMA thread's wait runs out
+          if (stall && it >= NS) {  // stop issuing: the MMA thread's wait runs out
             --it;
             break;
           }
-          const int tap = u / upt, kq = u % upt;
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
           fence_proxy_async();
-          mbar_expect_tx(&S.full[st], a_bytes + b_bytes);
-          tma_load_5d(stage_a + st * a_bytes, &map, 0, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, kq * a.kc, &S.full[st]);
-          bulk_load(stage_b + st * b_bytes, a.w + ((size_t)tap * (a.cin / 8) + (size_t)kq * a.kc) * a.cout * 8, b_bytes,
-                    &S.full[st]);
+          mbar_expect_tx(&S.full[st], lay.a_bytes + lay.b_bytes);
+          if (a.halo) {
+            // the row of 128 output voxels with a one-voxel halo in x, y and
+            // z, 16 input channels: every tap is a view of it
+            tma_load_5d(stage_a + st * lay.a_bytes, &map, 0, x0 - 1, y0 - 1, z0 - 1, 2 * u, &S.full[st]);
+          } else {
+            const int tap = u / upt, kq = u % upt;
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            tma_load_5d(stage_a + st * lay.a_bytes, &map, 0, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, kq * a.kc,
+                        &S.full[st]);
+            if (lay.b_bytes)
+              bulk_load(stage_b + st * lay.b_bytes,
+                        a.w + ((size_t)tap * (a.cin / 8) + (size_t)kq * a.kc) * a.cout * 8, lay.b_bytes, &S.full[st]);
+          }
         }
         if (stall) break;
       }
       // at an abort, let the copies still in flight land before the CTA exits
       if (*abort) {
         __threadfence_block();
-        for (int j = S.consumed; j < it; ++j)
-          mbar_wait_bounded(&S.full[j % kConvStages], (j / kConvStages) & 1, kConvLimitNs);
+        for (int j = S.consumed; j < it; ++j) mbar_wait_bounded(&S.full[j % NS], (j / NS) & 1, kConvLimitNs);
+        if (lay.w_bytes) mbar_wait_bounded(&S.wbar, 0, kConvLimitNs);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMAs ----
       const uint32_t idesc = idesc_bf16_f32(kConvTileM, a.cout);
+      const uint32_t wchunk = (uint32_t)a.cout * 16u;  // bytes of one 8-channel chunk of one tap's weights
       int it = 0, tc = 0;
       bool issued = false;
+      if (lay.w_bytes && !mbar_wait_bounded(&S.wbar, 0, kConvLimitNs, abort)) {
+        atomicExch(a.err, 1);
+        *abort = 1;
+      }
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tc) {
         const int b = tc & 1, n = tc >> 1;
         if (n > 0 && !mbar_wait_bounded(&S.acce[b], (n - 1) & 1, kConvLimitNs, abort)) {
@@ -146,8 +213,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         const uint32_t d = tmem + (uint32_t)b * acc_cols;
         bool ok = true;
         for (int u = 0; u < units; ++u, ++it) {
-          const int st = it % kConvStages;
-          if (!mbar_wait_bounded(&S.full[st], (it / kConvStages) & 1, kConvLimitNs, abort)) {
+          const int st = it % NS;
+          if (!mbar_wait_bounded(&S.full[st], (it / NS) & 1, kConvLimitNs, abort)) {
             atomicExch(a.err, 1);
             *abort = 1;
             ok = false;
@@ -155,12 +222,26 @@ __global__ void __launch_bounds__(kConvThreads, 1)
           }
           S.consumed = it + 1;
           tc_fence_after();
-          const unsigned char* A = stage_a + st * a_bytes;
-          const unsigned char* Bm = stage_b + st * b_bytes;
-          for (int ks = 0; ks < a.kc / 2; ++ks) {
-            const uint64_t ad = smem_desc_kmajor(A + ks * 2 * 2048, 2048, 128);
-            const uint64_t bd = smem_desc_kmajor(Bm + ks * 2 * a.cout * 16, (uint32_t)a.cout * 16, 128);
-            tc_mma_f16(d, ad, bd, idesc, (u > 0 || ks > 0) ? 1u : 0u);
+          const unsigned char* A = stage_a + st * lay.a_bytes;
+          if (a.halo) {
+            // channels 16u .. 16u + 15 of the 27 taps: each tap's 128 rows
+            // start (dz, dy, dx) rows into the halo box; the box's rows are
+            // 16 bytes apart and its two 8-channel chunks 9 x 130 rows apart
+            for (int tap = 0; tap < 27; ++tap) {
+              const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+              const uint64_t ad = smem_desc_kmajor(A + ((dz * 3 + dy) * 130 + dx) * 16, 9u * 130u * 16u, 128);
+              const uint64_t bd = smem_desc_kmajor(wres + ((size_t)tap * (a.cin / 8) + 2 * u) * wchunk, wchunk, 128);
+              tc_mma_f16(d, ad, bd, idesc, (u > 0 || tap > 0) ? 1u : 0u);
+            }
+          } else {
+            const int tap = u / upt, kq = u % upt;
+            const unsigned char* Bm = lay.w_bytes ? wres + ((size_t)tap * (a.cin / 8) + (size_t)kq * a.kc) * wchunk
+                                                  : stage_b + st * lay.b_bytes;
+            for (int ks = 0; ks < a.kc / 2; ++ks) {
+              const uint64_t ad = smem_desc_kmajor(A + ks * 2 * 2048, 2048, 128);
+              const uint64_t bd = smem_desc_kmajor(Bm + ks * 2 * wchunk, wchunk, 128);
+              tc_mma_f16(d, ad, bd, idesc, (u > 0 || ks > 0) ? 1u : 0u);
+            }
           }
           tc_commit(&S.empty[st]);
           issued = true;
@@ -170,8 +251,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       }
       // at an abort, wait for the MMAs in flight before TMEM is released
       if (*abort && issued) {
-        for (int j = (it > kConvStages ? it - kConvStages : 0); j < it; ++j)
-          mbar_wait_bounded(&S.empty[j % kConvStages], (j / kConvStages) & 1, kConvLimitNs);
+        for (int j = (it > NS ? it - NS : 0); j < it; ++j)
+          mbar_wait_bounded(&S.empty[j % NS], (j / NS) & 1, kConvLimitNs);
       }
     }
   } else {
@@ -275,14 +356,6 @@ int conv_kc(int cin) {
   return 2;
 }
 
-// The stages plus 32 KB of slack after them: every operand address the
-// MMAs form stays inside the allocation even for a descriptor whose two
-// core-matrix strides were read the other way round (at most 15 x 2048 +
-// 255 bytes past an operand's start).
-size_t conv_smem_bytes(int cin, int cout, int kc) {
-  (void)cin;
-  return 1024 + (size_t)kConvStages * ((size_t)kc * 2048 + (size_t)kc * cout * 16) + 32768;
-}
 
 
 
@@ -348,7 +421,7 @@ int conv_grid(const ConvArgs& a, size_t smem_bytes) {
 
 cudaError_t launch_conv(const CUtensorMap& map, const ConvArgs& a, int grid, cudaStream_t s) {
   count_launch();
-  conv_kernel<<<grid, kConvThreads, conv_smem_bytes(a.cin, a.cout, a.kc), s>>>(map, a);
+  conv_kernel<<<grid, kConvThreads, conv_smem_bytes(a), s>>>(map, a);
   return cudaGetLastError();
 }
 

@@ -171,8 +171,6 @@ mg_status setup_conv(mg_unet* N, Conv& C) {
   int bx, by, bz;
   conv_tile_box(C.in.W, C.in.H, C.in.D, &bx, &by, &bz);
   const int kc = conv_kc(C.cin_pad);
-  if (!make_conv_input_map(&C.map_in, C.in.p, C.in.W, C.in.H, C.in.D, C.cin_pad, bx, by, bz, kc))
-    return ufail(N, MG_ERR_CUDA, "tensor map of a convolution input was refused");
   ConvArgs& a = C.args;
   std::memset(&a, 0, sizeof(a));
   a.W = C.in.W;
@@ -194,7 +192,11 @@ mg_status setup_conv(mg_unet* N, Conv& C) {
   a.out_stride = C.out.stride;
   a.out_off = C.out.off;
   a.err = N->err;
-  C.smem = conv_smem_bytes(a.cin, a.cout, a.kc);
+  conv_plan(a);
+  C.smem = conv_smem_bytes(a);
+  if (!(a.halo ? make_conv_input_map(&C.map_in, C.in.p, a.W, a.H, a.D, a.cin, 130, 3, 3, 2)
+               : make_conv_input_map(&C.map_in, C.in.p, a.W, a.H, a.D, a.cin, bx, by, bz, kc)))
+    return ufail(N, MG_ERR_CUDA, "tensor map of a convolution input was refused");
   return MG_OK;
 }
 
@@ -231,8 +233,6 @@ mg_status setup_conv_backward(mg_unet* N, Conv& C, const Tensor* to, const Tenso
   if (!to) return MG_OK;
   // backward data: K = cout (the gradient's channels), N = cin_pad
   const int kc = conv_kc(C.cout);
-  if (!make_conv_input_map(&C.map_gz_bd, C.gz.p, C.gz.W, C.gz.H, C.gz.D, C.cout, bx, by, bz, kc))
-    return ufail(N, MG_ERR_CUDA, "tensor map of a backward convolution was refused");
   ConvArgs& a = C.bargs;
   std::memset(&a, 0, sizeof(a));
   a.W = C.in.W;
@@ -259,7 +259,11 @@ mg_status setup_conv_backward(mg_unet* N, Conv& C, const Tensor* to, const Tenso
   a.out_stride = to->stride;
   a.out_off = to->off;
   a.err = N->err;
-  C.bsmem = conv_smem_bytes(a.cin, a.cout, a.kc);
+  conv_plan(a);
+  C.bsmem = conv_smem_bytes(a);
+  if (!(a.halo ? make_conv_input_map(&C.map_gz_bd, C.gz.p, a.W, a.H, a.D, a.cin, 130, 3, 3, 2)
+               : make_conv_input_map(&C.map_gz_bd, C.gz.p, a.W, a.H, a.D, a.cin, bx, by, bz, kc)))
+    return ufail(N, MG_ERR_CUDA, "tensor map of a backward convolution was refused");
   return MG_OK;
 }
 

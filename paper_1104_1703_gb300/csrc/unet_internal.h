@@ -16,7 +16,7 @@
 namespace gbmg {
 
 constexpr int kConvThreads = 192;  // warp 0 copies, warp 1 issues the MMAs, warps 2-5 drain the accumulators
-constexpr int kConvStages = 4;
+constexpr int kConvMaxStages = 16;
 constexpr int kConvTileM = 128;    // voxels per output tile (the MMA's M)
 
 // One 3x3x3 convolution (zero padding 1) as an implicit GEMM: output tile of
@@ -38,14 +38,30 @@ struct ConvArgs {
   float* out_f32;             // nullable: also out_f32[v][o] (FP32, before rounding)
   int* err;                   // set to 1 when a wait runs out
   int debug_stall;            // test hook: the copy thread of CTA 0 stops issuing
+  // pipeline (conv_plan): stages in flight, the layer's weights resident in
+  // shared memory, and the halo path (a tile is one row of 128 voxels whose
+  // input is copied once with a one-voxel halo; needs resident weights)
+  int stages;
+  int wres;
+  int halo;
 };
 
-size_t conv_smem_bytes(int cin, int cout, int kc);
+struct ConvLayout {
+  unsigned w_load;   // bytes of the packed weights copied in once (a multiple of 16)
+  unsigned w_bytes;  // their shared-memory footprint, rounded to 1 KB (0: staged per unit)
+  unsigned a_bytes;  // input bytes per unit
+  unsigned b_bytes;  // weight bytes per unit
+  int units;         // units per tile
+};
+__host__ __device__ ConvLayout conv_layout(const ConvArgs& a);
+void conv_plan(ConvArgs& a);
+size_t conv_smem_bytes(const ConvArgs& a);
+
 __host__ __device__ uint32_t conv_tmem_cols(int cout);
 int conv_kc(int cin);
 cudaError_t init_conv_kernel(size_t smem_bytes);
 // `map` describes the input tensor: dims (8, W, H, D, cin / 8), box
-// (8, bx, by, bz, kc), BF16.
+// (8, bx, by, bz, kc), BF16; for the halo path box (8, 130, 3, 3, 2).
 bool make_conv_input_map(CUtensorMap* map, const __nv_bfloat16* x, int W, int H, int D, int cin, int bx, int by,
                          int bz, int kc);
 void conv_tile_box(int W, int H, int D, int* bx, int* by, int* bz);

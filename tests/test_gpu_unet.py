@@ -48,9 +48,10 @@ def _params(levels, base, seed):
 
 
 def _input(n, seed):
+    shape = (n, n, n) if np.isscalar(n) else tuple(n)
     rng = np.random.default_rng(seed)
-    x = rng.normal(size=(3, n, n, n))
-    x[1] = np.where(rng.random((n, n, n)) < 0.7, 1.0, -1.0)
+    x = rng.normal(size=(3,) + shape)
+    x[1] = np.where(rng.random(shape) < 0.7, 1.0, -1.0)
     return x.astype(np.float32)
 
 
@@ -70,11 +71,14 @@ def dev():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("levels,n", [(1, 16), (2, 16), (3, 16), (4, 16), (2, 24), (3, 32)])
+# grids with rows of 128 and 256 voxels take the halo-row path of the
+# convolution at level 0 (and level 1 of the 256-voxel rows)
+@pytest.mark.parametrize("levels,n", [(1, 16), (2, 16), (3, 16), (4, 16), (2, 24), (3, 32), (1, (4, 6, 128)),
+                                      (2, (8, 4, 256)), (3, (4, 8, 128))])
 def test_each_convolution_matches_the_oracle(dev, levels, n):
     P = _params(levels, 16, 11 + levels)
-    x = _input(n, 5 + n)
-    net = B.UNet(levels, 16, (n, n, n))
+    x = _input(n, 5 + (n if np.isscalar(n) else n[2]))
+    net = B.UNet(levels, 16, x.shape[1:])
     net.set_params(flat(P))
     net.forward(x)
     names = _names(levels)
@@ -130,8 +134,8 @@ def test_params_round_trip(dev):
 def _grad_case(levels, n, seed):
     P = _params(levels, 16, seed)
     x = _input(n, seed + 2)
-    g = np.random.default_rng(seed + 3).normal(size=(n, n, n)).astype(np.float32)
-    net = B.UNet(levels, 16, (n, n, n))
+    g = np.random.default_rng(seed + 3).normal(size=x.shape[1:]).astype(np.float32)
+    net = B.UNet(levels, 16, x.shape[1:])
     net.set_params(flat(P))
     net.forward(x)
     net.backward(g)
@@ -169,7 +173,7 @@ def _split(P, G):
     return d
 
 
-@pytest.mark.parametrize("levels,n", [(2, 16), (3, 16)])
+@pytest.mark.parametrize("levels,n", [(2, 16), (3, 16), (2, (4, 4, 128))])
 def test_each_backward_step_matches_the_oracle(dev, levels, n):
     """Per layer, on the network's own tensors: the weight and bias
     gradients are the oracle's convolution backward of the layer's input and
