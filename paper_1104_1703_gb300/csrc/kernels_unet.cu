@@ -67,12 +67,16 @@ __host__ __device__ ConvLayout conv_layout(const ConvArgs& a) {
     l.b_bytes = a.wres ? 0u : (unsigned)a.kc * (unsigned)a.cout * 16u;
     l.units = 27 * (a.cin / (8 * a.kc));
   }
+  // a TMA copy's shared-memory destination must be 128-byte aligned: the
+  // stages are laid out at a stride rounded up to 128 bytes (the weight
+  // stages' size, a multiple of 256, already is)
+  l.a_stride = (l.a_bytes + 127u) / 128u * 128u;
   return l;
 }
 
 size_t conv_smem_bytes(const ConvArgs& a) {
   const ConvLayout l = conv_layout(a);
-  return 1024 + (size_t)l.w_bytes + (size_t)a.stages * (l.a_bytes + l.b_bytes);
+  return 1024 + (size_t)l.w_bytes + (size_t)a.stages * (l.a_stride + l.b_bytes);
 }
 
 // Pipeline depth, resident weights and the halo path of a convolution: a
@@ -86,7 +90,7 @@ void conv_plan(ConvArgs& a) {
   a.halo = (a.bx == 128 && a.wres) ? 1 : 0;
   a.stages = 1;
   const ConvLayout l = conv_layout(a);
-  const size_t per = l.a_bytes + l.b_bytes;
+  const size_t per = l.a_stride + l.b_bytes;
   const size_t budget = per > 12 * 1024 ? 220 * 1024 : 110 * 1024;
   long long n = ((long long)budget - 1024 - (long long)l.w_bytes) / (long long)per;
   if (n > kConvMaxStages) n = kConvMaxStages;
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const ConvLayout lay = conv_layout(a);
   unsigned char* wres = smem_raw + 1024;  // resident weights (when lay.w_bytes > 0)
   unsigned char* stage_a = wres + lay.w_bytes;
-  unsigned char* stage_b = stage_a + a.stages * lay.a_bytes;
+  unsigned char* stage_b = stage_a + a.stages * lay.a_stride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = a.ntx * a.nty * a.ntz;
   const int units = lay.units;
@@ -171,11 +175,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
           if (a.halo) {
             // the row of 128 output voxels with a one-voxel halo in x, y and
             // z, 16 input channels: every tap is a view of it
-            tma_load_5d(stage_a + st * lay.a_bytes, &map, 0, x0 - 1, y0 - 1, z0 - 1, 2 * u, &S.full[st]);
+            tma_load_5d(stage_a + st * lay.a_stride, &map, 0, x0 - 1, y0 - 1, z0 - 1, 2 * u, &S.full[st]);
           } else {
             const int tap = u / upt, kq = u % upt;
             const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-            tma_load_5d(stage_a + st * lay.a_bytes, &map, 0, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, kq * a.kc,
+            tma_load_5d(stage_a + st * lay.a_stride, &map, 0, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, kq * a.kc,
                         &S.full[st]);
             if (lay.b_bytes)
               bulk_load(stage_b + st * lay.b_bytes,
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
           }
           S.consumed = it + 1;
           tc_fence_after();
-          const unsigned char* A = stage_a + st * lay.a_bytes;
+          const unsigned char* A = stage_a + st * lay.a_stride;
           if (a.halo) {
             // channels 16u .. 16u + 15 of the 27 taps: each tap's 128 rows
             // start (dz, dy, dx) rows into the halo box; the box's rows are

@@ -49,7 +49,8 @@ struct ConvArgs {
 struct ConvLayout {
   unsigned w_load;   // bytes of the packed weights copied in once (a multiple of 16)
   unsigned w_bytes;  // their shared-memory footprint, rounded to 1 KB (0: staged per unit)
-  unsigned a_bytes;  // input bytes per unit
+  unsigned a_bytes;  // input bytes per unit (the copy's size)
+  unsigned a_stride; // their shared-memory stride, a multiple of 128 bytes
   unsigned b_bytes;  // weight bytes per unit
   int units;         // units per tile
 };
