@@ -95,7 +95,15 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  tiles staged in shared memory); 0 = four list half-sweeps
  *                  (faster on GB300: the pass moves fewer bytes but waits on
  *                  its chain of barrier-separated stages).  The results are
- *                  bit-identical. */
+ *                  bit-identical.
+ *  fp64_sum        FP64 form, level-0 Gauss-Seidel sweeps: 1 = form each
+ *                  cell's sum of its six neighbour values in 64-bit integer
+ *                  arithmetic (exponent-aligned fixed point, rounded once to
+ *                  the nearest double; subnormal values count as zero), so
+ *                  that the update issues one FP64 instruction instead of
+ *                  six; 0 = five FP64 additions.  Both are accurate to about
+ *                  one rounding of the sum; the results differ in the last
+ *                  bits. */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -105,6 +113,7 @@ typedef struct {
   int inner_cycles;
   int coarse_cluster;
   int smoother_pass;
+  int fp64_sum;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -125,7 +134,8 @@ typedef struct {
 
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
- * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 0. */
+ * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 0,
+ * fp64_sum = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

@@ -4,6 +4,7 @@
 // of mg_internal.h, and the one-CTA V-cycle on small coarse levels.
 #pragma once
 
+#include "exact_sum.cuh"
 #include "mg_internal.h"
 
 namespace gbmg {
@@ -115,6 +116,14 @@ __device__ __forceinline__ bool entry_ok(const Geom& g, long long at, unsigned s
 template <typename T>
 __device__ __forceinline__ T nbr_sum(const T* __restrict__ o, long long at, int dx, int P, long long sz) {
   return ((o[at] + o[at + dx]) + (o[at - P] + o[at + P])) + (o[at - sz] + o[at + sz]);
+}
+
+// The same six values summed in integer arithmetic (exact_sum.cuh: one
+// rounding, no FP64 instruction).
+__device__ __forceinline__ double nbr_sum_exact(const double* __restrict__ o, long long at, int dx, int P,
+                                                long long sz) {
+  const double x[6] = {o[at], o[at + dx], o[at - P], o[at + P], o[at - sz], o[at + sz]};
+  return exact_sum(x);
 }
 
 // tab[0..7] = 1/(6+n), tab[8..15] = 6+n: the level-0 diagonal and its

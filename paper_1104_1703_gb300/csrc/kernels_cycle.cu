@@ -67,8 +67,10 @@ struct PerThread {
 // With SCALED (level 0 of the FP64 method) the right-hand side comes
 // pre-multiplied by 1/D, b/D, so the update (sum - b) / D is one fused
 // multiply-add, sum * (1/D) - b/D: 6 FP64 instructions instead of 7 on
-// the FP64-pipe-bound sweep.
-template <int KIND, typename T, bool UPDATE, bool SCALED = false>
+// the FP64-pipe-bound sweep.  With EXACT as well the neighbour sum is
+// formed in integer arithmetic (nbr_sum_exact), which leaves the fused
+// multiply-add as the update's only FP64 instruction.
+template <int KIND, typename T, bool UPDATE, bool SCALED = false, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   pdl_wait();
   constexpr int PER = PerThread<T>::value;
@@ -88,7 +90,10 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
       at[u] = e & kListAt;
       ok[u] = ok[u] && entry_ok(a.g, at[u], 3);
       if (ok[u]) {
-        s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        if constexpr (EXACT)
+          s[u] = nbr_sum_exact(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        else
+          s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
         b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
         d[u] = inv_diag<KIND>(KIND == 0 ? a.code[at[u]] : 0, a.invd, at[u], tab);
       }
@@ -577,6 +582,12 @@ cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, bool update, 
   }
   if (L.level == 0 && sizeof(T) == 8 && L.rhsd[0]) {
     a.rhsd = (const T*)L.rhsd[colour];
+    if constexpr (sizeof(T) == 8) {
+      if (L.exact_sum) {
+        launch_pdl(gs_list_kernel<0, T, false, true, true>, dim3(grid), dim3(kListBlock), 0, s, a);
+        return cudaGetLastError();
+      }
+    }
     launch_pdl(gs_list_kernel<0, T, false, true>, dim3(grid), dim3(kListBlock), 0, s, a);
     return cudaGetLastError();
   }

@@ -171,7 +171,8 @@ bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
-         (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1);
+         (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
+         (o.fp64_sum == 0 || o.fp64_sum == 1);
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -665,6 +666,7 @@ void mg_default_options(mg_options* opt) {
   opt->inner_cycles = 1;
   opt->coarse_cluster = 0;
   opt->smoother_pass = 0;
+  opt->fp64_sum = 1;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -872,7 +874,10 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->zero_jobs = (ZeroJob*)(base + o_zjobs);
   H->f32_jobs = (F32Job*)(base + o_fjobs);
   H->list_blocks = lblocks;
-  for (int l = 0; l < H->nlev; ++l) H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
+  for (int l = 0; l < H->nlev; ++l) {
+    H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
+    H->L[l].exact_sum = (l == 0 && !mixed && o.fp64_sum == 1) ? 1 : 0;
+  }
   for (int c = 0; c < 2; ++c) {
     H->L[0].rhsd[c] = mixed ? nullptr : (double*)(base + o_rhsd[c]);
     H->F.rhoh2[c] = (double*)(base + o_rhoh2[c]);
