@@ -103,7 +103,12 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  that the update issues one FP64 instruction instead of
  *                  six; 0 = five FP64 additions.  Both are accurate to about
  *                  one rounding of the sum; the results differ in the last
- *                  bits. */
+ *                  bits.
+ *  fine_segments   level-0 Gauss-Seidel sweeps: 1 = one thread per slot of
+ *                  the row segments (8 slots of one colour's half-row) that
+ *                  hold an active cell, so that a warp reads whole runs of
+ *                  every array; 0 = one thread per active cell of the
+ *                  colour's compact list.  The results are bit-identical. */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -114,6 +119,7 @@ typedef struct {
   int coarse_cluster;
   int smoother_pass;
   int fp64_sum;
+  int fine_segments;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -135,7 +141,7 @@ typedef struct {
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
  * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 0,
- * fp64_sum = 1. */
+ * fp64_sum = 1, fine_segments = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

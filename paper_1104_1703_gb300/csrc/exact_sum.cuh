@@ -21,8 +21,9 @@
 // below 2^(64 - 1023) (every term below about 1e-289) is returned as zero,
 // and a result below the smallest normal double flushes to a zero of its
 // sign; an overflow rounds to the infinity of its sign.  If any term is
-// infinite or NaN the plain FP64 sum (left to right) is returned, so that a
-// diverging solve still sees a non-finite value.
+// infinite or NaN the result is what IEEE addition gives: NaN if a term is
+// NaN or infinities of both signs meet, else the infinity (so a diverging
+// solve still sees a non-finite value).
 #pragma once
 
 #include <cstdint>
@@ -77,11 +78,19 @@ __host__ __device__ __forceinline__ double exact_sum(const double (&x)[N]) {
     e[j] = (int)((b[j] >> 52) & 0x7ffu);
     emax = e[j] > emax ? e[j] : emax;
   }
-  if (emax == 0x7ff) {  // an infinity or a NaN among the terms
-    double s = x[0];
+  if (emax == 0x7ff) {
+    // an infinity or a NaN among the terms: the IEEE sum's value, decided on
+    // the bits (no FP64 instruction on this path either)
+    bool nan = false, pinf = false, ninf = false;
 #pragma unroll
-    for (int j = 1; j < N; ++j) s += x[j];
-    return s;
+    for (int j = 0; j < N; ++j) {
+      if (e[j] != 0x7ff) continue;
+      if (b[j] & 0xfffffffffffffull) nan = true;
+      else if (b[j] >> 63) ninf = true;
+      else pinf = true;
+    }
+    if (nan || (pinf && ninf)) return double_of(0x7ff8000000000000ull);
+    return double_of(pinf ? 0x7ff0000000000000ull : 0xfff0000000000000ull);
   }
   if (emax < 64) return 0.0;
   long long S = 0;

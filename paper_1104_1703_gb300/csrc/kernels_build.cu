@@ -340,16 +340,21 @@ __global__ void combine_rhs_kernel(long long total, const double* __restrict__ r
 // per-block ordered writes.  Slot e = (k*ny + j)*hx + q.
 constexpr int kListThreads = 256;
 
-__device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, uint8_t bit, long long e,
-                                            long long n, long long& at, int& j, int& k) {
+__device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, uint8_t bit, int seg_shift,
+                                            long long e, long long n, long long& at, int& j, int& k) {
   if (e >= n) return false;
   const unsigned u = (unsigned)e;  // slots per colour < 2^31
-  const unsigned t = u / (unsigned)g.hx;
-  const int q = (int)(u - t * (unsigned)g.hx);
+  const unsigned per_row = seg_shift ? (unsigned)((g.hx + (1 << seg_shift) - 1) >> seg_shift) : (unsigned)g.hx;
+  const unsigned t = u / per_row;
+  const int q = (int)(u - t * per_row) << seg_shift;
   k = (int)(t / (unsigned)g.ny);
   j = (int)(t - (unsigned)k * (unsigned)g.ny);
   at = g.at(q, j, k);
-  return (code[at] & bit) != 0;
+  if (!seg_shift) return (code[at] & bit) != 0;
+  const int nv = min(1 << seg_shift, g.hx - q);
+  bool any = false;
+  for (int l = 0; l < nv; ++l) any = any || (code[at + l] & bit) != 0;
+  return any;
 }
 
 // exclusive scan of nb block counts in place (one block of 1024 threads);
@@ -380,13 +385,13 @@ __device__ void list_scan_block(uint32_t* block_counts, int nb, uint32_t* count)
 // ordered writes of the members of local block `lb` of a list, from the
 // block's offset in it
 __device__ void list_write_block(const Geom& g, const uint8_t* __restrict__ code, int colour, uint8_t bit,
-                                 uint32_t block_offset, unsigned lb, uint32_t* list) {
+                                 int seg_shift, uint32_t block_offset, unsigned lb, uint32_t* list) {
   __shared__ uint32_t warp_base[kListThreads / 32];
-  const long long n = (long long)g.hx * g.ny * g.nz;
+  const long long n = list_job_slots(g, seg_shift);
   const long long e = (long long)lb * kListThreads + threadIdx.x;
   long long at = 0;
   int j = 0, k = 0;
-  const bool m = list_member(g, code, bit, e, n, at, j, k);
+  const bool m = list_member(g, code, bit, seg_shift, e, n, at, j, k);
   const unsigned bal = __ballot_sync(0xffffffffu, m);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) warp_base[w] = __popc(bal);
@@ -427,11 +432,11 @@ __global__ void __launch_bounds__(kListThreads) list_count_all_kernel(const List
   __syncthreads();
   const ListJob& J = jobs[js];
   const Geom g = J.g;
-  const long long n = (long long)g.hx * g.ny * g.nz;
+  const long long n = list_job_slots(g, J.seg_shift);
   const long long e = (long long)(blockIdx.x - J.block0) * kListThreads + threadIdx.x;
   long long at;
   int j, k;
-  const bool m = list_member(g, J.code, J.bit, e, n, at, j, k);
+  const bool m = list_member(g, J.code, J.bit, J.seg_shift, e, n, at, j, k);
   const int cnt = __syncthreads_count(m);
   if (threadIdx.x == 0) scratch[blockIdx.x] = (uint32_t)cnt;
 }
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(kListThreads) list_write_all_kernel(const List
   if (threadIdx.x == 0) js = find_job(jobs, njobs, blockIdx.x);
   __syncthreads();
   const ListJob& J = jobs[js];
-  list_write_block(J.g, J.code, J.colour, J.bit, scratch[blockIdx.x], blockIdx.x - J.block0, J.list);
+  list_write_block(J.g, J.code, J.colour, J.bit, J.seg_shift, scratch[blockIdx.x], blockIdx.x - J.block0, J.list);
 }
 
 // Many device buffers zeroed, or converted FP64 -> FP32, in one launch:

@@ -108,6 +108,57 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   }
 }
 
+// K4 on level 0 over row segments (list[0] of level 0): a group of
+// kSegSlots lanes takes one segment, lane l its slot q0 + l, so that every
+// array is read in runs of consecutive slots; PER segments per group are in
+// flight at once.  A lane on an inactive or padding slot (code 0) writes 0,
+// the value such a slot always holds, so the group writes whole runs.  The
+// arithmetic per active cell is gs_list_kernel's, with the same options.
+template <typename T, bool UPDATE, bool SCALED, bool EXACT>
+__global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
+  pdl_wait();
+  constexpr int PER = 2;
+  constexpr int GROUPS = 32 / kSegSlots;  // segments per warp and round
+  __shared__ T tab[16];
+  init_tab(tab);
+  const uint32_t n = *a.count;
+  const int lane = threadIdx.x & 31;
+  const int l = lane & (kSegSlots - 1);
+  const uint32_t group = ((blockIdx.x * kListBlock + threadIdx.x) >> 5) * GROUPS + (lane >> kSegShift);
+  const uint32_t ngroups = (gridDim.x * kListBlock >> 5) * GROUPS;
+  for (uint32_t base = group; base < n; base += PER * ngroups) {
+    long long at[PER];
+    T s[PER], b[PER], d[PER];
+    bool ok[PER], act[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = base + u * ngroups;
+      ok[u] = i < n;
+      const uint32_t e = ok[u] ? a.list[i] : 0u;
+      at[u] = (long long)(e & kListAt);
+      ok[u] = ok[u] && entry_ok(a.g, at[u], 9);
+      at[u] += l;
+      if (ok[u]) {
+        const uint8_t code = a.code[at[u]];
+        act[u] = (code & kActive2) != 0;
+        if constexpr (EXACT)
+          s[u] = nbr_sum_exact(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        else
+          s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
+        d[u] = tab[__popc((unsigned)code >> kGhostShift)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok[u]) continue;
+      const T v = SCALED ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+      a.self[at[u]] = act[u] ? v : T(0);
+      if (UPDATE && act[u]) a.phi64[at[u]] += widen_f32(v);
+    }
+  }
+}
+
 // K9, first pass: the sum of r^2 per block into partials[blockIdx.x], r^ =
 // sum_nbr Phi_j - D Phi_i - b the scaled residual of the listed unknowns
 // (the grid is fixed per level, so the partials do not depend on scheduling).
@@ -531,6 +582,15 @@ int exact_grid(uint32_t n, int per) {
   return b < 1 ? 1 : (int)b;
 }
 
+// grid for n row segments: kSegSlots lanes per segment, two segments per
+// group of lanes for long lists
+int seg_grid(uint32_t n) {
+  const long long groups_per_block = (long long)kListBlock / kSegSlots;
+  const int per = (long long)n < 4LL * device_sms() * groups_per_block * 2 ? 1 : 2;
+  const long long b = ((long long)n + groups_per_block * per - 1) / (groups_per_block * per);
+  return b < 1 ? 1 : (int)b;
+}
+
 template <typename T>
 bool small_smem(const Geom& g) {
   return 2 * g.total * (long long)sizeof(T) <= kSmallSmemBytes;
@@ -569,8 +629,38 @@ ListArgs<T> list_args(const LevelDev& L, int order, int colour) {
   return a;
 }
 
+// level 0 by row segments (gs_seg_kernel), when the hierarchy keeps them
+template <typename T>
+cudaError_t half_sweep_seg(const LevelDev& L, int colour, bool update, cudaStream_t s) {
+  ListArgs<T> a = list_args<T>(L, 2, colour);
+  a.phi64 = L.phi[colour];
+  a.list = L.list[0][colour];
+  a.count = L.count + colour;
+  const int grid = seg_grid(L.hcount[colour]);
+  count_launch();
+  if (update) {
+    if (sizeof(T) != 4) return cudaErrorInvalidValue;
+    launch_pdl(gs_seg_kernel<T, true, false, false>, dim3(grid), dim3(kListBlock), 0, s, a);
+    return cudaGetLastError();
+  }
+  if (sizeof(T) == 8 && L.rhsd[0]) {
+    a.rhsd = (const T*)L.rhsd[colour];
+    if constexpr (sizeof(T) == 8) {
+      if (L.exact_sum) {
+        launch_pdl(gs_seg_kernel<T, false, true, true>, dim3(grid), dim3(kListBlock), 0, s, a);
+        return cudaGetLastError();
+      }
+    }
+    launch_pdl(gs_seg_kernel<T, false, true, false>, dim3(grid), dim3(kListBlock), 0, s, a);
+    return cudaGetLastError();
+  }
+  launch_pdl(gs_seg_kernel<T, false, false, false>, dim3(grid), dim3(kListBlock), 0, s, a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, bool update, cudaStream_t s) {
+  if (L.level == 0 && L.list[0][colour]) return half_sweep_seg<T>(L, colour, update, s);
   ListArgs<T> a = list_args<T>(L, order, colour);
   a.phi64 = L.phi[colour];
   const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], PerThread<T>::value);

@@ -167,12 +167,21 @@ Geom make_geom(int nx, int ny, int nz) {
   return g;
 }
 
+// The lists a level keeps, by order: 1 and 2 on coarse levels; level 0 has
+// one active set (order 2, aliased as order 1) and, when the fine level
+// sweeps by row segments, its segment lists in slot 0.
+std::vector<int> list_orders(int level, bool seg) {
+  if (level > 0) return {1, 2};
+  if (seg) return {0, 2};
+  return {2};
+}
+
 bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
          (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
-         (o.fp64_sum == 0 || o.fp64_sum == 1);
+         (o.fp64_sum == 0 || o.fp64_sum == 1) && (o.fine_segments == 0 || o.fine_segments == 1);
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -667,6 +676,7 @@ void mg_default_options(mg_options* opt) {
   opt->coarse_cluster = 0;
   opt->smoother_pass = 0;
   opt->fp64_sum = 1;
+  opt->fine_segments = 1;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -757,6 +767,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     size_t f_phi[2], f_rhs[2], f_invd[2], f_diag[2];
   } off[kMaxLevels];
   const bool mixed = o.precision == 1;
+  const bool seg = o.fine_segments == 1;
   for (int l = 0; l < H->nlev; ++l) {
     Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
     H->L[l].g = g;
@@ -765,8 +776,8 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       off[l].phi[c] = A.reserve(sizeof(double) * g.total);
       off[l].rhs[c] = A.reserve(sizeof(double) * g.total);
       off[l].code[c] = A.reserve(g.total);
-      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
-        off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)g.hx * g.ny * g.nz);
+      for (int o : list_orders(l, seg))
+        off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)list_job_slots(g, o == 0 ? kSegShift : 0));
       if (mixed) {
         off[l].f_phi[c] = A.reserve(sizeof(float) * g.total);
         off[l].f_rhs[c] = A.reserve(sizeof(float) * g.total);
@@ -788,15 +799,16 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   unsigned lblocks = 0;
   for (int l = 0; l < H->nlev; ++l) {
     const Geom& g = H->L[l].g;
-    const unsigned nb = (unsigned)(((long long)g.hx * g.ny * g.nz + 255) / 256);
-    for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+    for (int o : list_orders(l, seg))
       for (int c = 0; c < 2; ++c) {
         ListJob j = {};
         j.g = g;
+        j.seg_shift = o == 0 ? kSegShift : 0;
+        const unsigned nb = (unsigned)((list_job_slots(g, j.seg_shift) + 255) / 256);
         j.block0 = lblocks;
         j.nblocks = nb;
         j.colour = c;
-        j.bit = o == 2 ? kActive2 : kActive1;
+        j.bit = o == 1 ? kActive1 : kActive2;
         ljobs.push_back(j);
         lblocks += nb;
       }
@@ -855,9 +867,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       H->L[l].phi[c] = (double*)(base + off[l].phi[c]);
       H->L[l].rhs[c] = (double*)(base + off[l].rhs[c]);
       H->L[l].code[c] = (uint8_t*)(base + off[l].code[c]);
-      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o) H->L[l].list[o][c] = (uint32_t*)(base + off[l].list[o][c]);
-      if (l == 0) H->L[l].list[1][c] = H->L[l].list[2][c];
       H->L[l].list[0][c] = nullptr;
+      for (int o : list_orders(l, seg)) H->L[l].list[o][c] = (uint32_t*)(base + off[l].list[o][c]);
+      if (l == 0) H->L[l].list[1][c] = H->L[l].list[2][c];
       LevelDev& Lm = H->L[l];
       Lm.phi32[c] = mixed ? (float*)(base + off[l].f_phi[c]) : nullptr;
       Lm.rhs32[c] = mixed ? (float*)(base + off[l].f_rhs[c]) : nullptr;
@@ -915,7 +927,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   if (st == MG_OK) {
     size_t jn = 0;
     for (int l = 0; l < H->nlev; ++l)
-      for (int o = (l == 0 ? 2 : 1); o <= 2; ++o)
+      for (int o : list_orders(l, seg))
         for (int c = 0; c < 2; ++c, ++jn) {
           ljobs[jn].code = H->L[l].code[c];
           ljobs[jn].list = H->L[l].list[o][c];

@@ -100,6 +100,9 @@ struct LevelDev {
   // has one active set: list[1] == list[2].  count[order*2 + colour] is the
   // list length (device memory, so captured graphs stay valid when the mask
   // changes).
+  // Level 0 also keeps, in list[0][c] and count[c], the row segments of
+  // kSegSlots slots of colour c that hold an active cell (ListJob with
+  // seg_shift kSegShift; nullptr when the hierarchy sweeps by cell lists).
   uint32_t* list[3][2];
   uint32_t* count;
   uint32_t hcount[6];  // host copy of count (sizes the launch grids)
@@ -118,6 +121,11 @@ enum { kFP64 = 0, kFP32 = 1 };
 
 constexpr uint32_t kListAt = 0x7fffffffu;
 constexpr uint32_t kListPlusX = 0x80000000u;
+// Row segments of the fine level: 8 slots (16 cells).  A segment never
+// reaches past its row's padding: q0 + 8 = 8 ceil(hx / 8) <= P since P is a
+// multiple of 16 with P >= hx + 1, and padding slots hold code 0.
+constexpr int kSegShift = 3;
+constexpr int kSegSlots = 1 << kSegShift;
 
 struct FineExtra {
   double* rhoh2[2];  // h^2 rho, split layout
@@ -154,6 +162,10 @@ cudaError_t launch_coarse_coeffs(const LevelDev& Lc, unsigned long long* counts2
 // three launches).  block0: the job's first block in the launch, nblocks
 // its blocks of kListThreads (256) slots; the scratch holds one word per
 // block of all jobs.
+// With seg_shift > 0 the job lists row segments instead of cells: the
+// 2^seg_shift consecutive slots of one colour's half-row starting at slot
+// q0 = t 2^seg_shift, for every segment with an active slot, written as the
+// offset of slot q0 with the row's x-direction bit (the same entry format).
 struct ListJob {
   Geom g;
   const uint8_t* code;
@@ -162,7 +174,13 @@ struct ListJob {
   unsigned block0, nblocks;
   int colour;
   uint8_t bit;
+  int seg_shift;
 };
+// list entries a job scans (cells, or row segments with seg_shift > 0)
+__host__ __device__ inline long long list_job_slots(const Geom& g, int seg_shift) {
+  const long long per_row = seg_shift ? (g.hx + (1 << seg_shift) - 1) >> seg_shift : g.hx;
+  return per_row * g.ny * g.nz;
+}
 cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_blocks, uint32_t* scratch,
                                cudaStream_t s);
 // Buffers of `words` 8-byte words to zero, and FP64 -> FP32 copies, many

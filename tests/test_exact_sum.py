@@ -7,8 +7,8 @@ host through tests/host/exact_sum_check.cu, against exact arithmetic:
   - everywhere else it is within half an ulp of the result plus 5 units of
     2^(e_max - 1082) of the exact rational sum (fractions.Fraction);
   - the documented edge cases: subnormal terms count as zero, sums whose
-    largest term is below 2^-959 are zero, overflow gives an infinity, and a
-    non-finite term gives the plain left-to-right sum.
+    largest term is below 2^-959 are zero, overflow gives an infinity, and
+    non-finite terms give the non-finite value IEEE addition gives.
 tests/test_gpu_exact_sum.py checks that the GPU computes the same bits."""
 import math
 import os
@@ -111,6 +111,7 @@ def check_against_exact(sets, got):
             plain = x[0]
             for v in x[1:]:
                 plain += v
+            # NaN, or the infinity IEEE addition gives
             ok = (math.isnan(plain) and math.isnan(r)) or plain == r
             if not ok:
                 fails.append((x, r, "non-finite"))
