@@ -104,11 +104,13 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  six; 0 = five FP64 additions.  Both are accurate to about
  *                  one rounding of the sum; the results differ in the last
  *                  bits.
- *  fine_segments   level-0 Gauss-Seidel sweeps: 1 = one thread per slot of
- *                  the row segments (8 slots of one colour's half-row) that
- *                  hold an active cell, so that a warp reads whole runs of
- *                  every array; 0 = one thread per active cell of the
- *                  colour's compact list.  The results are bit-identical. */
+ *  fine_segments   mixed form, level-0 FP32 Gauss-Seidel sweeps: 1, 2 = one
+ *                  thread per slot of the row segments (8, 16 slots of one
+ *                  colour's half-row) that hold an active cell, so that a
+ *                  warp reads whole runs of every array; 0 = one thread per
+ *                  active cell of the colour's compact list.  The results
+ *                  are bit-identical.  (The FP64 sweeps always use the cell
+ *                  lists.) */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;

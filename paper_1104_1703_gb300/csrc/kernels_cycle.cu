@@ -108,51 +108,66 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   }
 }
 
-// K4 on level 0 over row segments (list[0] of level 0): a group of
-// kSegSlots lanes takes one segment, lane l its slot q0 + l, so that every
-// array is read in runs of consecutive slots; PER segments per group are in
-// flight at once.  A lane on an inactive or padding slot (code 0) writes 0,
-// the value such a slot always holds, so the group writes whole runs.  The
-// arithmetic per active cell is gs_list_kernel's, with the same options.
-template <typename T, bool UPDATE, bool SCALED, bool EXACT>
+// K4 on level 0 of the mixed form's FP32 cycles, over row segments
+// (list[0] of level 0): a group of 2^SHIFT lanes takes one segment, lane l
+// its slot q0 + l, so that every array is read in runs of consecutive
+// slots; PER segments per group are in flight at once.  A lane on an
+// inactive or padding slot (code 0) writes 0, the value such a slot always
+// holds, so the group writes whole runs.  The grid is persistent (a few
+// blocks per SM) and each group loads the segment entries of its next round
+// before it works on the current one, which takes the entry load off the
+// chain of dependent loads.  The arithmetic per active cell is
+// gs_list_kernel's.  (The FP64 sweeps keep the cell lists: their integer
+// neighbour sum makes them instruction-bound, and a segment's idle lanes
+// would add to that.)
+template <typename T, bool UPDATE, int SHIFT>
 __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
   pdl_wait();
   constexpr int PER = 2;
-  constexpr int GROUPS = 32 / kSegSlots;  // segments per warp and round
+  constexpr int GROUPS = 32 >> SHIFT;  // segments per warp and round
   __shared__ T tab[16];
   init_tab(tab);
   const uint32_t n = *a.count;
   const int lane = threadIdx.x & 31;
-  const int l = lane & (kSegSlots - 1);
-  const uint32_t group = ((blockIdx.x * kListBlock + threadIdx.x) >> 5) * GROUPS + (lane >> kSegShift);
+  const int l = lane & ((1 << SHIFT) - 1);
+  const uint32_t group = ((blockIdx.x * kListBlock + threadIdx.x) >> 5) * GROUPS + (lane >> SHIFT);
   const uint32_t ngroups = (gridDim.x * kListBlock >> 5) * GROUPS;
-  for (uint32_t base = group; base < n; base += PER * ngroups) {
+  const uint32_t step = PER * ngroups;
+  uint32_t next[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t i = group + u * ngroups;
+    next[u] = i < n ? a.list[i] : 0u;
+  }
+  for (uint32_t base = group; base < n; base += step) {
+    uint32_t cur[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      cur[u] = next[u];
+      const uint32_t i = base + step + u * ngroups;
+      next[u] = i < n ? a.list[i] : 0u;
+    }
     long long at[PER];
     T s[PER], b[PER], d[PER];
     bool ok[PER], act[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t i = base + u * ngroups;
-      ok[u] = i < n;
-      const uint32_t e = ok[u] ? a.list[i] : 0u;
+      const uint32_t e = cur[u];
       at[u] = (long long)(e & kListAt);
-      ok[u] = ok[u] && entry_ok(a.g, at[u], 9);
+      ok[u] = base + u * ngroups < n && entry_ok(a.g, at[u], 9);
       at[u] += l;
       if (ok[u]) {
         const uint8_t code = a.code[at[u]];
         act[u] = (code & kActive2) != 0;
-        if constexpr (EXACT)
-          s[u] = nbr_sum_exact(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-        else
-          s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-        b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
+        s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        b[u] = a.rhs[at[u]];
         d[u] = tab[__popc((unsigned)code >> kGhostShift)];
       }
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (!ok[u]) continue;
-      const T v = SCALED ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+      const T v = (s[u] - b[u]) * d[u];
       a.self[at[u]] = act[u] ? v : T(0);
       if (UPDATE && act[u]) a.phi64[at[u]] += widen_f32(v);
     }
@@ -582,12 +597,14 @@ int exact_grid(uint32_t n, int per) {
   return b < 1 ? 1 : (int)b;
 }
 
-// grid for n row segments: kSegSlots lanes per segment, two segments per
-// group of lanes for long lists
-int seg_grid(uint32_t n) {
-  const long long groups_per_block = (long long)kListBlock / kSegSlots;
-  const int per = (long long)n < 4LL * device_sms() * groups_per_block * 2 ? 1 : 2;
-  const long long b = ((long long)n + groups_per_block * per - 1) / (groups_per_block * per);
+// grid for n row segments of 2^shift slots (one lane per slot), at most
+// the blocks that stay resident together (8 per SM at 256 threads), which
+// then loop
+int seg_grid(uint32_t n, int shift) {
+  const long long groups_per_block = (long long)kListBlock >> shift;
+  long long b = ((long long)n + groups_per_block - 1) / groups_per_block;
+  const long long cap = 8LL * device_sms();
+  if (b > cap) b = cap;
   return b < 1 ? 1 : (int)b;
 }
 
@@ -629,38 +646,29 @@ ListArgs<T> list_args(const LevelDev& L, int order, int colour) {
   return a;
 }
 
-// level 0 by row segments (gs_seg_kernel), when the hierarchy keeps them
-template <typename T>
+// level 0 of the FP32 cycles by row segments (gs_seg_kernel), when the
+// hierarchy keeps them
+template <int SHIFT>
 cudaError_t half_sweep_seg(const LevelDev& L, int colour, bool update, cudaStream_t s) {
-  ListArgs<T> a = list_args<T>(L, 2, colour);
+  ListArgs<float> a = list_args<float>(L, 2, colour);
   a.phi64 = L.phi[colour];
   a.list = L.list[0][colour];
   a.count = L.count + colour;
-  const int grid = seg_grid(L.hcount[colour]);
+  const int grid = seg_grid(L.hcount[colour], SHIFT);
   count_launch();
-  if (update) {
-    if (sizeof(T) != 4) return cudaErrorInvalidValue;
-    launch_pdl(gs_seg_kernel<T, true, false, false>, dim3(grid), dim3(kListBlock), 0, s, a);
-    return cudaGetLastError();
-  }
-  if (sizeof(T) == 8 && L.rhsd[0]) {
-    a.rhsd = (const T*)L.rhsd[colour];
-    if constexpr (sizeof(T) == 8) {
-      if (L.exact_sum) {
-        launch_pdl(gs_seg_kernel<T, false, true, true>, dim3(grid), dim3(kListBlock), 0, s, a);
-        return cudaGetLastError();
-      }
-    }
-    launch_pdl(gs_seg_kernel<T, false, true, false>, dim3(grid), dim3(kListBlock), 0, s, a);
-    return cudaGetLastError();
-  }
-  launch_pdl(gs_seg_kernel<T, false, false, false>, dim3(grid), dim3(kListBlock), 0, s, a);
+  if (update)
+    launch_pdl(gs_seg_kernel<float, true, SHIFT>, dim3(grid), dim3(kListBlock), 0, s, a);
+  else
+    launch_pdl(gs_seg_kernel<float, false, SHIFT>, dim3(grid), dim3(kListBlock), 0, s, a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t half_sweep_t(const LevelDev& L, int order, int colour, bool update, cudaStream_t s) {
-  if (L.level == 0 && L.list[0][colour]) return half_sweep_seg<T>(L, colour, update, s);
+  if constexpr (sizeof(T) == 4) {
+    if (L.level == 0 && L.seg_shift == 3) return half_sweep_seg<3>(L, colour, update, s);
+    if (L.level == 0 && L.seg_shift == 4) return half_sweep_seg<4>(L, colour, update, s);
+  }
   ListArgs<T> a = list_args<T>(L, order, colour);
   a.phi64 = L.phi[colour];
   const int grid = exact_grid(L.hcount[list_order(L, order) * 2 + colour], PerThread<T>::value);

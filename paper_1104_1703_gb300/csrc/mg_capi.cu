@@ -181,7 +181,7 @@ bool valid_options(const mg_options& o) {
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
          (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
-         (o.fp64_sum == 0 || o.fp64_sum == 1) && (o.fine_segments == 0 || o.fine_segments == 1);
+         (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 1;
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -767,7 +767,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     size_t f_phi[2], f_rhs[2], f_invd[2], f_diag[2];
   } off[kMaxLevels];
   const bool mixed = o.precision == 1;
-  const bool seg = o.fine_segments == 1;
+  // fine_segments 1, 2: row segments of 8, 16 slots for the FP32 sweeps
+  const bool seg = mixed && o.fine_segments >= 1;
+  const int seg_shift = seg ? kSegShiftMin + o.fine_segments - 1 : 0;
   for (int l = 0; l < H->nlev; ++l) {
     Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
     H->L[l].g = g;
@@ -777,7 +779,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       off[l].rhs[c] = A.reserve(sizeof(double) * g.total);
       off[l].code[c] = A.reserve(g.total);
       for (int o : list_orders(l, seg))
-        off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)list_job_slots(g, o == 0 ? kSegShift : 0));
+        off[l].list[o][c] = A.reserve(sizeof(uint32_t) * (size_t)list_job_slots(g, o == 0 ? seg_shift : 0));
       if (mixed) {
         off[l].f_phi[c] = A.reserve(sizeof(float) * g.total);
         off[l].f_rhs[c] = A.reserve(sizeof(float) * g.total);
@@ -803,7 +805,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
       for (int c = 0; c < 2; ++c) {
         ListJob j = {};
         j.g = g;
-        j.seg_shift = o == 0 ? kSegShift : 0;
+        j.seg_shift = o == 0 ? seg_shift : 0;
         const unsigned nb = (unsigned)((list_job_slots(g, j.seg_shift) + 255) / 256);
         j.block0 = lblocks;
         j.nblocks = nb;
@@ -889,6 +891,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   for (int l = 0; l < H->nlev; ++l) {
     H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
     H->L[l].exact_sum = (l == 0 && !mixed && o.fp64_sum == 1) ? 1 : 0;
+    H->L[l].seg_shift = l == 0 ? seg_shift : 0;
   }
   for (int c = 0; c < 2; ++c) {
     H->L[0].rhsd[c] = mixed ? nullptr : (double*)(base + o_rhsd[c]);

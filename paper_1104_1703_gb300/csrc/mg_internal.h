@@ -101,13 +101,15 @@ struct LevelDev {
   // list length (device memory, so captured graphs stay valid when the mask
   // changes).
   // Level 0 also keeps, in list[0][c] and count[c], the row segments of
-  // kSegSlots slots of colour c that hold an active cell (ListJob with
-  // seg_shift kSegShift; nullptr when the hierarchy sweeps by cell lists).
+  // 2^seg_shift slots of colour c that hold an active cell (ListJob with
+  // that seg_shift; nullptr and seg_shift 0 when the hierarchy sweeps by
+  // cell lists).
   uint32_t* list[3][2];
   uint32_t* count;
   uint32_t hcount[6];  // host copy of count (sizes the launch grids)
   double* rhsd[2];     // level 0 of the FP64 method: b / D (nullptr elsewhere)
   int exact_sum = 0;   // level 0 of the FP64 method: neighbour sums in integer arithmetic (exact_sum.cuh)
+  int seg_shift = 0;   // level 0: log2 of the row-segment length (0: no segment lists)
   // FP32 copies for the inner cycles of the mixed-precision form (nullptr
   // when the hierarchy was created for FP64 only); level 0: phi32 is the
   // correction e, rhs32 is -r^ of the FP64 residual.
@@ -121,11 +123,11 @@ enum { kFP64 = 0, kFP32 = 1 };
 
 constexpr uint32_t kListAt = 0x7fffffffu;
 constexpr uint32_t kListPlusX = 0x80000000u;
-// Row segments of the fine level: 8 slots (16 cells).  A segment never
-// reaches past its row's padding: q0 + 8 = 8 ceil(hx / 8) <= P since P is a
-// multiple of 16 with P >= hx + 1, and padding slots hold code 0.
-constexpr int kSegShift = 3;
-constexpr int kSegSlots = 1 << kSegShift;
+// Row segments of the fine level: 8 or 16 slots (16 or 32 cells).  A
+// segment never reaches past its row's padding: q0 + 2^s = 2^s ceil(hx / 2^s)
+// <= P for s <= 4 since P is a multiple of 16 with P >= hx + 1, and padding
+// slots hold code 0.
+constexpr int kSegShiftMin = 3, kSegShiftMax = 4;
 
 struct FineExtra {
   double* rhoh2[2];  // h^2 rho, split layout
