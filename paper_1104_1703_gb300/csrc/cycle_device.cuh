@@ -207,6 +207,8 @@ struct BottomLevel {
   const uint32_t* list[2];   // unknowns of this order, per colour
   const uint32_t* count;     // their numbers (device memory), [colour]
   long long smem_off;    // element offset of this level's staged arrays (phi0, phi1, rhs0, rhs1)
+  long long rec_off;     // byte offset of this level's unknown records in shared memory
+  uint32_t nrec[2];      // their numbers per colour (the host's copy of count)
 };
 
 template <typename T>
@@ -216,83 +218,165 @@ struct BottomArgs {
   uint8_t bit;
   int n_pre, n_post, coarse_sweeps;
   int n_cycles;  // coarse iterations per level (Section 5.3): 1 V-cycle, 2 or more W-cycle
+  int first_smem;  // levels first_smem .. nlev-1 are staged in shared memory (with SMEM)
 };
 
-// a level's working arrays: staged in shared memory for the whole kernel
+// a level's working arrays: its records (list entries and, second order,
+// 1/D per unknown) always in shared memory, its correction and right-hand
+// side there when staged
 template <typename T>
 struct BottomView {
   Geom g;
   T* phi[2];
   T* rhs[2];
-  const T* invd[2];
   const T* diag[2];
   const uint8_t* code[2];
-  const uint32_t* list[2];
+  uint32_t* list[2];  // shared-memory copies of the lists
+  T* rinvd[2];        // 1/D of the listed unknowns, in list order (second order)
   uint32_t n[2];
 };
+
+// Shared-memory plan of a bottom launch over levels lb .. lb + a.nlev - 1
+// (host side): first the unknown records of every level (read by every
+// step: in shared memory they cost no global round trip), then the
+// correction and right-hand side of the deepest levels that still fit.
+// Returns the dynamic shared memory bytes.
+template <typename T>
+size_t plan_bottom_smem(BottomArgs<T>& a, const LevelDev* levels, int lb, int order) {
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  size_t off = 0;
+  for (int i = 0; i < a.nlev; ++i) {
+    const LevelDev& L = levels[lb + i];
+    a.L[i].nrec[0] = L.hcount[order * 2];
+    a.L[i].nrec[1] = L.hcount[order * 2 + 1];
+    const size_t n = (size_t)a.L[i].nrec[0] + a.L[i].nrec[1];
+    a.L[i].rec_off = (long long)off;
+    off += al(4 * n) + al(sizeof(T) * n);
+  }
+  a.first_smem = a.nlev;
+  size_t staged = 0;
+  for (int i = a.nlev - 1; i >= 0; --i) {
+    const size_t need = 4 * (size_t)levels[lb + i].g.total * sizeof(T);
+    if (off + staged + need > (size_t)kBottomSmemBytes) break;
+    staged += need;
+    a.first_smem = i;
+  }
+  long long e = (long long)(off / sizeof(T));
+  for (int i = 0; i < a.nlev; ++i) {
+    a.L[i].smem_off = e;
+    if (i >= a.first_smem) e += 4 * levels[lb + i].g.total;
+  }
+  return (size_t)e * sizeof(T);
+}
 
 // Gauss-Seidel sweeps of one bottom level over its lists of unknowns.  A
 // level with at most 64 unknowns per colour is swept by warp 0 alone, with
 // warp-level barriers between the half-sweeps (the deepest level of a
 // complex domain often has a handful of unknowns and gets 2 * coarse_sweeps
-// half-sweeps); otherwise the whole block works and synchronises.
+// half-sweeps); otherwise the whole block works and synchronises.  Such a
+// sweep is bound by the latency of its dependent chain, so up to two
+// unknowns per colour and thread (every level the bottom takes, at 1024
+// threads) each thread first loads what stays fixed over the sweeps (slot,
+// x-direction, 1/D and b) into registers, and a half-sweep is only the six
+// neighbour loads, the update and its store.  (The arithmetic is the list
+// kernels', so a level gives the same bits in the bottom as outside it.)
 template <int KIND, typename T>
 __device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
   const Geom& g = L.g;
   const bool one_warp = L.n[0] <= 64 && L.n[1] <= 64;
-  if (one_warp) {
-    if (threadIdx.x < 32) {
-      for (int s = 0; s < sweeps; ++s)
-        for (int c = 0; c < 2; ++c) {
-          for (uint32_t i = threadIdx.x; i < L.n[c]; i += 32) {
-            const uint32_t e = L.list[c][i];
-            const long long at = e & kListAt;
-            if (!entry_ok(g, at, 1)) continue;
-            L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
-                           inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
-          }
-          __syncwarp();
-        }
-    }
+  const unsigned nthr = one_warp ? 32u : blockDim.x;
+  if (threadIdx.x >= nthr) {
     __syncthreads();
     return;
   }
-  for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < 2; ++c) {
-      for (uint32_t i = threadIdx.x; i < L.n[c]; i += blockDim.x) {
-        const uint32_t e = L.list[c][i];
-        const long long at = e & kListAt;
-        if (!entry_ok(g, at, 2)) continue;
-        L.phi[c][at] = (nbr_sum<T>(L.phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
-                       inv_diag<KIND>(0, L.invd[c], at, (const T*)nullptr);
+  T* const phi[2] = {L.phi[0], L.phi[1]};
+  const int P = g.P;
+  const long long sz = g.sz;
+  if (L.n[0] <= 2 * nthr && L.n[1] <= 2 * nthr) {
+    long long at[2][2];
+    int dx[2][2];
+    T id[2][2], b[2][2];
+    bool has[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t i = threadIdx.x + k * nthr;
+        has[c][k] = i < L.n[c];
+        const uint32_t e = has[c][k] ? L.list[c][i] : 0u;
+        at[c][k] = e & kListAt;
+        has[c][k] = has[c][k] && entry_ok(g, at[c][k], one_warp ? 1 : 2);
+        dx[c][k] = (e & kListPlusX) ? 1 : -1;
+        id[c][k] = has[c][k] ? (KIND == 1 ? L.rinvd[c][i] : T(1) / T(6)) : T(0);
+        b[c][k] = has[c][k] ? L.rhs[c][at[c][k]] : T(0);
       }
-      __syncthreads();
-    }
+    for (int s = 0; s < sweeps; ++s)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (has[c][k]) phi[c][at[c][k]] = (nbr_sum<T>(phi[c ^ 1], at[c][k], dx[c][k], P, sz) - b[c][k]) * id[c][k];
+        if (one_warp) __syncwarp();
+        else __syncthreads();
+      }
+  } else {
+    for (int s = 0; s < sweeps; ++s)
+      for (int c = 0; c < 2; ++c) {
+        for (uint32_t i = threadIdx.x; i < L.n[c]; i += nthr) {
+          const uint32_t e = L.list[c][i];
+          const long long at = e & kListAt;
+          if (!entry_ok(g, at, 2)) continue;
+          phi[c][at] = (nbr_sum<T>(phi[c ^ 1], at, (e & kListPlusX) ? 1 : -1, g.P, g.sz) - L.rhs[c][at]) *
+                       (KIND == 1 ? L.rinvd[c][i] : T(1) / T(6));
+        }
+        if (one_warp) __syncwarp();
+        else __syncthreads();
+      }
+  }
+  if (one_warp) __syncthreads();
 }
 
 // residual of level f and R1 into level f+1 in one pass over the coarse
 // cells (each coarse cell evaluates its own children): b = -1/2 sum r^,
 // dPhi = 0.  Children of the black colour carry no residual after a full
-// sweep (black_zero).
+// sweep (black_zero).  The children's codes and diagonals (global memory)
+// are loaded together, in one round trip, before the residuals, which are
+// summed in the order (dk, dj, colour) as restrict_kernel does.  Rows and
+// planes past the level's end are its zero halo, whose codes are 0.
 template <int KIND, typename T>
 __device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, bool black_zero) {
-  const Geom& g = F.g;
-  const Geom& gc = C.g;
+  const Geom g = F.g;
+  const Geom gc = C.g;
   const int nc = gc.nx * gc.ny * gc.nz;
+  const int ncol = black_zero ? 1 : 2;
   for (int e = threadIdx.x; e < nc; e += blockDim.x) {
     const int I = e % gc.nx, t = e / gc.nx, J = t % gc.ny, K = t / gc.ny;
-    T sum = 0;
+    long long at[2][2];
+    bool act[2][2][2];
+    T dg[2][2][2];
+#pragma unroll
     for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
       for (int dj = 0; dj < 2; ++dj) {
-        const int j = 2 * J + dj, k = 2 * K + dk;
-        if (j >= g.ny || k >= g.nz) continue;
-        const long long at = g.at(I, j, k);
-        for (int c = 0; c < (black_zero ? 1 : 2); ++c) {
-          if (!(F.code[c][at] & bit)) continue;
-          const T nb = nbr_sum<T>(F.phi[c ^ 1], at, x_offset(c, j, k), g.P, g.sz);
-          sum += fma(-diag_of<KIND>(0, F.diag[c], at, (const T*)nullptr), F.phi[c][at], nb) - F.rhs[c][at];
+        at[dk][dj] = g.at(I, 2 * J + dj, 2 * K + dk);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          act[dk][dj][c] = c < ncol && (F.code[c][at[dk][dj]] & bit);
+          dg[dk][dj][c] = diag_of<KIND>(0, F.diag[c], at[dk][dj], (const T*)nullptr);
         }
       }
+    T sum = 0;
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (act[dk][dj][c]) {
+            const long long a = at[dk][dj];
+            const T nb = nbr_sum<T>(F.phi[c ^ 1], a, x_offset(c, 2 * J + dj, 2 * K + dk), g.P, g.sz);
+            sum += fma(-dg[dk][dj][c], F.phi[c][a], nb) - F.rhs[c][a];
+          }
     const int Cc = (I + J + K) & 1;
     const long long atc = gc.at(I >> 1, J, K);
     C.rhs[Cc][atc] = T(-0.5) * sum;
@@ -302,16 +386,17 @@ __device__ void bottom_restrict(const BottomView<T>& F, const BottomView<T>& C, 
 }
 
 
-// P2 of level f+1 into the unknowns of level f
+// P2 of level f+1 into the listed unknowns of level f (their records in
+// shared memory give the slots, as prolong_list_kernel's lists do)
 template <typename T>
-__device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, uint8_t bit, int first_colour) {
+__device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, int first_colour) {
   const Geom& g = F.g;
-  const int n = g.hx * g.ny * g.nz;
   for (int c = first_colour; c < 2; ++c)
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int q = e % g.hx, t = e / g.hx, j = t % g.ny, k = t / g.ny;
-      const long long at = g.at(q, j, k);
-      if (!(F.code[c][at] & bit)) continue;
+    for (uint32_t i = threadIdx.x; i < F.n[c]; i += blockDim.x) {
+      const long long at = F.list[c][i] & kListAt;
+      if (!entry_ok(g, at, 11)) continue;
+      int q, j, k;
+      g.slot_of(at, &q, &j, &k);
       const T w = p2_sum(C.g, (const T*)C.phi[0], (const T*)C.phi[1], q, j, k, c, PlainLoad());
       F.phi[c][at] = fma(w, T(1) / T(64), F.phi[c][at]);
     }
@@ -323,11 +408,12 @@ __device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, u
 // lb .. deepest, inside one CTA, from level lb's current state: its
 // right-hand side as the restriction left it and its correction (zero on
 // the first of a W-cycle's visits, the previous visit's result after that).
-// With SMEM the correction and right-hand side of every level (halo
-// included) live in shared memory for the whole kernel, so the many
-// barrier-separated steps (2 * coarse_sweeps of them on each visit of the
-// deepest level) read on-chip data that the previous step wrote; the results
-// go back to global memory at the end.  Each step is a block-strided loop
+// With SMEM the correction and right-hand side of the deepest levels (from
+// first_smem on, halo included) live in shared memory for the whole kernel,
+// so the many barrier-separated steps (2 * coarse_sweeps of them on each
+// visit of the deepest level) read on-chip data that the previous step
+// wrote; the results go back to global memory at the end.  Levels above
+// first_smem (too large to stage) work in global memory.  Each step is a block-strided loop
 // over the level's slots closed by __syncthreads.  This replaces about six
 // launches per level visit and the 2 * coarse_sweeps launches of each
 // coarsest solve.
@@ -335,37 +421,111 @@ template <int KIND, typename T, bool SMEM>
 __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
-  if (threadIdx.x == 0)
-    for (int i = 0; i < a.nlev; ++i) {
+  // thread i sets up level i (the list lengths are global loads: made at
+  // once rather than one after another)
+  if (threadIdx.x < (unsigned)a.nlev) {
+    const int i = threadIdx.x;
+    {
       const BottomLevel<T>& L = a.L[i];
       V[i].g = L.g;
+      const bool st = SMEM && i >= a.first_smem;
+      const uint32_t nr = L.nrec[0] + L.nrec[1];
+      uint32_t* rl = reinterpret_cast<uint32_t*>(smem_raw + L.rec_off);
+      T* ri = reinterpret_cast<T*>(smem_raw + L.rec_off + ((4 * (size_t)nr + 15) & ~(size_t)15));
       for (int c = 0; c < 2; ++c) {
-        V[i].phi[c] = SMEM ? sm + L.smem_off + c * L.g.total : L.phi[c];
-        V[i].rhs[c] = SMEM ? sm + L.smem_off + (2 + c) * L.g.total : L.rhs[c];
-        V[i].invd[c] = L.invd[c];
+        V[i].phi[c] = st ? sm + L.smem_off + c * L.g.total : L.phi[c];
+        V[i].rhs[c] = st ? sm + L.smem_off + (2 + c) * L.g.total : L.rhs[c];
         V[i].diag[c] = L.diag[c];
         V[i].code[c] = L.code[c];
-        V[i].list[c] = L.list[c];
-        V[i].n[c] = L.count[c];
+        V[i].list[c] = rl + (c ? L.nrec[0] : 0);
+        V[i].rinvd[c] = ri + (c ? L.nrec[0] : 0);
+        // the device count, bounded by the records planned for it (the two
+        // agree: the host copy is read after every list build)
+        const uint32_t n = L.count[c];
+        V[i].n[c] = n < L.nrec[c] ? n : L.nrec[c];
       }
     }
+  }
   __syncthreads();
-  if (SMEM) {
-    // stage: level lb's b, and its dPhi (zero after the restriction, so
-    // read only for a W-cycle, whose later visits start from the previous
-    // one's result); the deeper levels are fully written before they are
-    // read, except their zero halo
-    const bool keep = a.n_cycles > 1;
-    for (int i = 0; i < a.nlev; ++i) {
-      const long long tot = a.L[i].g.total;
-      for (int c = 0; c < 2; ++c)
-        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-          V[i].phi[c][e] = i == 0 && keep ? a.L[0].phi[c][e] : T(0);
-          V[i].rhs[c][e] = i == 0 ? a.L[0].rhs[c][e] : T(0);
+  // Staging, as batches of independent global loads (each costs one round
+  // trip to L2, far longer than the arithmetic of a small level):
+  //  - the unknown records of every level, over one flat index: list
+  //    entries, then (second order) 1/D of each listed unknown;
+  //  - with SMEM, level lb's b and (W-cycle: later visits start from the
+  //    previous one's result) its dPhi; the deeper staged levels are fully
+  //    written before they are read except their zero halo, so they are
+  //    zeroed.
+  __shared__ uint32_t seg_end[2 * kBottomMaxLevels];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < 2 * a.nlev; ++k) {
+      run += V[k >> 1].n[k & 1];
+      seg_end[k] = run;
+    }
+  }
+  __syncthreads();
+  {
+    const uint32_t total = seg_end[2 * a.nlev - 1];
+    constexpr int U = 4;
+    for (uint32_t r0 = threadIdx.x; r0 < total; r0 += U * blockDim.x) {
+      uint32_t ent[U], idx[U];
+      int seg[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t r = r0 + u * blockDim.x;
+        int k = 0;
+        while (k < 2 * a.nlev - 1 && r >= seg_end[k]) ++k;
+        seg[u] = k;
+        idx[u] = r - (k ? seg_end[k - 1] : 0u);
+        ent[u] = r < total ? a.L[k >> 1].list[k & 1][idx[u]] : 0u;
+      }
+      T iv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        iv[u] = (KIND == 1 && r0 + u * blockDim.x < total)
+                    ? a.L[seg[u] >> 1].invd[seg[u] & 1][ent[u] & kListAt] : T(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (r0 + u * blockDim.x < total) {
+          V[seg[u] >> 1].list[seg[u] & 1][idx[u]] = ent[u];
+          if (KIND == 1) V[seg[u] >> 1].rinvd[seg[u] & 1][idx[u]] = iv[u];
         }
     }
-    __syncthreads();
   }
+  if (SMEM) {
+    const bool keep = a.n_cycles > 1;
+    for (int i = a.first_smem > 1 ? a.first_smem : 1; i < a.nlev; ++i) {
+      const long long tot = a.L[i].g.total;
+      for (int c = 0; c < 2; ++c)
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) V[i].phi[c][e] = V[i].rhs[c][e] = T(0);
+    }
+    if (a.first_smem == 0) {
+      const long long tot = a.L[0].g.total;
+      constexpr int U = 8;
+      for (long long e0 = threadIdx.x; e0 < 2 * tot; e0 += U * (long long)blockDim.x) {
+        T r[U], ph[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + u * (long long)blockDim.x;
+          const int c = e >= tot;
+          const long long o = e - c * tot;
+          r[u] = e < 2 * tot ? a.L[0].rhs[c][o] : T(0);
+          ph[u] = (e < 2 * tot && keep) ? a.L[0].phi[c][o] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + u * (long long)blockDim.x;
+          const int c = e >= tot;
+          const long long o = e - c * tot;
+          if (e < 2 * tot) {
+            V[0].rhs[c][o] = r[u];
+            V[0].phi[c][o] = ph[u];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
   // The recursion mg(i) = {smooth n_pre; restrict into i+1; N_cycles times
   // mg(i+1); prolong; smooth n_post}, with mg(deepest) = coarse_sweeps
   // sweeps, unrolled with one counter per level (the same in every thread):
@@ -382,14 +542,14 @@ __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
     bottom_smooth<KIND>(V[last], a.coarse_sweeps);
     for (i = last - 1; i >= 0; --i) {  // ascend until a level owes a visit
       if (--owe[i] > 0) break;
-      bottom_prolong(V[i], V[i + 1], a.bit, a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel
+      bottom_prolong(V[i], V[i + 1], a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel
       bottom_smooth<KIND>(V[i], a.n_post);
     }
     if (i < 0) break;
     ++i;  // visit level i+1 again, from its current correction
   }
   if (SMEM) {
-    for (int i = 0; i < a.nlev; ++i) {
+    for (int i = a.first_smem; i < a.nlev; ++i) {
       const long long tot = a.L[i].g.total;
       for (int c = 0; c < 2; ++c)
         for (long long e = threadIdx.x; e < tot; e += blockDim.x) {

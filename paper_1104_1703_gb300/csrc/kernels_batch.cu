@@ -353,7 +353,6 @@ size_t batch_fill_bottom(void* host_args, int slot, const LevelDev* levels, int 
   B.kind = order == 2 ? 1 : 2;
   a.nlev = deepest - lb + 1;
   if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return kBottomTooDeep;
-  long long off = 0;
   for (int i = 0; i < a.nlev; ++i) {
     const LevelDev& L = levels[lb + i];
     a.L[i].g = L.g;
@@ -366,13 +365,13 @@ size_t batch_fill_bottom(void* host_args, int slot, const LevelDev* levels, int 
       a.L[i].list[c] = L.list[order][c];
     }
     a.L[i].count = L.count + order * 2;
-    a.L[i].smem_off = off;
-    off += 4 * L.g.total;
   }
   a.bit = order == 1 ? kActive1 : kActive2;
-  const size_t bytes = (size_t)off * sizeof(double);
-  B.smem = bytes <= (size_t)kBottomSmemBytes ? 1 : 0;
-  return B.smem ? bytes : 0;
+  // unknown records of every level, then the deepest levels that fit
+  const size_t bytes = plan_bottom_smem(a, levels, lb, order);
+  if (bytes > (size_t)kBottomSmemBytes) return kBottomTooDeep;
+  B.smem = a.first_smem < a.nlev ? 1 : 0;
+  return bytes;
 }
 
 cudaError_t init_batch_kernels() {

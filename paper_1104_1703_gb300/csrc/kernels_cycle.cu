@@ -1005,18 +1005,23 @@ cudaError_t init_cycle_kernels() {
   GBMG_SMEM_ATTR(1, float)
   GBMG_SMEM_ATTR(2, float)
 #undef GBMG_SMEM_ATTR
-#define GBMG_BOTTOM_ATTR(K, T)                                                                         \
-  if (e == cudaSuccess)                                                                                \
-    e = cudaFuncSetAttribute(bottom_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define GBMG_BOTTOM_ATTR(K, T)                                                                          \
+  if (e == cudaSuccess)                                                                                 \
+    e = cudaFuncSetAttribute(bottom_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             kBottomSmemBytes);                                                         \
+  if (e == cudaSuccess)                                                                                 \
+    e = cudaFuncSetAttribute(bottom_kernel<K, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              kBottomSmemBytes);
   GBMG_BOTTOM_ATTR(1, double)
   GBMG_BOTTOM_ATTR(2, double)
   GBMG_BOTTOM_ATTR(1, float)
   GBMG_BOTTOM_ATTR(2, float)
 #undef GBMG_BOTTOM_ATTR
-#define GBMG_MID_ATTR(K, T)                                                                                    \
-  if (e == cudaSuccess)                                                                                        \
-    e = cudaFuncSetAttribute(mid_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemBytes);
+#define GBMG_MID_ATTR(K, T)                                                                                     \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(mid_kernel<K, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemBytes); \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(mid_kernel<K, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemBytes);
   GBMG_MID_ATTR(1, double)
   GBMG_MID_ATTR(2, double)
   GBMG_MID_ATTR(1, float)
@@ -1047,14 +1052,14 @@ cudaError_t launch_prolong(const LevelDev& Lc, const LevelDev& Lf, int order, in
 }
 
 
-// Fills the bottom arguments for levels lb .. deepest; returns the dynamic
-// shared memory they need staged (0 when they do not fit: global memory).
+// Fills the bottom arguments for levels lb .. deepest and their shared
+// memory plan (plan_bottom_smem): the returned bytes hold the unknown
+// records of every level and the staged levels (first_smem on).
 template <typename T>
 bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
                  int n_cycles, BottomArgs<T>& a, size_t* smem_bytes) {
   a.nlev = deepest - lb + 1;
   if (lb < 1 || a.nlev < 1 || a.nlev > kBottomMaxLevels) return false;
-  long long off = 0;
   for (int i = 0; i < a.nlev; ++i) {
     const LevelDev& L = levels[lb + i];
     const Fields<T> f = fields(L, T());
@@ -1068,17 +1073,14 @@ bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_p
       a.L[i].list[c] = L.list[order][c];
     }
     a.L[i].count = L.count + order * 2;
-    a.L[i].smem_off = off;
-    off += 4 * L.g.total;
   }
   a.bit = bit_of(lb, order);
   a.n_pre = n_pre;
   a.n_post = n_post;
   a.coarse_sweeps = coarse_sweeps;
   a.n_cycles = n_cycles;
-  const size_t bytes = (size_t)off * sizeof(T);
-  *smem_bytes = bytes <= (size_t)kBottomSmemBytes ? bytes : 0;
-  return true;
+  *smem_bytes = plan_bottom_smem(a, levels, lb, order);
+  return *smem_bytes <= (size_t)kBottomSmemBytes;
 }
 
 template <typename T>
@@ -1088,14 +1090,14 @@ cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int
   size_t bytes = 0;
   if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, a, &bytes))
     return cudaErrorInvalidValue;
-  const bool sm = bytes > 0;
+  const bool sm = a.first_smem < a.nlev;  // some level's correction staged
   count_launch();
   if (order == 1) {
     if (sm) launch_pdl(bottom_kernel<2, T, true>, dim3(1), dim3(kBottomThreads), bytes, s, a);
-    else launch_pdl(bottom_kernel<2, T, false>, dim3(1), dim3(kBottomThreads), 0, s, a);
+    else launch_pdl(bottom_kernel<2, T, false>, dim3(1), dim3(kBottomThreads), bytes, s, a);
   } else {
     if (sm) launch_pdl(bottom_kernel<1, T, true>, dim3(1), dim3(kBottomThreads), bytes, s, a);
-    else launch_pdl(bottom_kernel<1, T, false>, dim3(1), dim3(kBottomThreads), 0, s, a);
+    else launch_pdl(bottom_kernel<1, T, false>, dim3(1), dim3(kBottomThreads), bytes, s, a);
   }
   return cudaGetLastError();
 }
@@ -1144,8 +1146,9 @@ cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order,
   if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, 1, a.bottom, &bytes))
     return cudaErrorInvalidValue;
   count_launch();
-  if (order == 1) return bytes ? launch_mid_cluster<2, T, true>(a, bytes, s) : launch_mid_cluster<2, T, false>(a, 0, s);
-  return bytes ? launch_mid_cluster<1, T, true>(a, bytes, s) : launch_mid_cluster<1, T, false>(a, 0, s);
+  const bool sm = a.bottom.first_smem < a.bottom.nlev;
+  if (order == 1) return sm ? launch_mid_cluster<2, T, true>(a, bytes, s) : launch_mid_cluster<2, T, false>(a, bytes, s);
+  return sm ? launch_mid_cluster<1, T, true>(a, bytes, s) : launch_mid_cluster<1, T, false>(a, bytes, s);
 }
 
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
