@@ -529,6 +529,7 @@ def run_batched(args, B, device, stream, world):
            "launches_per_cycle": bt.launches_per_cycle(),
            "tuning": {"threads": tune.threads, "persistent_ctas": tune.persistent_ctas,
                       "bottom_slots": tune.bottom_slots, "n_pre": tune.n_pre, "n_post": tune.n_post,
+                      "chunk_entries": tune.chunk or 2 * tune.threads,
                       "ms_per_cycle": tune.ms_per_cycle, "autotune_s": tune_s},
            "sequential_mg_solve": out.get("sequential"),
            "speedup_vs_sequential": (out["sequential"]["time_to_tol_ms"] / out["batched"]["time_to_tol_ms"]

@@ -364,20 +364,25 @@ typedef struct mg_batch mg_batch; /* opaque, library-owned */
 /* Launch parameters of a batch (results do not depend on them, except the
  * smoother schedule n_pre / n_post, which is part of the method):
  *  threads          threads per block of the chunked kernels: 128, 256 or
- *                   512; every block takes chunks of 2 * threads unknowns
+ *                   512
  *  persistent_ctas  0: one block per chunk; 1 .. 2^20: at most this many
  *                   blocks, each looping over chunks
  *  bottom_slots     a patch's coarse levels with at most this many cells per
  *                   colour (64 .. 16384) run inside the one-CTA bottom cycle
  *  n_pre, n_post    Gauss-Seidel sweeps around the coarse correction (0..8)
  *  ms_per_cycle     output of mg_batch_autotune: the measured time of one
- *                   batched cycle with these parameters (0 if not measured) */
+ *                   batched cycle with these parameters (0 if not measured)
+ *  chunk            the tile shape of the chunked kernels: list entries per
+ *                   chunk (a block works on one chunk at a time, 2 entries
+ *                   per thread in flight): 64 .. 65536, or 0 for
+ *                   2 * threads */
 typedef struct {
   int threads;
   int persistent_ctas;
   int bottom_slots;
   int n_pre, n_post;
   double ms_per_cycle;
+  int chunk;
 } mg_batch_tuning;
 
 /* Creates a batch of n_patches (1 .. 4096) patches.  masks[p] points to
@@ -418,7 +423,8 @@ mg_status mg_batch_set_tuning(mg_batch* batch, const mg_batch_tuning* tuning);
 /* Autotuner: times candidate launch parameters (threads 128/256/512, one
  * block per chunk or 4 / 8 resident blocks per multiprocessor, bottom_slots
  * 1024/2048/4096) on `reps` batched cycles each (CUDA events on the batch's
- * stream) and keeps the fastest.  With flags & MG_TUNE_SCHEDULE it then
+ * stream) and keeps the fastest; then, with those, the chunk lengths 1, 2,
+ * 4 and 8 times threads.  With flags & MG_TUNE_SCHEDULE it then
  * times whole solves to tol from a zero initial guess for the smoother
  * schedules (n_pre, n_post) = (1,1), (2,1), (2,2), (3,3) and keeps the one
  * with the shortest time to tolerance.  Each patch's solution and hold

@@ -41,7 +41,7 @@ class MGSolveInfo(ctypes.Structure):
 
 class MGBatchTuning(ctypes.Structure):
     _fields_ = [("threads", _i), ("persistent_ctas", _i), ("bottom_slots", _i), ("n_pre", _i), ("n_post", _i),
-                ("ms_per_cycle", _d)]
+                ("ms_per_cycle", _d), ("chunk", _i)]
 
 
 MG_TUNE_SCHEDULE = 1

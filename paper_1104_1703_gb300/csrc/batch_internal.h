@@ -67,6 +67,7 @@ int batch_grid(int nchunks, int threads, int persistent_ctas);
 
 // Chunked kernels (threads per block = `threads`, chunk size <= 2 * threads).
 cudaError_t launch_batch_gs(const Chunk* chunks, int nchunks, const PatchLevel* pls, const int* state, bool fine,
+                            bool exact,
                             int threads, int grid, cudaStream_t s);
 // Level-0 chunks: mode 1: per-chunk sum of r^2 into partials[chunk]; 2:
 // per-chunk sum of b^2 (the residual of Phi = 0).

@@ -35,8 +35,10 @@ __device__ __forceinline__ const uint32_t* chunk_list(const PatchLevel& L, const
 
 // One colour of a Gauss-Seidel sweep over the entries of one chunk.  At
 // level 0 the right-hand side is b / D and the update one fused
-// multiply-add, as in the single-hierarchy FP64 sweep.
-template <int KIND>
+// multiply-add, as in the single-hierarchy FP64 sweep; with EXACT the
+// neighbour sum is formed in integer arithmetic as there (option
+// fp64_sum).
+template <int KIND, bool EXACT = false>
 __device__ __forceinline__ void gs_chunk(const PatchLevel& L, const Chunk& C, const double* tab) {
   const int c = C.colour;
   double* __restrict__ self = L.phi[c];
@@ -47,25 +49,30 @@ __device__ __forceinline__ void gs_chunk(const PatchLevel& L, const Chunk& C, co
   const uint32_t* __restrict__ list = chunk_list(L, C);
   const int P = L.g.P;
   const long long sz = L.g.sz;
-  long long at[kPer];
-  double s[kPer], b[kPer], d[kPer];
-  bool ok[kPer];
+  for (int i0 = 0; i0 < C.n; i0 += kPer * blockDim.x) {
+    long long at[kPer];
+    double s[kPer], b[kPer], d[kPer];
+    bool ok[kPer];
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int i = threadIdx.x + u * blockDim.x;
-    ok[u] = i < C.n;
-    const uint32_t e = ok[u] ? list[i] : 0u;
-    at[u] = e & kListAt;
-    ok[u] = ok[u] && entry_ok(L.g, at[u], 20);
-    if (ok[u]) {
-      s[u] = nbr_sum(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
-      b[u] = rhs[at[u]];
-      d[u] = inv_diag<KIND>(KIND == 0 ? code[at[u]] : 0, invd, at[u], tab);
+    for (int u = 0; u < kPer; ++u) {
+      const int i = i0 + threadIdx.x + u * blockDim.x;
+      ok[u] = i < C.n;
+      const uint32_t e = ok[u] ? list[i] : 0u;
+      at[u] = e & kListAt;
+      ok[u] = ok[u] && entry_ok(L.g, at[u], 20);
+      if (ok[u]) {
+        if constexpr (EXACT)
+          s[u] = nbr_sum_exact(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
+        else
+          s[u] = nbr_sum(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
+        b[u] = rhs[at[u]];
+        d[u] = inv_diag<KIND>(KIND == 0 ? code[at[u]] : 0, invd, at[u], tab);
+      }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < kPer; ++u)
-    if (ok[u]) self[at[u]] = KIND == 0 ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+    for (int u = 0; u < kPer; ++u)
+      if (ok[u]) self[at[u]] = KIND == 0 ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+  }
 }
 
 __global__ void __launch_bounds__(kBatchMaxThreads)
@@ -78,10 +85,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const PatchLevel& L = pls[C.pl];
     const int c = C.colour;
     const uint32_t* __restrict__ list = L.list[2][c] + C.start;
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int i = threadIdx.x + u * blockDim.x;
-      if (i >= C.n) continue;
+    for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
       const long long at = list[i] & kListAt;
       if (!entry_ok(L.g, at, 21)) continue;
       L.rhsd[c][at] = L.rhs[c][at] * tab[__popc((unsigned)L.code[c][at] >> kGhostShift)];
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
   }
 }
 
-template <bool FINE>
+template <bool FINE, bool EXACT = false>
 __global__ void __launch_bounds__(kBatchMaxThreads)
     batch_gs_kernel(const Chunk* __restrict__ chunks, int nchunks, const PatchLevel* __restrict__ pls,
                     const int* __restrict__ state) {
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const Chunk C = chunks[k];
     const PatchLevel& L = pls[C.pl];
     if (!chunk_runs(C, state[L.patch])) continue;
-    if (FINE) gs_chunk<0>(L, C, tab);
+    if (FINE) gs_chunk<0, EXACT>(L, C, tab);
     else if (C.tag == 2) gs_chunk<1>(L, C, tab);
     else gs_chunk<2>(L, C, tab);
   }
@@ -120,29 +124,31 @@ __device__ __forceinline__ double res_chunk(const PatchLevel& L, const Chunk& C,
   const int P = L.g.P;
   const long long sz = L.g.sz;
   double acc = 0.0;
-  long long at[kPer];
-  double r[kPer];
-  bool ok[kPer];
+  for (int i0 = 0; i0 < C.n; i0 += kPer * blockDim.x) {
+    long long at[kPer];
+    double r[kPer];
+    bool ok[kPer];
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int i = threadIdx.x + u * blockDim.x;
-    ok[u] = i < C.n;
-    const uint32_t e = ok[u] ? list[i] : 0u;
-    at[u] = e & kListAt;
-    ok[u] = ok[u] && entry_ok(L.g, at[u], 22);
-    if (ok[u]) {
-      if (MODE == 2) {
-        r[u] = -rhs[at[u]];
-      } else {
-        const double sn = nbr_sum(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
-        const uint8_t cd = KIND == 0 ? code[at[u]] : 0;
-        r[u] = fma(-diag_of<KIND>(cd, diag, at[u], tab), self[at[u]], sn) - rhs[at[u]];
+    for (int u = 0; u < kPer; ++u) {
+      const int i = i0 + threadIdx.x + u * blockDim.x;
+      ok[u] = i < C.n;
+      const uint32_t e = ok[u] ? list[i] : 0u;
+      at[u] = e & kListAt;
+      ok[u] = ok[u] && entry_ok(L.g, at[u], 22);
+      if (ok[u]) {
+        if (MODE == 2) {
+          r[u] = -rhs[at[u]];
+        } else {
+          const double sn = nbr_sum(other, at[u], (e & kListPlusX) ? 1 : -1, P, sz);
+          const uint8_t cd = KIND == 0 ? code[at[u]] : 0;
+          r[u] = fma(-diag_of<KIND>(cd, diag, at[u], tab), self[at[u]], sn) - rhs[at[u]];
+        }
       }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < kPer; ++u)
-    if (ok[u]) acc = fma(r[u], r[u], acc);
+    for (int u = 0; u < kPer; ++u)
+      if (ok[u]) acc = fma(r[u], r[u], acc);
+  }
   return acc;
 }
 
@@ -178,10 +184,7 @@ __device__ __forceinline__ void restrict_chunk(const PatchLevel& Lc, const Patch
   const uint32_t* __restrict__ list = Lc.list[2][c] + C.start;
   const Geom gc = Lc.g, gf = Lf.g;
   const int nsum = black_zero ? 1 : 2;
-#pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int i = threadIdx.x + u * blockDim.x;
-    if (i >= C.n) continue;
+  for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
     const long long at = list[i] & kListAt;
     if (!entry_ok(gc, at, 23)) continue;
     int Q, J, K;
@@ -241,25 +244,27 @@ __global__ void __launch_bounds__(kBatchMaxThreads)
     const int c = C.colour;
     const uint32_t* __restrict__ list = chunk_list(Lf, C);
     const Geom gf = Lf.g, gc = Lc.g;
-    long long at[kPer];
-    double w[kPer], old[kPer];
-    bool ok[kPer];
+    for (int i0 = 0; i0 < C.n; i0 += kPer * blockDim.x) {
+      long long at[kPer];
+      double w[kPer], old[kPer];
+      bool ok[kPer];
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int i = threadIdx.x + u * blockDim.x;
-      ok[u] = i < C.n;
-      if (!ok[u]) continue;
-      at[u] = list[i] & kListAt;
-      ok[u] = entry_ok(gf, at[u], 24);
-      if (!ok[u]) continue;
-      int q, j, kk;
-      gf.slot_of(at[u], &q, &j, &kk);
-      w[u] = p2_sum(gc, (const double*)Lc.phi[0], (const double*)Lc.phi[1], q, j, kk, c, PlainLoad());
-      old[u] = Lf.phi[c][at[u]];
+      for (int u = 0; u < kPer; ++u) {
+        const int i = i0 + threadIdx.x + u * blockDim.x;
+        ok[u] = i < C.n;
+        if (!ok[u]) continue;
+        at[u] = list[i] & kListAt;
+        ok[u] = entry_ok(gf, at[u], 24);
+        if (!ok[u]) continue;
+        int q, j, kk;
+        gf.slot_of(at[u], &q, &j, &kk);
+        w[u] = p2_sum(gc, (const double*)Lc.phi[0], (const double*)Lc.phi[1], q, j, kk, c, PlainLoad());
+        old[u] = Lf.phi[c][at[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u)
+        if (ok[u]) Lf.phi[c][at[u]] = fma(w[u], 1.0 / 64.0, old[u]);
     }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u)
-      if (ok[u]) Lf.phi[c][at[u]] = fma(w[u], 1.0 / 64.0, old[u]);
   }
 }
 
@@ -386,10 +391,12 @@ int batch_grid(int nchunks, int threads, int persistent_ctas) {
 }
 
 cudaError_t launch_batch_gs(const Chunk* chunks, int nchunks, const PatchLevel* pls, const int* state, bool fine,
-                            int threads, int grid, cudaStream_t s) {
+                            bool exact, int threads, int grid, cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   count_launch();
-  if (fine) launch_pdl(batch_gs_kernel<true>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
+  if (fine && exact)
+    launch_pdl(batch_gs_kernel<true, true>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
+  else if (fine) launch_pdl(batch_gs_kernel<true>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
   else launch_pdl(batch_gs_kernel<false>, dim3(grid), dim3(threads), 0, s, chunks, nchunks, pls, state);
   return cudaGetLastError();
 }

@@ -112,7 +112,7 @@ long long slots(const Geom& g) { return (long long)g.hx * g.ny * g.nz; }
 bool valid_tuning(const mg_batch_tuning& t) {
   return (t.threads == 128 || t.threads == 256 || t.threads == 512) && t.persistent_ctas >= 0 &&
          t.persistent_ctas <= (1 << 20) && t.bottom_slots >= 64 && t.bottom_slots <= 16384 && t.n_pre >= 0 &&
-         t.n_pre <= 8 && t.n_post >= 0 && t.n_post <= 8;
+         t.n_pre <= 8 && t.n_post >= 0 && t.n_post <= 8 && (t.chunk == 0 || (t.chunk >= 64 && t.chunk <= 65536));
 }
 
 // Gauss-Seidel updates of one V-cycle of patch H in `order` (as the
@@ -162,7 +162,7 @@ uint32_t list_len(const LevelDev& L, int order, int colour) {
 mg_status build_tables(mg_batch* B) {
   free_tables(B);
   const mg_batch_tuning& t = B->tune;
-  const int chunk = 2 * t.threads;
+  const int chunk = t.chunk > 0 ? t.chunk : 2 * t.threads;
   const int n = B->n;
   for (int o = 0; o < 2; ++o) {
     B->lb[o].assign(n, 0);
@@ -329,7 +329,8 @@ int grid_of(const mg_batch* B, const Table& T) { return batch_grid(T.n, B->tune.
 
 mg_status emit_gs(mg_batch* B, int l, int c, cudaStream_t s) {
   const Table& T = B->gs[l][c];
-  return lok(B, launch_batch_gs(B->d_chunks + T.off, T.n, B->d_pls, B->d_state, l == 0, B->tune.threads,
+  return lok(B, launch_batch_gs(B->d_chunks + T.off, T.n, B->d_pls, B->d_state, l == 0, B->opt.fp64_sum == 1,
+                                B->tune.threads,
                                 grid_of(B, T), s),
              "batched half-sweep");
 }
@@ -636,6 +637,7 @@ mg_status mg_batch_create(int n_patches, const int8_t* const* masks, mg_mem wher
   B->tune.n_pre = o.n_pre;
   B->tune.n_post = o.n_post;
   B->tune.ms_per_cycle = 0;
+  B->tune.chunk = 0;
   if (!valid_tuning(B->tune)) {
     delete B;
     return bfail(nullptr, MG_ERR_INVALID_ARG, "invalid options (n_pre, n_post must be in 0..8)");
@@ -811,6 +813,21 @@ mg_status mg_batch_autotune(mg_batch* B, int reps, double tol, int max_cycles, i
             top.ms_per_cycle = ms;
           }
         }
+    // the tile shape: list entries per chunk, with the best launch shape
+    const mg_batch_tuning shape = top;
+    for (int m = 1; m <= 8 && st == MG_OK; m *= 2) {
+      mg_batch_tuning t = shape;
+      t.chunk = m * shape.threads;
+      B->tune = t;
+      st = build_tables(B);
+      double ms = 0;
+      if (st == MG_OK) st = time_cycles(&ms);
+      if (st == MG_OK && ms < top_ms) {
+        top_ms = ms;
+        top = t;
+        top.ms_per_cycle = ms;
+      }
+    }
   }
   if (st == MG_OK && (flags & MG_TUNE_SCHEDULE)) {
     const int sched[4][2] = {{1, 1}, {2, 1}, {2, 2}, {3, 3}};

@@ -158,10 +158,12 @@ def test_batch_small_islands_switch(dev, oracle):
 
 def test_launch_parameters_do_not_change_results(dev, oracle):
     sols = None
-    for threads, pers, bots in ((256, 0, 4096), (128, 0, 1024), (512, 152 * 4, 2048), (256, 152 * 8, 64)):
+    for threads, pers, bots, chunk in ((256, 0, 4096, 0), (128, 0, 1024, 0), (512, 152 * 4, 2048, 0),
+                                       (256, 152 * 8, 64, 0), (128, 0, 4096, 1024), (256, 152 * 4, 2048, 64),
+                                       (512, 0, 4096, 4096)):
         Bt, _ = make_batch(dev, oracle, PATCHES)
         t = Bt.tuning
-        t.threads, t.persistent_ctas, t.bottom_slots = threads, pers, bots
+        t.threads, t.persistent_ctas, t.bottom_slots, t.chunk = threads, pers, bots, chunk
         Bt.tuning = t
         for _ in range(3):
             Bt.vcycle(want_rel=False)
@@ -203,6 +205,7 @@ def test_autotune_restores_state_and_keeps_parity(dev, oracle):
     holds = [Bt.patch(p).hold for p in range(4)]
     best = Bt.autotune(reps=2, tol=1e-8, max_cycles=60, flags=B.MG_TUNE_SCHEDULE)
     assert best.threads in (128, 256, 512) and best.bottom_slots in (1024, 2048, 4096)
+    assert best.chunk in (0, best.threads, 2 * best.threads, 4 * best.threads, 8 * best.threads)
     assert (best.n_pre, best.n_post) in ((1, 1), (2, 1), (2, 2), (3, 3)) and best.ms_per_cycle > 0
     for p in range(4):
         assert np.array_equal(Bt.patch(p).get_solution(), before[p])
