@@ -316,6 +316,11 @@ class Form:
         self.n_active = self.H.level_info(0)[1]
         # the fine level's FP32 sweep pairs run as temporal-blocked passes
         self.pass_on = precision == 1 and self.H.smoother_pass
+        d = B.mg_default_options()
+        # FP32 level-0 sweeps over row segments; FP64 ones with the integer neighbour sum
+        self.seg_on = precision == 1 and not self.pass_on and int(extra.get("fine_segments", d.fine_segments)) >= 1
+        self.exact_on = precision == 0 and int(extra.get("fp64_sum", d.fp64_sum)) == 1
+        self.kinds = (self.pass_on, self.seg_on, self.exact_on)
 
     def step(self, mask, rho, out=None):
         H = self.H
@@ -370,7 +375,7 @@ def time_form(f, args, mask, rho, stream, world, device, out=None, timing=False)
 
 
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1104_1703_gb300", "csrc", f)
-               for f in ("kernels_cycle.cu", "cycle_device.cuh", "kernels_pass.cu")]
+               for f in ("kernels_cycle.cu", "cycle_device.cuh", "kernels_pass.cu", "exact_sum.cuh")]
 
 
 def kernel_source_hash():
@@ -398,35 +403,41 @@ def profiled_traffic(profile):
     return int(m_bytes.group(1))
 
 
-def roofline(st, n_active, precision, peaks, fp64_rate=None, pass_on=False):
+def roofline(st, n_active, precision, peaks, fp64_rate=None, pass_on=False, seg_on=False, exact_on=True):
     """Roofline of the dominant kernel, the level-0 Gauss-Seidel smoother,
-    from its CUDA-event-timed launches inside the timed region.  A list
+    from its CUDA-event-timed launches inside the timed region.  A
     half-sweep launch updates one colour of the unknowns (n_active / 2 on
     average); a temporal-blocked pass launch runs two red-black sweeps (four
     half-sweeps, 2 n_active updates).  Algorithmic bytes are counted per
-    update as for the unfused half-sweeps, so the pass's `achieved` is the
-    bandwidth the half-sweeps would need to match it."""
+    active update as for the unfused half-sweeps (a row-segment sweep also
+    touches the inactive slots of its segments; those are not counted), so
+    the pass's `achieved` is the bandwidth the half-sweeps would need to
+    match it."""
     gs_s = st["gs_ms"] / 1e3 / max(st["gs_n"], 1)
     half = n_active / 2.0
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     if precision == 0:
-        # the method's 7 FP64 operations per update (6 adds, 1 multiply); the
-        # sweep on b/D issues 6 (5 adds and one fused multiply-add); 25 B per
-        # update over the red+black sweep
-        ops = 6.0
+        # 25 B per update over the red+black sweep: read the other colour 8,
+        # b/D 8, code 1, write 8.  The method's 7 FP64 operations per update
+        # (6 adds, 1 multiply) issue as 1 fused multiply-add when the
+        # neighbour sum is formed in integer arithmetic (fp64_sum), else 6
+        ops = 1.0 if exact_on else 6.0
         if fp64_rate:
             peak, psrc = fp64_rate / 1e12, "measured DFMA rate on this GPU (mg_probe_fp64_rate)"
         else:
             peak, psrc = 2 * 152 * 2.07e9 / 1e12, "nominal: 2 FP64 lane-ops/clk/SM x 152 SMs x 2.07 GHz"
-        ach = ops * half / gs_s / 1e12
-        return {"bound": "alu", "kernel": "gs_list_kernel<0,double> (level-0 red/black Gauss-Seidel, FP64)",
-                "achieved": ach, "peak": peak, "unit": "T FP64 instr/s", "frac": ach / peak,
-                "issued_fp64_ops_per_update": ops, "method_fp64_ops_per_update": 7,
-                "traffic": profiled_traffic("gs_list_fp64_level0_sphere_union_256.md"),
-                "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": psrc,
-                "hbm_view": {"achieved_gbs": 25.0 * half / gs_s / 1e9, "peak_gbs": hbm_peak,
-                             "frac": 25.0 * half / gs_s / 1e9 / hbm_peak, "peak_source": src}}
+        ach = 25.0 * half / gs_s / 1e9
+        name = ("gs_list_kernel<0,double,...,exact> (level-0 red/black Gauss-Seidel, FP64, integer neighbour sum)"
+                if exact_on else "gs_list_kernel<0,double> (level-0 red/black Gauss-Seidel, FP64)")
+        return {"bound": "hbm", "kernel": name,
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": profiled_traffic("gs_list_fp64_exact_level0_sphere_union_256.md" if exact_on
+                                            else "gs_list_fp64_level0_sphere_union_256.md"),
+                "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src,
+                "fp64_pipe_view": {"achieved": ops * half / gs_s / 1e12, "peak": peak, "unit": "T FP64 instr/s",
+                                   "frac": ops * half / gs_s / 1e12 / peak, "issued_fp64_ops_per_update": ops,
+                                   "method_fp64_ops_per_update": 7, "peak_source": psrc}}
     # FP32: read the other colour 4 + b 4 + code 1, write 4 = 13 B per update
     if pass_on:
         upd = 2.0 * n_active
@@ -438,6 +449,12 @@ def roofline(st, n_active, precision, peaks, fp64_rate=None, pass_on=False):
                 "traffic": profiled_traffic("smooth_pass_fp32_level0_sphere_union_256.md"),
                 "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
     ach = 13.0 * half / gs_s / 1e9
+    if seg_on:
+        return {"bound": "hbm", "kernel": "gs_seg_kernel<float> (level-0 red/black Gauss-Seidel over 8-slot row "
+                                          "segments, FP32 inner cycle)",
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": profiled_traffic("gs_seg_fp32_level0_sphere_union_256.md"),
+                "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
     return {"bound": "hbm", "kernel": "gs_list_kernel<0,float> (level-0 red/black Gauss-Seidel, FP32 inner cycle)",
             "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
             "traffic": profiled_traffic("gs_list_fp32_level0_sphere_union_256.md"),
@@ -676,7 +693,7 @@ def run_ours(args):
     # zero guess), for their error against the oracle's converged solution
     solutions = {FORMS[args.precision]: main.H.get_solution(), FORMS[1 - args.precision]: other.H.get_solution()}
     fp64_rate = B.mg_probe_fp64_rate(4096)
-    main_pass, other_pass = main.pass_on, other.pass_on
+    main_kinds, other_kinds = main.kinds, other.kinds
     del main, other
     pass_probe = None
     if not args.no_pass_probe and not args.smoother_pass:
@@ -688,7 +705,7 @@ def run_ours(args):
         st_pk = time_form(fp, probe, mask_d, rho_d, stream, world, device, timing=True)
         pass_probe = {"time_to_tol_ms": 1e3 * st_p["elapsed"] / probe.steps, "steps": probe.steps,
                       "active": fp.pass_on,
-                      "roofline": roofline(st_pk, n_active, 1, peaks_of(), fp64_rate, fp.pass_on)}
+                      "roofline": roofline(st_pk, n_active, 1, peaks_of(), fp64_rate, *fp.kinds)}
         del fp
     wcyc = None if args.no_wcycles else run_wcycles(args, B, device, stream, world, mask_d, rho_d, w["h"])
     batched = None if args.no_batch else run_batched(args, B, device, stream, world)
@@ -712,12 +729,12 @@ def run_ours(args):
         # active fine cells x multigrid V-cycles (the mixed form's FP32 cycles: steps x inner cycles) per second
         "fine_cell_vcycles_per_s": world * n_active * st_main["cycles"] * (args.inner_cycles if args.precision == 1 else 1)
                                    * args.steps / st_main["elapsed"],
-        "roofline": roofline(st_main_k, n_active, args.precision, peaks, fp64_rate, main_pass),
+        "roofline": roofline(st_main_k, n_active, args.precision, peaks, fp64_rate, *main_kinds),
         FORMS[1 - args.precision]: {"time_to_tol_ms": ms(st_other),
                                      "value": st_other["updates"] / st_other["elapsed"],
                                      "cycles_per_solve": st_other["cycles"],
                                      "roofline": roofline(st_other_k, n_active, 1 - args.precision, peaks,
-                                                          fp64_rate, other_pass)},
+                                                          fp64_rate, *other_kinds)},
         "e2e": {"value": st_e2e["updates"] / st_e2e["elapsed"], "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms(st_e2e)},
         "clocks": clk,
