@@ -96,11 +96,13 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  (faster on GB300: the pass moves fewer bytes but waits on
  *                  its chain of barrier-separated stages).  The results are
  *                  bit-identical.
- *  fp64_sum        FP64 form, level-0 Gauss-Seidel sweeps: 1 = form each
- *                  cell's sum of its six neighbour values in 64-bit integer
- *                  arithmetic (exponent-aligned fixed point, rounded once to
- *                  the nearest double; subnormal values count as zero), so
- *                  that the update issues one FP64 instruction instead of
+ *  fp64_sum        level-0 FP64 kernels (the FP64 form's Gauss-Seidel
+ *                  sweeps, residual norms and residual + restriction, and
+ *                  the mixed form's FP64 residual): 1 = form each cell's sum
+ *                  of its six neighbour values in 64-bit integer arithmetic
+ *                  (exponent-aligned fixed point, rounded once to the
+ *                  nearest double; subnormal values count as zero), so that
+ *                  a sweep's update issues one FP64 instruction instead of
  *                  six; 0 = five FP64 additions.  Both are accurate to about
  *                  one rounding of the sum; the results differ in the last
  *                  bits.

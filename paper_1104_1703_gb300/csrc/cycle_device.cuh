@@ -126,6 +126,15 @@ __device__ __forceinline__ double nbr_sum_exact(const double* __restrict__ o, lo
   return exact_sum(x);
 }
 
+// nbr_sum, or (EXACT, FP64) nbr_sum_exact
+template <bool EXACT, typename T>
+__device__ __forceinline__ T nbr_sum_sel(const T* __restrict__ o, long long at, int dx, int P, long long sz) {
+  if constexpr (EXACT && sizeof(T) == 8)
+    return nbr_sum_exact(reinterpret_cast<const double*>(o), at, dx, P, sz);
+  else
+    return nbr_sum(o, at, dx, P, sz);
+}
+
 // tab[0..7] = 1/(6+n), tab[8..15] = 6+n: the level-0 diagonal and its
 // inverse for n ghost faces
 template <typename T>

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
 // K9, first pass: the sum of r^2 per block into partials[blockIdx.x], r^ =
 // sum_nbr Phi_j - D Phi_i - b the scaled residual of the listed unknowns
 // (the grid is fixed per level, so the partials do not depend on scheduling).
-template <int KIND, typename T>
+template <int KIND, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
   pdl_wait();
   constexpr int PER = PerThread<T>::value;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
       at[u] = e & kListAt;
       ok[u] = ok[u] && entry_ok(g, at[u], 4);
       if (ok[u]) {
-        const T s = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+        const T s = nbr_sum_sel<EXACT>(a.other, at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
         const uint8_t code = KIND == 0 ? a.code[at[u]] : 0;
         r[u] = fma(-diag_of<KIND>(code, a.diag, at[u], tab), a.self[at[u]], s) - a.rhs[at[u]];
       }
@@ -293,7 +293,7 @@ struct RestrictArgs {
 };
 
 // Children residuals of coarse cell (I, J, K) (the scaled residuals r^ of its active children, summed in a fixed order).
-template <int KIND, bool BLACK_ZERO, typename T>
+template <int KIND, bool BLACK_ZERO, typename T, bool EXACT = false>
 __device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, int I, int J, int K, const T* tab) {
   const Geom& gf = a.gf;
   T sum = 0;
@@ -310,7 +310,7 @@ __device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, int I,
       for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c) {
         const uint8_t cd = a.code[c][at];
         if (!(cd & a.bit)) continue;
-        const T s = nbr_sum(a.phi[c ^ 1], at, x_offset(c, j, k), gf.P, gf.sz);
+        const T s = nbr_sum_sel<EXACT>(a.phi[c ^ 1], at, x_offset(c, j, k), gf.P, gf.sz);
         sum += fma(-diag_of<KIND>(cd, a.diag[c], at, tab), a.phi[c][at], s) - a.rhs[c][at];
       }
     }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArg
 // never written in a cycle: their correction stays the 0 it was reset to,
 // and their right-hand side is never read.  Every lane holds a coarse
 // unknown, which spares the FP64 pipe the idle lanes of a box-wide grid.
-template <int KIND, bool BLACK_ZERO, typename T>
+template <int KIND, bool BLACK_ZERO, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<T> a) {
   pdl_wait();
   constexpr int PER = 2;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<
       if (!ok[u]) continue;
       int Q, J, K;
       gc.slot_of(atc[u], &Q, &J, &K);
-      sum[u] = child_residual_sum<KIND, BLACK_ZERO>(a, 2 * Q + ((C ^ J ^ K) & 1), J, K, tab);
+      sum[u] = child_residual_sum<KIND, BLACK_ZERO, T, EXACT>(a, 2 * Q + ((C ^ J ^ K) & 1), J, K, tab);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -513,6 +513,7 @@ struct RefineArgs {
   double* partials;
 };
 
+template <bool EXACT>
 __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs a) {
   pdl_wait();
   constexpr int PER = 2;
@@ -538,7 +539,7 @@ __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs 
       at[u] = e & kListAt;
       ok[u] = entry_ok(g, at[u], 7);
       if (!ok[u]) continue;
-      const double s = nbr_sum(a.phi[1 - c], at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
+      const double s = nbr_sum_sel<EXACT>(a.phi[1 - c], at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
       const double D = tab[8 + __popc((unsigned)a.code[c][at[u]] >> kGhostShift)];
       r[u] = fma(-D, a.phi[c][at[u]], s) - a.rhs[c][at[u]];
     }
@@ -753,6 +754,11 @@ cudaError_t restrict_t(const LevelDev& Lf, const LevelDev& Lc, int order, bool b
   if (!all_cells && Lf.level == 0) {
     const int lgrid = exact_grid(Lc.hcount[4] + Lc.hcount[5], 2);
     count_launch();
+    if (sizeof(T) == 8 && Lf.exact_sum) {  // level 0, FP64: the residuals with the integer neighbour sum
+      if (black_zero) launch_pdl(restrict_list_kernel<0, true, T, true>, dim3(lgrid), dim3(kListBlock), 0, s, a);
+      else launch_pdl(restrict_list_kernel<0, false, T, true>, dim3(lgrid), dim3(kListBlock), 0, s, a);
+      return cudaGetLastError();
+    }
 #define GBMG_RESTRICT_LIST(K)                                                                            \
   if (black_zero) launch_pdl(restrict_list_kernel<K, true, T>, dim3(lgrid), dim3(kListBlock), 0, s, a); \
   else launch_pdl(restrict_list_kernel<K, false, T>, dim3(lgrid), dim3(kListBlock), 0, s, a);
@@ -1204,7 +1210,8 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
       ListArgs<double> a = list_args<double>(L0, 2, c);
       a.partials = partials + c * grid;
       count_launch();
-      launch_pdl(res_list_kernel<0, double>, dim3(grid), dim3(kListBlock), 0, s, a);
+      if (L0.exact_sum) launch_pdl(res_list_kernel<0, double, true>, dim3(grid), dim3(kListBlock), 0, s, a);
+      else launch_pdl(res_list_kernel<0, double>, dim3(grid), dim3(kListBlock), 0, s, a);
     }
   }
   count_launch();
@@ -1229,7 +1236,8 @@ cudaError_t launch_refine_residual(const LevelDev& L0, double* partials, int max
   const int blocks = 2 * list_grid(L0.g);
   if (blocks > max_partials) return cudaErrorInvalidValue;
   count_launch(2);
-  launch_pdl(refine_residual_kernel, dim3(blocks), dim3(kListBlock), 0, s, a);
+  if (L0.exact_sum) launch_pdl(refine_residual_kernel<true>, dim3(blocks), dim3(kListBlock), 0, s, a);
+  else launch_pdl(refine_residual_kernel<false>, dim3(blocks), dim3(kListBlock), 0, s, a);
   launch_pdl(finalize_kernel, dim3(1), dim3(kFinalThreads), 0, s, partials, blocks, out);
   return cudaGetLastError();
 }

@@ -1,20 +1,26 @@
 // Kernels of the learned initial guess's network: the 3x3x3 convolution as a
-// tcgen05 implicit GEMM, and the packing of its weights.
+// tcgen05 implicit GEMM, its weight gradients, and the packing of weights.
 //
 // Convolution.  An output tile is 128 voxels (a box of bx x by x bz) by cout
 // channels, accumulated in tensor memory (TMEM) in FP32 over K = 27 taps x
-// cin input channels.  For each tap the input tile is the output tile's box
-// shifted by the tap's offset: one TMA copy of a 5-D view of the
-// channels-last input, (8 channels, x, y, z, channel chunk), lands it in
-// shared memory as [chunk][voxel][8 channels], which is the canonical
-// K-major layout of the MMA's A operand (8-row x 16-byte core matrices,
-// 128 bytes apart along M and 2048 bytes apart along K).  Voxels outside the
-// grid read 0 (the convolution's zero padding).  The weights of the tap come
-// from a packed [27][cin / 8][cout][8] array by one bulk copy, in the same
-// layout for the B operand.  Per 16 input channels one tcgen05.mma
-// (kind::f16, BF16 x BF16 -> FP32, M = 128, N = cout) accumulates.
+// cin input channels.  Per 16 input channels one tcgen05.mma (kind::f16,
+// BF16 x BF16 -> FP32, M = 128, N = cout) accumulates.  The A operand comes
+// from the channels-last input by TMA copies of a 5-D view of it,
+// (8 channels, x, y, z, channel chunk), landing in shared memory in the
+// canonical K-major layout (8-row x 16-byte core matrices); voxels outside
+// the grid read 0 (the convolution's zero padding).  Two ways to stage it:
+//  - halo rows (a tile that is one whole row of 128 voxels): one copy per 16
+//    input channels of the box (130 x 3 x 3) around the row; each of the 27
+//    taps is then a view of it, offset by (dz * 3 + dy) * 130 + dx rows, so
+//    the input is read once instead of 27 times;
+//  - tap tiles (other shapes): one copy per tap and channel chunk of the
+//    tile's box shifted by the tap.
+// The B operand (the weights, packed [27][cin / 8][cout][8]) stays resident
+// in shared memory for the whole launch when it fits (up to 72 KB), loaded
+// once per CTA by one bulk copy; otherwise it is staged with each tap.  The
+// pipeline depth is as many stages as fit in the shared-memory budget.
 //
-// Roles: warp 0's lane 0 issues the copies into a ring of 4 stages, warp 1
+// Roles: warp 0's lane 0 issues the copies into the ring of stages, warp 1
 // allocates TMEM and its lane 0 issues the MMAs (each stage is released by a
 // tcgen05.commit when its MMAs have read it), warps 2-5 read the two
 // accumulator buffers back (tcgen05.ld, one TMEM lane quarter per warp),
@@ -97,10 +103,6 @@ void conv_plan(ConvArgs& a) {
   if (n < 2) n = 2;
   a.stages = (int)n;
 }
-
-namespace {
-
-}  // namespace
 
 // TMEM columns of a convolution CTA: two FP32 accumulators of cout columns,
 // rounded up to the power of two the allocator takes.

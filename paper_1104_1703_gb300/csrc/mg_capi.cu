@@ -890,7 +890,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->list_blocks = lblocks;
   for (int l = 0; l < H->nlev; ++l) {
     H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
-    H->L[l].exact_sum = (l == 0 && !mixed && o.fp64_sum == 1) ? 1 : 0;
+    H->L[l].exact_sum = (l == 0 && o.fp64_sum == 1) ? 1 : 0;
     H->L[l].seg_shift = l == 0 ? seg_shift : 0;
   }
   for (int c = 0; c < 2; ++c) {

@@ -108,7 +108,7 @@ struct LevelDev {
   uint32_t* count;
   uint32_t hcount[6];  // host copy of count (sizes the launch grids)
   double* rhsd[2];     // level 0 of the FP64 method: b / D (nullptr elsewhere)
-  int exact_sum = 0;   // level 0 of the FP64 method: neighbour sums in integer arithmetic (exact_sum.cuh)
+  int exact_sum = 0;   // level 0: FP64 neighbour sums in integer arithmetic (exact_sum.cuh)
   int seg_shift = 0;   // level 0: log2 of the row-segment length (0: no segment lists)
   // FP32 copies for the inner cycles of the mixed-precision form (nullptr
   // when the hierarchy was created for FP64 only); level 0: phi32 is the
