@@ -201,7 +201,7 @@ __device__ __forceinline__ void block_reduce_store(double acc, double* out) {
 // Bottom of the V-cycle in one CTA
 // ---------------------------------------------------------------------------
 
-constexpr int kBottomThreads = 1024;
+constexpr int kBottomThreads = 512;
 constexpr int kBottomMaxLevels = 8;
 constexpr int kBottomSmemBytes = 200 * 1024;
 
@@ -289,6 +289,44 @@ size_t plan_bottom_smem(BottomArgs<T>& a, const LevelDev* levels, int lb, int or
 // x-direction, 1/D and b) into registers, and a half-sweep is only the six
 // neighbour loads, the update and its store.  (The arithmetic is the list
 // kernels', so a level gives the same bits in the bottom as outside it.)
+// The hoisted sweeps with K unknowns per colour and thread (K = 1 when a
+// colour has at most one unknown per thread, which keeps the loop's state in
+// registers under the bottom kernel's 64-register budget).
+template <int KIND, typename T, int K>
+__device__ __forceinline__ void bottom_sweeps_hoisted(const BottomView<T>& L, int sweeps, unsigned nthr,
+                                                      bool one_warp) {
+  const Geom& g = L.g;
+  T* const phi[2] = {L.phi[0], L.phi[1]};
+  const int P = g.P;
+  const long long sz = g.sz;
+  long long at[2][K];
+  int dx[2][K];
+  T id[2][K], b[2][K];
+  bool has[2][K];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t i = threadIdx.x + k * nthr;
+      has[c][k] = i < L.n[c];
+      const uint32_t e = has[c][k] ? L.list[c][i] : 0u;
+      at[c][k] = e & kListAt;
+      has[c][k] = has[c][k] && entry_ok(g, at[c][k], one_warp ? 1 : 2);
+      dx[c][k] = (e & kListPlusX) ? 1 : -1;
+      id[c][k] = has[c][k] ? (KIND == 1 ? L.rinvd[c][i] : T(1) / T(6)) : T(0);
+      b[c][k] = has[c][k] ? L.rhs[c][at[c][k]] : T(0);
+    }
+  for (int s = 0; s < sweeps; ++s)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (has[c][k]) phi[c][at[c][k]] = (nbr_sum<T>(phi[c ^ 1], at[c][k], dx[c][k], P, sz) - b[c][k]) * id[c][k];
+      if (one_warp) __syncwarp();
+      else __syncthreads();
+    }
+}
+
 template <int KIND, typename T>
 __device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
   const Geom& g = L.g;
@@ -299,35 +337,10 @@ __device__ void bottom_smooth(const BottomView<T>& L, int sweeps) {
     return;
   }
   T* const phi[2] = {L.phi[0], L.phi[1]};
-  const int P = g.P;
-  const long long sz = g.sz;
-  if (L.n[0] <= 2 * nthr && L.n[1] <= 2 * nthr) {
-    long long at[2][2];
-    int dx[2][2];
-    T id[2][2], b[2][2];
-    bool has[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const uint32_t i = threadIdx.x + k * nthr;
-        has[c][k] = i < L.n[c];
-        const uint32_t e = has[c][k] ? L.list[c][i] : 0u;
-        at[c][k] = e & kListAt;
-        has[c][k] = has[c][k] && entry_ok(g, at[c][k], one_warp ? 1 : 2);
-        dx[c][k] = (e & kListPlusX) ? 1 : -1;
-        id[c][k] = has[c][k] ? (KIND == 1 ? L.rinvd[c][i] : T(1) / T(6)) : T(0);
-        b[c][k] = has[c][k] ? L.rhs[c][at[c][k]] : T(0);
-      }
-    for (int s = 0; s < sweeps; ++s)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-          if (has[c][k]) phi[c][at[c][k]] = (nbr_sum<T>(phi[c ^ 1], at[c][k], dx[c][k], P, sz) - b[c][k]) * id[c][k];
-        if (one_warp) __syncwarp();
-        else __syncthreads();
-      }
+  if (L.n[0] <= nthr && L.n[1] <= nthr) {
+    bottom_sweeps_hoisted<KIND, T, 1>(L, sweeps, nthr, one_warp);
+  } else if (L.n[0] <= 2 * nthr && L.n[1] <= 2 * nthr) {
+    bottom_sweeps_hoisted<KIND, T, 2>(L, sweeps, nthr, one_warp);
   } else {
     for (int s = 0; s < sweeps; ++s)
       for (int c = 0; c < 2; ++c) {
@@ -510,25 +523,49 @@ __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
     }
     if (a.first_smem == 0) {
       const long long tot = a.L[0].g.total;
-      constexpr int U = 8;
-      for (long long e0 = threadIdx.x; e0 < 2 * tot; e0 += U * (long long)blockDim.x) {
-        T r[U], ph[U];
+      if (keep) {
+        constexpr int U = 8;
+        for (long long e0 = threadIdx.x; e0 < 2 * tot; e0 += U * (long long)blockDim.x) {
+          T r[U], ph[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const long long e = e0 + u * (long long)blockDim.x;
-          const int c = e >= tot;
-          const long long o = e - c * tot;
-          r[u] = e < 2 * tot ? a.L[0].rhs[c][o] : T(0);
-          ph[u] = (e < 2 * tot && keep) ? a.L[0].phi[c][o] : T(0);
+          for (int u = 0; u < U; ++u) {
+            const long long e = e0 + u * (long long)blockDim.x;
+            const int c = e >= tot;
+            const long long o = e - c * tot;
+            r[u] = e < 2 * tot ? a.L[0].rhs[c][o] : T(0);
+            ph[u] = e < 2 * tot ? a.L[0].phi[c][o] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long e = e0 + u * (long long)blockDim.x;
+            const int c = e >= tot;
+            const long long o = e - c * tot;
+            if (e < 2 * tot) {
+              V[0].rhs[c][o] = r[u];
+              V[0].phi[c][o] = ph[u];
+            }
+          }
         }
+      } else {
+        // b only (dPhi is 0), in batches of 24 loads per thread: the usual
+        // 16^3 top level of the bottom in one round trip at 512 threads
+        constexpr int U = 24;
+        for (long long e0 = threadIdx.x; e0 < 2 * tot; e0 += U * (long long)blockDim.x) {
+          T r[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const long long e = e0 + u * (long long)blockDim.x;
-          const int c = e >= tot;
-          const long long o = e - c * tot;
-          if (e < 2 * tot) {
-            V[0].rhs[c][o] = r[u];
-            V[0].phi[c][o] = ph[u];
+          for (int u = 0; u < U; ++u) {
+            const long long e = e0 + u * (long long)blockDim.x;
+            const int c = e >= tot;
+            r[u] = e < 2 * tot ? a.L[0].rhs[c][e - c * tot] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long e = e0 + u * (long long)blockDim.x;
+            const int c = e >= tot;
+            if (e < 2 * tot) {
+              V[0].rhs[c][e - c * tot] = r[u];
+              V[0].phi[c][e - c * tot] = T(0);
+            }
           }
         }
       }

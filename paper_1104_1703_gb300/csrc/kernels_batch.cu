@@ -294,7 +294,7 @@ __device__ void level0_sweeps(const PatchLevel& L, const uint32_t* n, int sweeps
     }
 }
 
-__global__ void __launch_bounds__(kBottomThreads)
+__global__ void __launch_bounds__(kBottomThreads, 1)
     batch_bottom_kernel(const BatchBottom* __restrict__ args, int npatches, const PatchLevel* __restrict__ pls,
                         const int* __restrict__ state) {
   pdl_wait();

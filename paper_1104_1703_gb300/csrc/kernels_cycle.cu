@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
 
 // The one-CTA bottom V-cycle (bottom_run) as a kernel of its own.
 template <int KIND, typename T, bool SMEM>
-__global__ void __launch_bounds__(kBottomThreads) bottom_kernel(BottomArgs<T> a) {
+__global__ void __launch_bounds__(kBottomThreads, 1) bottom_kernel(BottomArgs<T> a) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bottom_run<KIND, T, SMEM>(a, smem_raw);
