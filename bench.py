@@ -71,6 +71,7 @@ def parse():
                    help="mixed form: FP32 V-cycles per FP64 refinement step (0: the fastest of 1..8, "
                         "measured before the timed run)")
     p.add_argument("--batch-only", action="store_true", help="time only the 96-patch batched workload")
+    p.add_argument("--learned-only", action="store_true", help="run only the learned-guess training and evaluation")
     p.add_argument("--no-holes", action="store_true", help="skip the 512^3 complex-boundary workload")
     p.add_argument("--no-wcycles", action="store_true", help="skip the W-cycle schedules (N_cycles = 2, 3)")
     p.add_argument("--profile", action="store_true",
@@ -625,6 +626,12 @@ def run_ours(args):
         torch.cuda.set_device(0)
     device = torch.device("cuda", torch.cuda.current_device())
     from paper_1104_1703_gb300 import binding as B
+
+    if args.learned_only:
+        res = run_learned(args)
+        if rank == 0:
+            print(json.dumps({"learned_guess": res}), flush=True)
+        return
 
     if args.batch_only:
         stream = torch.cuda.Stream(device=device)
