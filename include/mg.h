@@ -112,7 +112,15 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  warp reads whole runs of every array; 0 = one thread per
  *                  active cell of the colour's compact list.  The results
  *                  are bit-identical.  (The FP64 sweeps always use the cell
- *                  lists.) */
+ *                  lists.)
+ *  coarse_matrix   1 = solve the coarsest level, when it has at most 64
+ *                  unknowns and runs inside the one-CTA bottom cycle, through
+ *                  the precomputed affine map of its coarse_sweeps red-black
+ *                  sweeps (built once per mask, one launch): a small
+ *                  matrix-vector product instead of 2 * coarse_sweeps
+ *                  dependent half-sweeps per visit, the same result up to
+ *                  rounding; 0 = the sweeps.  (Batched patches use the
+ *                  sweeps.) */
 typedef struct {
   int n_pre, n_post, n_cycles, coarse_sweeps, hold_solves;
   double eta;
@@ -124,6 +132,7 @@ typedef struct {
   int smoother_pass;
   int fp64_sum;
   int fine_segments;
+  int coarse_matrix;
 } mg_options;
 
 #define MG_HIST_MAX 256
@@ -145,7 +154,7 @@ typedef struct {
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
  * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 0,
- * fp64_sum = 1, fine_segments = 1. */
+ * fp64_sum = 1, fine_segments = 1, coarse_matrix = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

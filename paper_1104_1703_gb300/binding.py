@@ -30,7 +30,8 @@ _d = ctypes.c_double
 class MGOptions(ctypes.Structure):
     _fields_ = [("n_pre", _i), ("n_post", _i), ("n_cycles", _i), ("coarse_sweeps", _i), ("hold_solves", _i),
                 ("eta", _d), ("order", _i), ("use_graphs", _i), ("precision", _i), ("inner_cycles", _i),
-                ("coarse_cluster", _i), ("smoother_pass", _i), ("fp64_sum", _i), ("fine_segments", _i)]
+                ("coarse_cluster", _i), ("smoother_pass", _i), ("fp64_sum", _i), ("fine_segments", _i),
+                ("coarse_matrix", _i)]
 
 
 class MGSolveInfo(ctypes.Structure):

@@ -228,7 +228,17 @@ struct BottomArgs {
   int n_pre, n_post, coarse_sweeps;
   int n_cycles;  // coarse iterations per level (Section 5.3): 1 V-cycle, 2 or more W-cycle
   int first_smem;  // levels first_smem .. nlev-1 are staged in shared memory (with SMEM)
+  // The coarsest solve as a precomputed map (coarse_matrix_kernel), or
+  // nullptr: n_r + n_b rows, n_r + 2 n_b columns (row-major), for the
+  // deepest level's n_r red and n_b black unknowns.
+  const T* cmat;
+  uint32_t cmat_n[2];
 };
+
+// Largest coarsest level solved through its precomputed map: unknowns of
+// both colours together (the map has at most kCoarseMatMax rows and
+// 2 kCoarseMatMax columns; eight of the bottom's 512 threads per row)
+constexpr int kCoarseMatMax = 64;
 
 // a level's working arrays: its records (list entries and, second order,
 // 1/D per unknown) always in shared memory, its correction and right-hand
@@ -425,6 +435,56 @@ __device__ void bottom_prolong(const BottomView<T>& F, const BottomView<T>& C, i
   __syncthreads();
 }
 
+// The coarsest solve through its precomputed map (option coarse_matrix): the
+// coarse_sweeps red-black sweeps of level L are an affine map of the
+// level's right-hand side b and of its black unknowns' current correction
+// (the first red half-sweep overwrites every red one unread),
+//   (x_r, x_b)_final = M (b_r, b_b, x_b)_initial,
+// which coarse_matrix_kernel has tabulated column by column with the same
+// sweeps.  Eight threads form each output row's dot product (partial sums
+// strided over the columns, then combined by shuffles).  The result equals
+// the sweeps' up to rounding.  Falls back to the sweeps when the level's
+// current counts are not the map's.
+template <int KIND, typename T>
+__device__ void bottom_coarse_map(const BottomView<T>& L, const T* __restrict__ M, const uint32_t* mn, int sweeps,
+                                  T* v) {
+  const uint32_t nr = mn[0], nb = mn[1];
+  if (L.n[0] != nr || L.n[1] != nb || nr + nb > (uint32_t)kCoarseMatMax || blockDim.x < 8 * kCoarseMatMax) {
+    bottom_smooth<KIND>(L, sweeps);
+    return;
+  }
+  const uint32_t nt = nr + nb, ncol = nt + nb;
+  for (uint32_t j = threadIdx.x; j < ncol; j += blockDim.x) {
+    const int c = j < nr ? 0 : (j < nt ? 1 : 2);
+    const uint32_t u = c == 0 ? j : (c == 1 ? j - nr : j - nt);
+    const long long at = L.list[c == 0 ? 0 : 1][u] & kListAt;
+    v[j] = c < 2 ? L.rhs[c][at] : L.phi[1][at];
+  }
+  __syncthreads();
+  constexpr int kParts = 8;
+  const uint32_t i = threadIdx.x / kParts, p = threadIdx.x % kParts;
+  T acc0 = T(0), acc1 = T(0);
+  if (i < nt) {
+    const T* row = M + (size_t)i * ncol;
+    uint32_t j = p;
+    for (; j + kParts < ncol; j += 2 * kParts) {
+      acc0 = fma(row[j], v[j], acc0);
+      acc1 = fma(row[j + kParts], v[j + kParts], acc1);
+    }
+    if (j < ncol) acc0 = fma(row[j], v[j], acc0);
+  }
+  T acc = acc0 + acc1;
+#pragma unroll
+  for (int off = kParts / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  __syncthreads();  // every v read before the corrections are overwritten
+  if (i < nt && p == 0) {
+    const int c = i < nr ? 0 : 1;
+    const uint32_t u = c ? i - nr : i;
+    L.phi[c][L.list[c][u] & kListAt] = acc;
+  }
+  __syncthreads();
+}
+
 // The Section 2 recipe with N_cycles coarse iterations per level (Section
 // 5.3: 1 is the V-cycle, 2 or more a W-cycle) on the small coarse levels
 // lb .. deepest, inside one CTA, from level lb's current state: its
@@ -443,6 +503,7 @@ template <int KIND, typename T, bool SMEM>
 __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
+  __shared__ T cmat_v[2 * kCoarseMatMax];        // inputs of the coarsest solve's map
   // thread i sets up level i (the list lengths are global loads: made at
   // once rather than one after another)
   if (threadIdx.x < (unsigned)a.nlev) {
@@ -585,7 +646,8 @@ __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
       bottom_restrict<KIND>(V[i], V[i + 1], a.bit, a.n_pre >= 1);
       owe[i] = a.n_cycles;
     }
-    bottom_smooth<KIND>(V[last], a.coarse_sweeps);
+    if (a.cmat) bottom_coarse_map<KIND>(V[last], a.cmat, a.cmat_n, a.coarse_sweeps, cmat_v);
+    else bottom_smooth<KIND>(V[last], a.coarse_sweeps);
     for (i = last - 1; i >= 0; --i) {  // ascend until a level owes a visit
       if (--owe[i] > 0) break;
       bottom_prolong(V[i], V[i + 1], a.n_post >= 1 ? 1 : 0);  // red: see prolong_list_kernel

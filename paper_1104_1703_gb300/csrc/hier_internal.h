@@ -62,6 +62,13 @@ struct mg_hierarchy {
   int n_f32_jobs = 0;
   bool bc_zero = true;  // the folded boundary terms are all 0
   bool rhsd_valid = false;  // level 0's b / D matches its b
+  // the coarsest solve's precomputed map per order (option coarse_matrix):
+  // device pointer in the arena, its red / black counts, and whether it
+  // matches the current mask
+  void* cmat[3] = {nullptr, nullptr, nullptr};
+  uint32_t cmat_n[3][2] = {};
+  bool cmat_ok[3] = {false, false, false};
+  int cmat_prec = 0;
   double* partials = nullptr;
   int max_partials = 0;
   double* dscal = nullptr;             // device scalars

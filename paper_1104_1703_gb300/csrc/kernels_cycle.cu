@@ -979,6 +979,84 @@ __global__ void __launch_bounds__(kMidThreads, 1) mid_kernel(MidArgs<T> a) {
   }
 }
 
+// The coarsest solve's map for bottom_coarse_map: column j of M
+// is the result (x_r, x_b) of `sweeps` red-black sweeps of the deepest level
+// started from a unit input, b = e_j for j < n_r + n_b with a zero initial
+// correction, or the initial black correction e_(j - n_r - n_b) with b = 0.
+// One warp per column, kCmWarps columns per CTA.  Each CTA first indexes the
+// level's unknowns: slot -> position in its colour's list, then per unknown
+// the positions of its six neighbours of the other colour (-1 for a slot
+// that is not an unknown: it holds 0).  The sweeps then run on the unknowns'
+// values alone, in per-warp shared-memory vectors, with the operator's own
+// arithmetic and summation order: (sum of the six neighbours - b) * (1/D).
+constexpr int kCmWarps = 16;
+constexpr long long kCmMaxSlots = 8192;  // slots per colour array of a level the map is built for
+
+template <typename T>
+struct CoarseMatArgs {
+  Geom g;
+  const uint32_t* list[2];
+  const T* invd[2];
+  uint32_t n[2];
+  int sweeps;
+  T* out;
+};
+
+template <int KIND, typename T>
+__global__ void __launch_bounds__(kCmWarps * 32) coarse_matrix_kernel(CoarseMatArgs<T> a) {
+  __shared__ int8_t map[2][kCmMaxSlots];
+  __shared__ int8_t nbr[2][kCoarseMatMax][6];
+  __shared__ T id[2][kCoarseMatMax];
+  __shared__ T xs[kCmWarps][2][kCoarseMatMax];
+  const Geom& g = a.g;
+  const uint32_t nr = a.n[0], nb = a.n[1], nt = nr + nb, ncol = nt + nb;
+  if (g.total > kCmMaxSlots || nt > (uint32_t)kCoarseMatMax) return;
+  for (long long e = threadIdx.x; e < 2 * g.total; e += blockDim.x) map[e >= g.total][e % g.total] = -1;
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < nt; e += blockDim.x) {
+    const int c = e >= nr;
+    const uint32_t u = c ? e - nr : e;
+    const long long at = a.list[c][u] & kListAt;
+    if (entry_ok(g, at, 12)) map[c][at] = (int8_t)u;
+  }
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < nt; e += blockDim.x) {
+    const int c = e >= nr;
+    const uint32_t u = c ? e - nr : e;
+    const uint32_t ent = a.list[c][u];
+    long long at = ent & kListAt;
+    if (!entry_ok(g, at, 12)) at = g.off0;
+    const long long dx = (ent & kListPlusX) ? 1 : -1;
+    const long long off[6] = {0, dx, -(long long)g.P, (long long)g.P, -g.sz, g.sz};
+    for (int k = 0; k < 6; ++k) nbr[c][u][k] = map[c ^ 1][at + off[k]];
+    id[c][u] = KIND == 1 ? a.invd[c][at] : T(1) / T(6);
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t j = blockIdx.x * kCmWarps + w;
+  if (j >= ncol) return;
+  T(*x)[kCoarseMatMax] = xs[w];
+  for (uint32_t u = lane; u < (uint32_t)kCoarseMatMax; u += 32) {
+    x[0][u] = T(0);
+    x[1][u] = (j >= nt && u == j - nt) ? T(1) : T(0);
+  }
+  __syncwarp();
+  const int bc = j < nr ? 0 : (j < nt ? 1 : -1);  // the colour of the unit right-hand side
+  const uint32_t bu = bc == 0 ? j : j - nr;
+  for (int s = 0; s < a.sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      for (uint32_t u = lane; u < a.n[c]; u += 32) {
+        T v[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = nbr[c][u][k] >= 0 ? x[c ^ 1][nbr[c][u][k]] : T(0);
+        const T sum = ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
+        x[c][u] = (sum - ((bc == c && bu == u) ? T(1) : T(0))) * id[c][u];
+      }
+      __syncwarp();
+    }
+  for (uint32_t i = lane; i < nt; i += 32) a.out[(size_t)i * ncol + j] = i < nr ? x[0][i] : x[1][i - nr];
+}
+
 // b / D of the level-0 unknowns (D = 6 + ghost faces), for SCALED sweeps;
 // 0 on inactive cells.
 __global__ void scale_rhs_kernel(long long total, const double* __restrict__ r0, const double* __restrict__ r1,
@@ -1085,17 +1163,24 @@ bool fill_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_p
   a.n_post = n_post;
   a.coarse_sweeps = coarse_sweeps;
   a.n_cycles = n_cycles;
+  a.cmat = nullptr;
+  a.cmat_n[0] = a.cmat_n[1] = 0;
   *smem_bytes = plan_bottom_smem(a, levels, lb, order);
   return *smem_bytes <= (size_t)kBottomSmemBytes;
 }
 
 template <typename T>
 cudaError_t bottom_t(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post, int coarse_sweeps,
-                     int n_cycles, cudaStream_t s) {
+                     int n_cycles, const T* cmat, const uint32_t* cmat_n, cudaStream_t s) {
   BottomArgs<T> a;
   size_t bytes = 0;
   if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, a, &bytes))
     return cudaErrorInvalidValue;
+  if (cmat && cmat_n) {  // the coarsest solve through its precomputed map
+    a.cmat = cmat;
+    a.cmat_n[0] = cmat_n[0];
+    a.cmat_n[1] = cmat_n[1];
+  }
   const bool sm = a.first_smem < a.nlev;  // some level's correction staged
   count_launch();
   if (order == 1) {
@@ -1127,7 +1212,7 @@ cudaError_t launch_mid_cluster(const MidArgs<T>& a, size_t bytes, cudaStream_t s
 
 template <typename T>
 cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
-                  int coarse_sweeps, cudaStream_t s) {
+                  int coarse_sweeps, const T* cmat, const uint32_t* cmat_n, cudaStream_t s) {
   MidArgs<T> a;
   a.nmid = lb - m;
   if (m < 1 || a.nmid < 1 || a.nmid > kMidMaxLevels) return cudaErrorInvalidValue;
@@ -1151,6 +1236,11 @@ cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order,
   size_t bytes = 0;
   if (!fill_bottom(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, 1, a.bottom, &bytes))
     return cudaErrorInvalidValue;
+  if (cmat && cmat_n) {
+    a.bottom.cmat = cmat;
+    a.bottom.cmat_n[0] = cmat_n[0];
+    a.bottom.cmat_n[1] = cmat_n[1];
+  }
   count_launch();
   const bool sm = a.bottom.first_smem < a.bottom.nlev;
   if (order == 1) return sm ? launch_mid_cluster<2, T, true>(a, bytes, s) : launch_mid_cluster<2, T, false>(a, bytes, s);
@@ -1158,17 +1248,57 @@ cudaError_t mid_t(const LevelDev* levels, int m, int lb, int deepest, int order,
 }
 
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
-                          int coarse_sweeps, int n_cycles, int prec, cudaStream_t s) {
-  return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, s)
-                       : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles, s);
+                          int coarse_sweeps, int n_cycles, int prec, const void* cmat, const uint32_t* cmat_n,
+                          cudaStream_t s) {
+  return prec == kFP32 ? bottom_t<float>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles,
+                                         static_cast<const float*>(cmat), cmat_n, s)
+                       : bottom_t<double>(levels, lb, deepest, order, n_pre, n_post, coarse_sweeps, n_cycles,
+                                          static_cast<const double*>(cmat), cmat_n, s);
+}
+
+bool coarse_map_fits(const LevelDev& L, int order) {
+  return L.level >= 1 && L.g.total <= kCmMaxSlots &&
+         (long long)L.hcount[order * 2] + L.hcount[order * 2 + 1] <= kCoarseMatMax;
+}
+
+size_t coarse_map_bytes(int prec) {
+  return (size_t)kCoarseMatMax * 2 * kCoarseMatMax * (prec == kFP32 ? sizeof(float) : sizeof(double));
+}
+
+template <typename T>
+cudaError_t coarse_map_t(const LevelDev& L, int order, int sweeps, T* out, cudaStream_t s) {
+  const Fields<T> f = fields(L, T());
+  CoarseMatArgs<T> a;
+  a.g = L.g;
+  for (int c = 0; c < 2; ++c) {
+    a.list[c] = L.list[order][c];
+    a.invd[c] = f.invd[c];
+    a.n[c] = L.hcount[order * 2 + c];
+  }
+  a.sweeps = sweeps;
+  a.out = out;
+  const uint32_t ncol = a.n[0] + 2 * a.n[1];
+  const unsigned grid = (ncol + kCmWarps - 1) / kCmWarps;
+  if (grid == 0) return cudaSuccess;
+  count_launch();
+  if (order == 1) coarse_matrix_kernel<2, T><<<grid, kCmWarps * 32, 0, s>>>(a);
+  else coarse_matrix_kernel<1, T><<<grid, kCmWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_map(const LevelDev& L, int order, int sweeps, int prec, void* out, cudaStream_t s) {
+  return prec == kFP32 ? coarse_map_t<float>(L, order, sweeps, static_cast<float*>(out), s)
+                       : coarse_map_t<double>(L, order, sweeps, static_cast<double*>(out), s);
 }
 
 bool mid_level(const Geom& g) { return (long long)g.hx * g.ny * g.nz <= kMidSlots; }
 
 cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
-                       int coarse_sweeps, int prec, cudaStream_t s) {
-  return prec == kFP32 ? mid_t<float>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps, s)
-                       : mid_t<double>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps, s);
+                       int coarse_sweeps, int prec, const void* cmat, const uint32_t* cmat_n, cudaStream_t s) {
+  return prec == kFP32 ? mid_t<float>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps,
+                                      static_cast<const float*>(cmat), cmat_n, s)
+                       : mid_t<double>(levels, m, lb, deepest, order, n_pre, n_post, coarse_sweeps,
+                                       static_cast<const double*>(cmat), cmat_n, s);
 }
 
 cudaError_t launch_scale_rhs(const LevelDev& L0, cudaStream_t s) {

@@ -181,7 +181,8 @@ bool valid_options(const mg_options& o) {
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
          (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
-         (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 1;
+         (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 1 &&
+         (o.coarse_matrix == 0 || o.coarse_matrix == 1);
 }
 
 // Number of levels: halve (ceil) until every dimension is at most 2.
@@ -329,11 +330,13 @@ mg_status smooth(mg_hierarchy* H, int l, int order, int sweeps, int prec = kFP64
 // FP64 or (inner cycles of the mixed form) FP32.
 mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool update_last = false) {
   const mg_options& o = H->opt;
+  // the coarsest solve's precomputed map, when it matches this solve
+  const void* cmat = (H->cmat_ok[order] && H->cmat_prec == prec) ? H->cmat[order] : nullptr;
   // the small coarse levels run as one single-CTA launch, which carries
   // the N_cycles recursion below level l itself
   if (l >= 1 && small_level(H->L[l].g))
     return launch_ok(H, launch_bottom(H->L, l, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps,
-                                      o.n_cycles, prec, H->cur),
+                                      o.n_cycles, prec, cmat, H->cmat_n[order], H->cur),
                      "bottom cycle");
   // the middle levels and the bottom as one launch of a thread-block cluster
   if (l >= 1 && o.n_cycles == 1 && o.coarse_cluster && mid_level(H->L[l].g) && l < H->deepest[order]) {
@@ -341,7 +344,7 @@ mg_status iteration(mg_hierarchy* H, int l, int order, int prec = kFP64, bool up
     while (lb < H->deepest[order] && !small_level(H->L[lb].g)) ++lb;
     if (lb - l <= 4)
       return launch_ok(H, launch_mid(H->L, l, lb, H->deepest[order], order, o.n_pre, o.n_post, o.coarse_sweeps,
-                                     prec, H->cur),
+                                     prec, cmat, H->cmat_n[order], H->cur),
                        "middle levels");
   }
   if (l == H->deepest[order]) return smooth(H, l, order, o.coarse_sweeps, prec, update_last);
@@ -588,6 +591,17 @@ mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
     H->deepest[o] = -1;
     for (int l = 0; l < H->nlev && H->active[o][l] > 0; ++l) H->deepest[o] = l;
   }
+  // the coarsest solve's map of each order, for the W-cycle's bottom
+  for (int o = 1; o <= 2; ++o) {
+    H->cmat_ok[o] = false;
+    const int d = H->deepest[o];
+    if (!H->cmat[o] || d < 1 || !small_level(H->L[d].g) || !coarse_map_fits(H->L[d], o)) continue;
+    CKS(launch_ok(H, launch_coarse_map(H->L[d], o, H->opt.coarse_sweeps, H->cmat_prec, H->cmat[o], s),
+                  "coarsest-solve map"));
+    H->cmat_n[o][0] = H->L[d].hcount[o * 2];
+    H->cmat_n[o][1] = H->L[d].hcount[o * 2 + 1];
+    H->cmat_ok[o] = true;
+  }
   return MG_OK;
 }
 
@@ -677,6 +691,7 @@ void mg_default_options(mg_options* opt) {
   opt->smoother_pass = 0;
   opt->fp64_sum = 1;
   opt->fine_segments = 1;
+  opt->coarse_matrix = 1;
 }
 
 const char* mg_status_string(mg_status st) {
@@ -847,6 +862,11 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   size_t o_part = A.reserve(sizeof(double) * H->max_partials);
   size_t o_scal = A.reserve(sizeof(double) * 8);
   size_t o_err = A.reserve(sizeof(int) * 4);
+  // the coarsest solve's maps, in the cycles' precision
+  const bool cmaps = o.coarse_matrix == 1;
+  const int cprec = mixed ? kFP32 : kFP64;
+  size_t o_cmat[3] = {0, 0, 0};
+  for (int ord = 1; ord <= 2 && cmaps; ++ord) o_cmat[ord] = A.reserve(coarse_map_bytes(cprec));
   size_t o_cnt = A.reserve(sizeof(unsigned long long) * 2 * kMaxLevels);
 
   cudaError_t e = dev_malloc((void**)&H->arena, A.used);
@@ -904,6 +924,8 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->partials = (double*)(base + o_part);
   H->dscal = (double*)(base + o_scal);
   H->err_flag = (int*)(base + o_err);
+  H->cmat_prec = cprec;
+  for (int ord = 1; ord <= 2; ++ord) H->cmat[ord] = cmaps ? (void*)(base + o_cmat[ord]) : nullptr;
   for (int l = 0; l < H->nlev; ++l) H->L[l].g.fault = (unsigned*)(H->err_flag + 1);
   H->counts = (unsigned long long*)(base + o_cnt);
   if (pass) {

@@ -249,8 +249,16 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
 // One multigrid iteration with n_cycles coarse iterations per level (1: V,
 // 2 or more: W) on levels lb .. deepest in one CTA, for small levels (every
 // level lb..deepest satisfies small_level); lb >= 1.
+// cmat / cmat_n (nullable): the coarsest solve's precomputed map and its
+// red and black unknown counts (launch_coarse_map builds it)
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
-                          int coarse_sweeps, int n_cycles, int prec, cudaStream_t s);
+                          int coarse_sweeps, int n_cycles, int prec, const void* cmat, const uint32_t* cmat_n,
+                          cudaStream_t s);
+// The coarsest solve of level L (order) as a map, for the bottom cycle:
+// whether it fits, the bytes of one map, and its build (one launch).
+bool coarse_map_fits(const LevelDev& L, int order);
+size_t coarse_map_bytes(int prec);
+cudaError_t launch_coarse_map(const LevelDev& L, int order, int sweeps, int prec, void* out, cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
 // Middle levels (more than 4096, at most kMidSlots cells per colour): the
 // V-cycle from level m (1 <= m < lb) through levels m .. lb-1, and the bottom
@@ -258,7 +266,7 @@ int residual_norm_blocks(const Geom& g);
 constexpr long long kMidSlots = 1 << 17;
 bool mid_level(const Geom& g);
 cudaError_t launch_mid(const LevelDev* levels, int m, int lb, int deepest, int order, int n_pre, int n_post,
-                       int coarse_sweeps, int prec, cudaStream_t s);
+                       int coarse_sweeps, int prec, const void* cmat, const uint32_t* cmat_n, cudaStream_t s);
 // Mixed precision: FP64 residual of level 0 over every unknown -> FP32
 // right-hand side -r^ and zero FP32 correction, plus the norm (like
 // launch_residual_norm2); and Phi += e in FP64.

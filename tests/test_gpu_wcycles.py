@@ -157,3 +157,40 @@ def test_boundary_gradient_chain_on_device(dev, oracle):
         errs[d] = np.abs(phi - p["phi_exact"])[p["mask"] > 0].max()
     assert max(errs[0.2], errs[0.12]) <= 1.1 * min(errs[0.2], errs[0.12])
     assert errs[0.0] >= 2.0 * errs[0.2]
+
+
+@pytest.mark.parametrize("name", ["ball32", "holes32", "blob48x32x40"])
+@pytest.mark.parametrize("n_cycles,precision", [(1, 0), (2, 0), (3, 0), (1, 1), (2, 1)])
+def test_coarsest_map_matches_the_sweeps(dev, name, n_cycles, precision):
+    """The coarsest solve through its precomputed map (option coarse_matrix)
+    against the coarse_sweeps sweeps it tabulates, in V- and W-cycles of both
+    forms: the same decisions and cycle counts, solutions and residual
+    histories within rounding."""
+    w = CASES[name]
+    res = []
+    for cm in (0, 1):
+        H, _ = make_pair(w, dev, n_cycles=n_cycles, precision=precision, coarse_matrix=cm)
+        st, info = H.solve(1e-10, 60)
+        assert st == 0
+        res.append((info, H.get_solution()))
+    (i0, s0), (i1, s1) = res
+    assert (i0["cycles"], i0["order"], i0["switched"]) == (i1["cycles"], i1["order"], i1["switched"])
+    assert relerr(s1, s0) < 1e-12
+    assert np.abs(i1["hist"] - i0["hist"]).max() <= 1e-9 * i0["r_zero"]
+
+
+def test_coarsest_map_follows_a_mask_update(dev):
+    """The map is rebuilt with the hierarchy: after update_mask a W(2) solve
+    equals a fresh hierarchy's."""
+    a, b = CASES["blob48x32x40"], W.blob_patch((40, 32, 48), seed=105)
+    H, _ = make_pair(a, dev, n_cycles=2)
+    H.solve(1e-10, 60)
+    H.update_mask(torch.from_numpy(b["mask"]).to(dev))
+    H.set_rhs(torch.from_numpy(b["rho"]).to(dev))
+    H.set_dirichlet_from_coarse(torch.from_numpy(b["phi_c"]).to(dev), b["origin"])
+    H.set_solution(None)
+    st, info = H.solve(1e-10, 60)
+    F, _ = make_pair(b, dev, n_cycles=2)
+    st2, info2 = F.solve(1e-10, 60)
+    assert st == st2 == 0 and info["cycles"] == info2["cycles"]
+    assert np.array_equal(H.get_solution(), F.get_solution())
