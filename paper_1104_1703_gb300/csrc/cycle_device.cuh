@@ -500,7 +500,7 @@ __device__ void bottom_coarse_map(const BottomView<T>& L, const T* __restrict__ 
 // launches per level visit and the 2 * coarse_sweeps launches of each
 // coarsest solve.
 template <int KIND, typename T, bool SMEM>
-__device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
+__device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw, bool wait_after_setup = false) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ BottomView<T> V[kBottomMaxLevels];  // one copy per block, read by every thread
   __shared__ T cmat_v[2 * kCoarseMatMax];        // inputs of the coarsest solve's map
@@ -575,6 +575,10 @@ __device__ void bottom_run(const BottomArgs<T>& a, unsigned char* smem_raw) {
         }
     }
   }
+  // The level views and the unknown records are built with the mask and do
+  // not change during a solve: a kernel of its own stages them before the
+  // wait on the previous kernel, which wrote level lb's right-hand side.
+  if (wait_after_setup) pdl_wait();
   if (SMEM) {
     const bool keep = a.n_cycles > 1;
     for (int i = a.first_smem > 1 ? a.first_smem : 1; i < a.nlev; ++i) {

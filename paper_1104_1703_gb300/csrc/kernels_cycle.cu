@@ -72,36 +72,51 @@ struct PerThread {
 // multiply-add as the update's only FP64 instruction.
 template <int KIND, typename T, bool UPDATE, bool SCALED = false, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
-  pdl_wait();
   constexpr int PER = PerThread<T>::value;
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const uint32_t n = *a.count;
   const uint32_t stride = gridDim.x * kListBlock;
-  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+  uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
+  // A round's list entries and diagonals are built with the mask and do
+  // not change during a solve: the first round's are loaded before the wait
+  // on the previous kernel (their round trip overlaps its end), the next
+  // round's while the current one computes.
+  uint32_t e[PER];
+  T d[PER];
+  auto invariants = [&](uint32_t b0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = b0 + u * stride;
+      e[u] = i < n ? a.list[i] : 0u;
+      d[u] = i < n ? inv_diag<KIND>(KIND == 0 ? a.code[e[u] & kListAt] : 0, a.invd, e[u] & kListAt, tab) : T(0);
+    }
+  };
+  invariants(base);
+  pdl_wait();
+  for (; base < n; base += PER * stride) {
     long long at[PER];
-    T s[PER], b[PER], d[PER];
+    T s[PER], b[PER], dd[PER];
     bool ok[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t i = base + u * stride;
-      ok[u] = i < n;
-      const uint32_t e = ok[u] ? a.list[i] : 0u;
-      at[u] = e & kListAt;
+      ok[u] = base + u * stride < n;
+      at[u] = e[u] & kListAt;
       ok[u] = ok[u] && entry_ok(a.g, at[u], 3);
+      dd[u] = d[u];
       if (ok[u]) {
         if constexpr (EXACT)
-          s[u] = nbr_sum_exact(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+          s[u] = nbr_sum_exact(a.other, at[u], (e[u] & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
         else
-          s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+          s[u] = nbr_sum(a.other, at[u], (e[u] & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
         b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
-        d[u] = inv_diag<KIND>(KIND == 0 ? a.code[at[u]] : 0, a.invd, at[u], tab);
       }
     }
+    invariants(base + PER * stride);
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (!ok[u]) continue;
-      const T v = SCALED ? fma(s[u], d[u], -b[u]) : (s[u] - b[u]) * d[u];
+      const T v = SCALED ? fma(s[u], dd[u], -b[u]) : (s[u] - b[u]) * dd[u];
       a.self[at[u]] = v;
       if (UPDATE) a.phi64[at[u]] += widen_f32(v);
     }
@@ -122,7 +137,6 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
 // would add to that.)
 template <typename T, bool UPDATE, int SHIFT>
 __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
-  pdl_wait();
   constexpr int PER = 2;
   constexpr int GROUPS = 32 >> SHIFT;  // segments per warp and round
   __shared__ T tab[16];
@@ -139,6 +153,9 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
     const uint32_t i = group + u * ngroups;
     next[u] = i < n ? a.list[i] : 0u;
   }
+  // the segment entries are constant during a solve: the first ones are
+  // loaded before the wait on the previous kernel
+  pdl_wait();
   for (uint32_t base = group; base < n; base += step) {
     uint32_t cur[PER];
 #pragma unroll
@@ -411,12 +428,25 @@ struct ProlongArgs {
 // unknowns first would not change the result.
 template <typename T>
 __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T> a) {
-  pdl_wait();
   constexpr int PER = 2;
   const Geom gf = a.gf;
   const uint32_t n0 = a.skip_red ? 0u : *a.count[0], n = n0 + *a.count[1];
   const uint32_t stride = gridDim.x * kListBlock;
-  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+  uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
+  // the list entries are constant during a solve: the first round's are
+  // loaded before the wait on the previous kernel, the next round's while
+  // the current one computes
+  uint32_t e[PER];
+  auto entries = [&](uint32_t b0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = b0 + u * stride;
+      e[u] = i < n ? (i >= n0 ? a.list[1][i - n0] : a.list[0][i]) : 0u;
+    }
+  };
+  entries(base);
+  pdl_wait();
+  for (; base < n; base += PER * stride) {
     long long at[PER];
     int cc[PER];
     T w[PER], old[PER];
@@ -428,8 +458,7 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
       if (!ok[u]) continue;
       const int c = i >= n0;
       cc[u] = c;
-      const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
-      at[u] = e & kListAt;
+      at[u] = e[u] & kListAt;
       ok[u] = entry_ok(gf, at[u], 6);
       if (!ok[u]) continue;
       int q, j, k;
@@ -437,6 +466,7 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
       w[u] = p2_sum(a.gc, a.cphi[0], a.cphi[1], q, j, k, c, PlainLoad());
       old[u] = a.phi[c][at[u]];
     }
+    entries(base + PER * stride);
 #pragma unroll
     for (int u = 0; u < PER; ++u)
       if (ok[u]) a.phi[cc[u]][at[u]] = fma(w[u], T(1) / T(64), old[u]);
@@ -446,9 +476,8 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
 // The one-CTA bottom V-cycle (bottom_run) as a kernel of its own.
 template <int KIND, typename T, bool SMEM>
 __global__ void __launch_bounds__(kBottomThreads, 1) bottom_kernel(BottomArgs<T> a) {
-  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  bottom_run<KIND, T, SMEM>(a, smem_raw);
+  bottom_run<KIND, T, SMEM>(a, smem_raw, true);
 }
 
 struct NormArgs {
