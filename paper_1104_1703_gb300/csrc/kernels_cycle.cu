@@ -196,31 +196,43 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
 // (the grid is fixed per level, so the partials do not depend on scheduling).
 template <int KIND, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) res_list_kernel(ListArgs<T> a) {
-  pdl_wait();
   constexpr int PER = PerThread<T>::value;
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const Geom g = a.g;
   const uint32_t n = *a.count;
   const uint32_t stride = gridDim.x * kListBlock;
+  uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
+  // list entries and diagonals are fixed by the mask: loaded before the wait
+  // on the previous kernel (first round) and during the current round (next)
+  uint32_t e[PER];
+  T d[PER];
+  auto invariants = [&](uint32_t b0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t i = b0 + u * stride;
+      e[u] = i < n ? a.list[i] : 0u;
+      d[u] = i < n ? diag_of<KIND>(KIND == 0 ? a.code[e[u] & kListAt] : 0, a.diag, e[u] & kListAt, tab) : T(0);
+    }
+  };
+  invariants(base);
+  pdl_wait();
   double acc = 0.0;
-  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+  for (; base < n; base += PER * stride) {
     long long at[PER];
     T r[PER];
     bool ok[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t i = base + u * stride;
-      ok[u] = i < n;
-      const uint32_t e = ok[u] ? a.list[i] : 0u;
-      at[u] = e & kListAt;
+      ok[u] = base + u * stride < n;
+      at[u] = e[u] & kListAt;
       ok[u] = ok[u] && entry_ok(g, at[u], 4);
       if (ok[u]) {
-        const T s = nbr_sum_sel<EXACT>(a.other, at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
-        const uint8_t code = KIND == 0 ? a.code[at[u]] : 0;
-        r[u] = fma(-diag_of<KIND>(code, a.diag, at[u], tab), a.self[at[u]], s) - a.rhs[at[u]];
+        const T s = nbr_sum_sel<EXACT>(a.other, at[u], (e[u] & kListPlusX) ? 1 : -1, g.P, g.sz);
+        r[u] = fma(-d[u], a.self[at[u]], s) - a.rhs[at[u]];
       }
     }
+    invariants(base + PER * stride);
 #pragma unroll
     for (int u = 0; u < PER; ++u)
       if (ok[u]) acc = fma((double)r[u], (double)r[u], acc);
@@ -309,29 +321,55 @@ struct RestrictArgs {
   const uint32_t* ccount[2];
 };
 
-// Children residuals of coarse cell (I, J, K) (the scaled residuals r^ of its active children, summed in a fixed order).
+// What the mask fixes about the children of coarse cell (I, J, K): their
+// offsets, codes and diagonals (loaded before the wait on the previous
+// kernel; rows and planes past the fine level's end are its zero halo,
+// whose codes are 0).
+template <typename T>
+struct Children {
+  long long at[2][2];
+  uint8_t code[2][2][2];
+  T diag[2][2][2];
+};
+
+template <int KIND, bool BLACK_ZERO, typename T>
+__device__ __forceinline__ void child_invariants(const RestrictArgs<T>& a, int I, int J, int K, const T* tab,
+                                                 Children<T>& ch) {
+  const Geom& gf = a.gf;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      const int j = 2 * J + dj, k = 2 * K + dk;
+      const bool in = j < gf.ny && k < gf.nz;
+      ch.at[dk][dj] = gf.at(I, j, k);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const bool use = in && (c == 0 || !BLACK_ZERO);
+        const uint8_t cd = use ? a.code[c][ch.at[dk][dj]] : 0;
+        ch.code[dk][dj][c] = (cd & a.bit) ? cd : 0;
+        ch.diag[dk][dj][c] = use ? diag_of<KIND>(cd, a.diag[c], ch.at[dk][dj], tab) : T(0);
+      }
+    }
+}
+
+// Children residuals of coarse cell (I, J, K): the scaled residuals r^ of
+// its active children, summed in the order (dk, dj, colour).
 template <int KIND, bool BLACK_ZERO, typename T, bool EXACT = false>
-__device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, int I, int J, int K, const T* tab) {
+__device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, const Children<T>& ch, int J, int K) {
   const Geom& gf = a.gf;
   T sum = 0;
 #pragma unroll
-  for (int dk = 0; dk < 2; ++dk) {
-    const int k = 2 * K + dk;
-    if (k >= gf.nz) break;
+  for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
-    for (int dj = 0; dj < 2; ++dj) {
-      const int j = 2 * J + dj;
-      if (j >= gf.ny) break;
-      const long long at = gf.at(I, j, k);
+    for (int dj = 0; dj < 2; ++dj)
 #pragma unroll
       for (int c = 0; c < (BLACK_ZERO ? 1 : 2); ++c) {
-        const uint8_t cd = a.code[c][at];
-        if (!(cd & a.bit)) continue;
-        const T s = nbr_sum_sel<EXACT>(a.phi[c ^ 1], at, x_offset(c, j, k), gf.P, gf.sz);
-        sum += fma(-diag_of<KIND>(cd, a.diag[c], at, tab), a.phi[c][at], s) - a.rhs[c][at];
+        if (!ch.code[dk][dj][c]) continue;
+        const long long at = ch.at[dk][dj];
+        const T s = nbr_sum_sel<EXACT>(a.phi[c ^ 1], at, x_offset(c, 2 * J + dj, 2 * K + dk), gf.P, gf.sz);
+        sum += fma(-ch.diag[dk][dj][c], a.phi[c][at], s) - a.rhs[c][at];
       }
-    }
-  }
   return sum;
 }
 
@@ -346,15 +384,18 @@ __device__ __forceinline__ T child_residual_sum(const RestrictArgs<T>& a, int I,
 // residual.  Children outside the active set (of this order) count 0.
 template <int KIND, bool BLACK_ZERO, typename T>
 __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArgs<T> a) {
-  pdl_wait();
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const Geom gc = a.gc;
   const int I = blockIdx.x * kBlockX + threadIdx.x;
   const int J = blockIdx.y * kBlockY + threadIdx.y;
   const int K = blockIdx.z;
-  if (I >= gc.nx || J >= gc.ny) return;
-  const T sum = child_residual_sum<KIND, BLACK_ZERO>(a, I, J, K, tab);
+  const bool in = I < gc.nx && J < gc.ny;
+  Children<T> ch;
+  if (in) child_invariants<KIND, BLACK_ZERO>(a, I, J, K, tab, ch);  // fixed by the mask: before the wait
+  pdl_wait();
+  if (!in) return;
+  const T sum = child_residual_sum<KIND, BLACK_ZERO>(a, ch, J, K);
   const int C = (I + J + K) & 1;
   const long long atc = gc.at(I >> 1, J, K);
   a.crhs[C][atc] = T(-0.5) * sum;
@@ -369,21 +410,24 @@ __global__ void __launch_bounds__(kBlockX * kBlockY) restrict_kernel(RestrictArg
 // unknown, which spares the FP64 pipe the idle lanes of a box-wide grid.
 template <int KIND, bool BLACK_ZERO, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<T> a) {
-  pdl_wait();
   constexpr int PER = 2;
   __shared__ T tab[16];
   if (KIND == 0) init_tab(tab);
   const Geom gc = a.gc;
   const uint32_t n0 = *a.ccount[0], n = n0 + *a.ccount[1];
   const uint32_t stride = gridDim.x * kListBlock;
-  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
-    long long atc[PER];
-    int cc[PER];
-    T sum[PER];
-    bool ok[PER];
+  uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
+  long long atc[PER];
+  int cc[PER], JJ[PER], KK[PER];
+  bool ok[PER];
+  Children<T> ch[PER];
+  // the coarse unknowns and their children's codes and diagonals are fixed
+  // by the mask: the first round's are loaded before the wait on the
+  // previous kernel, the next round's while the current one computes
+  auto invariants = [&](uint32_t b0) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t i = base + u * stride;
+      const uint32_t i = b0 + u * stride;
       ok[u] = i < n;
       if (!ok[u]) continue;
       const int C = i >= n0;
@@ -391,15 +435,31 @@ __global__ void __launch_bounds__(kListBlock) restrict_list_kernel(RestrictArgs<
       atc[u] = (C ? a.clist[1][i - n0] : a.clist[0][i]) & kListAt;
       ok[u] = entry_ok(gc, atc[u], 5);
       if (!ok[u]) continue;
-      int Q, J, K;
-      gc.slot_of(atc[u], &Q, &J, &K);
-      sum[u] = child_residual_sum<KIND, BLACK_ZERO, T, EXACT>(a, 2 * Q + ((C ^ J ^ K) & 1), J, K, tab);
+      int Q;
+      gc.slot_of(atc[u], &Q, &JJ[u], &KK[u]);
+      child_invariants<KIND, BLACK_ZERO>(a, 2 * Q + ((C ^ JJ[u] ^ KK[u]) & 1), JJ[u], KK[u], tab, ch[u]);
     }
+  };
+  invariants(base);
+  pdl_wait();
+  for (; base < n; base += PER * stride) {
+    T sum[PER];
+    long long at2[PER];
+    int c2[PER];
+    bool ok2[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      if (!ok[u]) continue;
-      a.crhs[cc[u]][atc[u]] = T(-0.5) * sum[u];
-      a.cphi[cc[u]][atc[u]] = T(0);
+      ok2[u] = ok[u];
+      at2[u] = atc[u];
+      c2[u] = cc[u];
+      if (ok[u]) sum[u] = child_residual_sum<KIND, BLACK_ZERO, T, EXACT>(a, ch[u], JJ[u], KK[u]);
+    }
+    invariants(base + PER * stride);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!ok2[u]) continue;
+      a.crhs[c2[u]][at2[u]] = T(-0.5) * sum[u];
+      a.cphi[c2[u]][at2[u]] = T(0);
     }
   }
 }
