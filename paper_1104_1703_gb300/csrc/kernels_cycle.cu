@@ -604,15 +604,29 @@ struct RefineArgs {
 
 template <bool EXACT>
 __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs a) {
-  pdl_wait();
   constexpr int PER = 2;
   __shared__ double tab[16];
   init_tab(tab);
   const Geom g = a.g;
   const uint32_t n0 = *a.count[0], n = n0 + *a.count[1];
   const uint32_t stride = gridDim.x * kListBlock;
+  uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
+  // list entries and diagonals are fixed by the mask: the first round's are
+  // loaded before the wait on the previous kernel; each next round's
+  // entries while the current one computes, its diagonals with its data
+  uint32_t e[PER];
+  double D[PER];
+  auto entry = [&](uint32_t i) { return i < n ? (i >= n0 ? a.list[1][i - n0] : a.list[0][i]) : 0u; };
+#pragma unroll
+  for (int u = 0; u < PER; ++u) e[u] = entry(base + u * stride);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t i = base + u * stride;
+    D[u] = i < n ? tab[8 + __popc((unsigned)a.code[i >= n0][e[u] & kListAt] >> kGhostShift)] : 0.0;
+  }
+  pdl_wait();
   double acc = 0.0;
-  for (uint32_t base = blockIdx.x * kListBlock + threadIdx.x; base < n; base += PER * stride) {
+  for (bool first = true; base < n; base += PER * stride, first = false) {
     long long at[PER];
     int cc[PER];
     double r[PER];
@@ -624,14 +638,15 @@ __global__ void __launch_bounds__(kListBlock) refine_residual_kernel(RefineArgs 
       if (!ok[u]) continue;
       const int c = i >= n0;
       cc[u] = c;
-      const uint32_t e = c ? a.list[1][i - n0] : a.list[0][i];
-      at[u] = e & kListAt;
+      at[u] = e[u] & kListAt;
       ok[u] = entry_ok(g, at[u], 7);
       if (!ok[u]) continue;
-      const double s = nbr_sum_sel<EXACT>(a.phi[1 - c], at[u], (e & kListPlusX) ? 1 : -1, g.P, g.sz);
-      const double D = tab[8 + __popc((unsigned)a.code[c][at[u]] >> kGhostShift)];
-      r[u] = fma(-D, a.phi[c][at[u]], s) - a.rhs[c][at[u]];
+      const double s = nbr_sum_sel<EXACT>(a.phi[1 - c], at[u], (e[u] & kListPlusX) ? 1 : -1, g.P, g.sz);
+      const double Du = first ? D[u] : tab[8 + __popc((unsigned)a.code[c][at[u]] >> kGhostShift)];
+      r[u] = fma(-Du, a.phi[c][at[u]], s) - a.rhs[c][at[u]];
     }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) e[u] = entry(base + PER * stride + u * stride);
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (!ok[u]) continue;
