@@ -79,7 +79,7 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *                  and the folded boundary data stay FP64).  The paper has
  *                  no counterpart; the stopping test and the order switch
  *                  act on the FP64 residual norms as in FP64 mode.
- *  inner_cycles    FP32 V-cycles per refinement step (precision 1), 1..8.
+ *  inner_cycles    FP32 V-cycles per refinement step (precision 1), 1..16.
  *                  The stopping test and the switch act once per step; the
  *                  switch compares the step's residual ratio with
  *                  eta^inner_cycles (eta per multigrid iteration).

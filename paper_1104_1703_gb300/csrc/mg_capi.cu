@@ -179,7 +179,7 @@ std::vector<int> list_orders(int level, bool seg) {
 bool valid_options(const mg_options& o) {
   return o.n_pre >= 0 && o.n_post >= 0 && o.n_cycles >= 1 && o.n_cycles <= 4 && o.coarse_sweeps >= 1 &&
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
-         (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 8 &&
+         (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 16 &&
          (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
          (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 1 &&
          (o.coarse_matrix == 0 || o.coarse_matrix == 1);

@@ -99,7 +99,7 @@ def test_mixed_solve_against_oracle(dev, oracle, name):
     assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
 
 
-@pytest.mark.parametrize("inner", [3, 6, 8])
+@pytest.mark.parametrize("inner", [3, 6, 8, 13])
 @pytest.mark.parametrize("name", ["ball64", "holes64", "blob48x32x40", "union64"])
 def test_mixed_several_inner_cycles(dev, oracle, name, inner):
     """Several FP32 V-cycles per refinement step: the same tolerance as
@@ -122,10 +122,13 @@ def test_mixed_several_inner_cycles(dev, oracle, name, inner):
     st64, info64 = H64.solve(tol, 200)
     assert info["order"] == info64["order"] and info["switched"] == info64["switched"]
     # the switch is tested once per step, so a switching solve can spend up
-    # to a step of second-order cycles (and restart) before it trips
+    # to a step of second-order cycles (and restart) before it trips; and a
+    # step's FP32 cycles reduce the error equation's residual by at most
+    # about the FP32 precision, so two steps are the least for these
+    # tolerances however many cycles a step has
     slack = inner + 2 if not info["switched"] else 3 * inner
-    assert info64["cycles"] - 2 <= inner * info["cycles"] <= info64["cycles"] + slack, (info["cycles"],
-                                                                                      info64["cycles"])
+    assert info64["cycles"] - 2 <= inner * info["cycles"] <= max(info64["cycles"] + slack, 2 * inner), (
+        info["cycles"], info64["cycles"])
     per = []
     for order in (1, 2):   # updates of one V-cycle in each order
         Ho = _gpu(w, faces, precision=1, order=order)
