@@ -47,7 +47,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // KIND 0: level 0 (D from the ghost-face count); 1: coarse, second order
 // (per-cell D and 1/D); 2: coarse, first order (D = 6).
 template <int KIND, typename T>
-__device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, long long at, const T* tab) {
+__device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, uint32_t at, const T* tab) {
   if (KIND == 0) return tab[__popc((unsigned)code >> kGhostShift)];
   if (KIND == 1) return invd[at];
   return T(1) / T(6);
@@ -56,7 +56,7 @@ __device__ __forceinline__ T inv_diag(uint8_t code, const T* __restrict__ invd, 
 // The level-0 diagonal D = 6 + (ghost faces) comes from a table rather than
 // an int-to-double conversion, which would run on the FP64 pipe.
 template <int KIND, typename T>
-__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, long long at, const T* tab) {
+__device__ __forceinline__ T diag_of(uint8_t code, const T* __restrict__ diag, uint32_t at, const T* tab) {
   if (KIND == 0) return tab[8 + __popc((unsigned)code >> kGhostShift)];
   if (KIND == 1) return diag[at];
   return T(6);
@@ -125,6 +125,33 @@ __device__ __forceinline__ double nbr_sum_exact(const double* __restrict__ o, lo
   const double x[6] = {o[at], o[at + dx], o[at - P], o[at + P], o[at - sz], o[at + sz]};
   return exact_sum(x);
 }
+
+// The same sums on 32-bit slot offsets (a colour array holds fewer than
+// 2^31 elements, which the hierarchy's constructor checks), so that each
+// address is one multiply-add of the offset onto the base pointer rather than
+// 64-bit index arithmetic; xo is the offset of the x-neighbour that is not in
+// the same slot.  The order of the additions is nbr_sum's.
+template <typename T>
+__device__ __forceinline__ T nbr_sum32(const T* __restrict__ o, uint32_t at, uint32_t xo, uint32_t P, uint32_t sz) {
+  return ((o[at] + o[xo]) + (o[at - P] + o[at + P])) + (o[at - sz] + o[at + sz]);
+}
+
+__device__ __forceinline__ double nbr_sum_exact32(const double* __restrict__ o, uint32_t at, uint32_t xo, uint32_t P,
+                                                  uint32_t sz) {
+  const double x[6] = {o[at], o[xo], o[at - P], o[at + P], o[at - sz], o[at + sz]};
+  return exact_sum(x);
+}
+
+template <bool EXACT, typename T>
+__device__ __forceinline__ T nbr_sum_sel32(const T* __restrict__ o, uint32_t at, uint32_t xo, uint32_t P, uint32_t sz) {
+  if constexpr (EXACT && sizeof(T) == 8)
+    return nbr_sum_exact32(reinterpret_cast<const double*>(o), at, xo, P, sz);
+  else
+    return nbr_sum32(o, at, xo, P, sz);
+}
+
+// x-neighbour offset of list entry e at offset at
+__device__ __forceinline__ uint32_t x_nbr(uint32_t e, uint32_t at) { return (e & kListPlusX) ? at + 1u : at - 1u; }
 
 // nbr_sum, or (EXACT, FP64) nbr_sum_exact
 template <bool EXACT, typename T>

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   if (KIND == 0) init_tab(tab);
   const uint32_t n = *a.count;
   const uint32_t stride = gridDim.x * kListBlock;
+  const uint32_t P = (uint32_t)a.g.P, Z = (uint32_t)a.g.sz;
   uint32_t base = blockIdx.x * kListBlock + threadIdx.x;
   // A round's list entries and diagonals are built with the mask and do
   // not change during a solve: the first round's are loaded before the wait
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
   invariants(base);
   pdl_wait();
   for (; base < n; base += PER * stride) {
-    long long at[PER];
+    uint32_t at[PER];
     T s[PER], b[PER], dd[PER];
     bool ok[PER];
 #pragma unroll
@@ -105,10 +106,7 @@ __global__ void __launch_bounds__(kListBlock) gs_list_kernel(ListArgs<T> a) {
       ok[u] = ok[u] && entry_ok(a.g, at[u], 3);
       dd[u] = d[u];
       if (ok[u]) {
-        if constexpr (EXACT)
-          s[u] = nbr_sum_exact(a.other, at[u], (e[u] & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
-        else
-          s[u] = nbr_sum(a.other, at[u], (e[u] & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        s[u] = nbr_sum_sel32<EXACT>(a.other, at[u], x_nbr(e[u], at[u]), P, Z);
         b[u] = SCALED ? a.rhsd[at[u]] : a.rhs[at[u]];
       }
     }
@@ -147,6 +145,7 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
   const uint32_t group = ((blockIdx.x * kListBlock + threadIdx.x) >> 5) * GROUPS + (lane >> SHIFT);
   const uint32_t ngroups = (gridDim.x * kListBlock >> 5) * GROUPS;
   const uint32_t step = PER * ngroups;
+  const uint32_t P = (uint32_t)a.g.P, Z = (uint32_t)a.g.sz;
   uint32_t next[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
@@ -164,19 +163,19 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
       const uint32_t i = base + step + u * ngroups;
       next[u] = i < n ? a.list[i] : 0u;
     }
-    long long at[PER];
+    uint32_t at[PER];
     T s[PER], b[PER], d[PER];
     bool ok[PER], act[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const uint32_t e = cur[u];
-      at[u] = (long long)(e & kListAt);
+      at[u] = e & kListAt;
       ok[u] = base + u * ngroups < n && entry_ok(a.g, at[u], 9);
-      at[u] += l;
+      at[u] += (uint32_t)l;
       if (ok[u]) {
         const uint8_t code = a.code[at[u]];
         act[u] = (code & kActive2) != 0;
-        s[u] = nbr_sum(a.other, at[u], (e & kListPlusX) ? 1 : -1, a.g.P, a.g.sz);
+        s[u] = nbr_sum32(a.other, at[u], x_nbr(e, at[u]), P, Z);
         b[u] = a.rhs[at[u]];
         d[u] = tab[__popc((unsigned)code >> kGhostShift)];
       }
