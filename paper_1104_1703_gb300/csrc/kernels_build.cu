@@ -53,28 +53,46 @@ __device__ void block_count_add(unsigned long long* ctr, unsigned n) {
 }
 
 // Level 0: code byte (active bits and ghost-face flags) from the int8 mask,
-// and the active-cell count.
+// and the active-cell count.  A warp takes one row (j, k) at a time, 32
+// cells per round (no division per cell); the x-neighbours come from the
+// adjacent lanes (the round's two edge cells load theirs), and only active
+// cells load their y- and z-neighbours.
 __global__ void build_fine_kernel(LevelDev L, const int8_t* __restrict__ mask, unsigned long long* counts2) {
   const Geom g = L.g;
-  const long long n = g.ncells();
+  const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
+  const int lane = threadIdx.x & 31;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   unsigned n_act = 0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    natural_coords(idx, g.nx, g.ny, i, j, k);
-    const bool act = mask[idx] > 0;
-    n_act += act;
-    uint8_t code = 0;
-    if (act) {
-      code = kActive2 | kActive1;
-      const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-      bool nb[6] = {i > 0 && mask[idx - 1] > 0, i + 1 < g.nx && mask[idx + 1] > 0,
-                    j > 0 && mask[idx - sy] > 0, j + 1 < g.ny && mask[idx + sy] > 0,
-                    k > 0 && mask[idx - sz] > 0, k + 1 < g.nz && mask[idx + sz] > 0};
-      for (int d = 0; d < 6; ++d)
-        if (!nb[d]) code |= (uint8_t)(1u << (kGhostShift + d));
+  for (unsigned row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nw) {
+    const int k = (int)(row / (unsigned)g.ny);
+    const int j = (int)(row - (unsigned)k * (unsigned)g.ny);
+    const int8_t* __restrict__ m = mask + (long long)row * g.nx;
+    // even i has colour (j + k) & 1
+    uint8_t* const even = L.code[(j + k) & 1] + g.at(0, j, k);
+    uint8_t* const odd = L.code[(j + k + 1) & 1] + g.at(0, j, k);
+    const bool ylo = j > 0, yhi = j + 1 < g.ny, zlo = k > 0, zhi = k + 1 < g.nz;
+    for (int i0 = 0; i0 < g.nx; i0 += 32) {
+      const int i = i0 + lane;
+      const bool in = i < g.nx;
+      const int c = in ? (int)m[i] : 0;
+      const bool act = c > 0;
+      int xm = __shfl_up_sync(0xffffffffu, c, 1);
+      int xp = __shfl_down_sync(0xffffffffu, c, 1);
+      if (lane == 0) xm = i > 0 && in ? (int)m[i - 1] : 0;
+      if (lane == 31) xp = i + 1 < g.nx ? (int)m[i + 1] : 0;
+      uint8_t code = 0;
+      if (act) {
+        const bool nb[6] = {xm > 0, i + 1 < g.nx && xp > 0, ylo && m[i - sy] > 0, yhi && m[i + sy] > 0,
+                            zlo && m[i - sz] > 0, zhi && m[i + sz] > 0};
+        code = kActive2 | kActive1;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+          if (!nb[d]) code |= (uint8_t)(1u << (kGhostShift + d));
+      }
+      n_act += act;
+      if (in) ((i & 1) ? odd : even)[i >> 1] = code;
     }
-    L.code[colour_of(i, j, k)][g.at(i >> 1, j, k)] = code;
   }
   block_count_add(&counts2[0], n_act);
 }
@@ -335,26 +353,47 @@ __global__ void combine_rhs_kernel(long long total, const double* __restrict__ r
   }
 }
 
-// Stream compaction of the active cells of one colour, in slot order
-// (k, j, q), in three passes: per-block counts, one-block exclusive scan,
-// per-block ordered writes.  Slot e = (k*ny + j)*hx + q.
+// Stream compaction of the active cells (or row segments) of one colour, in
+// slot order (k, j, q), in three passes: per-block counts, one-block
+// exclusive scan, per-block ordered writes.  A thread scans one 16-slot chunk
+// of a row.
 constexpr int kListThreads = 256;
 
-__device__ __forceinline__ bool list_member(const Geom& g, const uint8_t* code, uint8_t bit, int seg_shift,
-                                            long long e, long long n, long long& at, int& j, int& k) {
-  if (e >= n) return false;
-  const unsigned u = (unsigned)e;  // slots per colour < 2^31
-  const unsigned per_row = seg_shift ? (unsigned)((g.hx + (1 << seg_shift) - 1) >> seg_shift) : (unsigned)g.hx;
-  const unsigned t = u / per_row;
-  const int q = (int)(u - t * per_row) << seg_shift;
-  k = (int)(t / (unsigned)g.ny);
-  j = (int)(t - (unsigned)k * (unsigned)g.ny);
-  at = g.at(q, j, k);
-  if (!seg_shift) return (code[at] & bit) != 0;
-  const int nv = min(1 << seg_shift, g.hx - q);
-  bool any = false;
-  for (int l = 0; l < nv; ++l) any = any || (code[at + l] & bit) != 0;
-  return any;
+// Chunk x of a list job: the 16 slots (q0 .. q0 + 15) of one row of one
+// colour, x = row * chunks_per_row + q0 / 16, rows in (k, j) order.  Returns
+// the membership bits of the chunk's candidates (bit c: cell q0 + c, or row
+// segment c of 2^seg_shift slots, holds a slot whose code has `bit`), with the
+// offset of slot q0 and the x-neighbour flag of the row.  Slots at q >= hx
+// are masked off whatever the padding holds.
+__device__ __forceinline__ unsigned list_chunk(const ListJob& J, unsigned x, long long& at0, uint32_t& flag) {
+  const Geom& g = J.g;
+  const unsigned per_row = (unsigned)(g.hx + (1 << kListChunkShift) - 1) >> kListChunkShift;
+  const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
+  if (x >= per_row * rows) return 0u;
+  const unsigned row = x / per_row;
+  const int q0 = (int)(x - row * per_row) << kListChunkShift;
+  const int k = (int)(row / (unsigned)g.ny);
+  const int j = (int)(row - (unsigned)k * (unsigned)g.ny);
+  at0 = g.at(q0, j, k);
+  flag = ((J.colour ^ j ^ k) & 1) ? kListPlusX : 0u;
+  const uint4 w = *reinterpret_cast<const uint4*>(J.code + at0);
+  const int p = J.bit == 1 ? 0 : (J.bit == 2 ? 1 : 31 - __clz((int)J.bit));
+  const unsigned word[4] = {w.x, w.y, w.z, w.w};
+  unsigned slots = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned y = (word[i] >> p) & 0x01010101u;  // byte b: 1 if slot 4i + b has the bit
+    slots |= ((y & 1u) | ((y >> 7) & 2u) | ((y >> 14) & 4u) | ((y >> 21) & 8u)) << (4 * i);
+  }
+  const int nv = g.hx - q0;  // slots of this row in the chunk (>= 1)
+  if (nv < 16) slots &= (1u << nv) - 1u;
+  const int sh = J.seg_shift;
+  if (sh == 0) return slots;
+  unsigned m = 0;
+  const int per = 1 << sh;
+  for (int c = 0; c < (16 >> sh); ++c)
+    if ((slots >> (c * per)) & ((1u << per) - 1u)) m |= 1u << c;
+  return m;
 }
 
 // exclusive scan of nb block counts in place (one block of 1024 threads);
@@ -382,35 +421,6 @@ __device__ void list_scan_block(uint32_t* block_counts, int nb, uint32_t* count)
   if (threadIdx.x == 1023) *count = part[1023];
 }
 
-// ordered writes of the members of local block `lb` of a list, from the
-// block's offset in it
-__device__ void list_write_block(const Geom& g, const uint8_t* __restrict__ code, int colour, uint8_t bit,
-                                 int seg_shift, uint32_t block_offset, unsigned lb, uint32_t* list) {
-  __shared__ uint32_t warp_base[kListThreads / 32];
-  const long long n = list_job_slots(g, seg_shift);
-  const long long e = (long long)lb * kListThreads + threadIdx.x;
-  long long at = 0;
-  int j = 0, k = 0;
-  const bool m = list_member(g, code, bit, seg_shift, e, n, at, j, k);
-  const unsigned bal = __ballot_sync(0xffffffffu, m);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) warp_base[w] = __popc(bal);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kListThreads / 32; ++i) {
-      const uint32_t c = warp_base[i];
-      warp_base[i] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  if (m) {
-    const uint32_t pos = block_offset + warp_base[w] + __popc(bal & ((1u << lane) - 1u));
-    list[pos] = (uint32_t)at | (((colour ^ j ^ k) & 1) ? kListPlusX : 0u);
-  }
-}
-
 // All the lists of a hierarchy in three launches: the same three passes,
 // with every block of a launch belonging to one list (a job) of the table.
 // Job b0 is the first global block of the job; the scratch holds one count
@@ -428,17 +438,21 @@ __device__ int find_job(const ListJob* jobs, int njobs, unsigned b) {
 __global__ void __launch_bounds__(kListThreads) list_count_all_kernel(const ListJob* __restrict__ jobs, int njobs,
                                                                       uint32_t* scratch) {
   __shared__ int js;
+  __shared__ unsigned warp_n[kListThreads / 32];
   if (threadIdx.x == 0) js = find_job(jobs, njobs, blockIdx.x);
   __syncthreads();
   const ListJob& J = jobs[js];
-  const Geom g = J.g;
-  const long long n = list_job_slots(g, J.seg_shift);
-  const long long e = (long long)(blockIdx.x - J.block0) * kListThreads + threadIdx.x;
-  long long at;
-  int j, k;
-  const bool m = list_member(g, J.code, J.bit, J.seg_shift, e, n, at, j, k);
-  const int cnt = __syncthreads_count(m);
-  if (threadIdx.x == 0) scratch[blockIdx.x] = (uint32_t)cnt;
+  long long at0 = 0;
+  uint32_t flag = 0;
+  unsigned n = __popc(list_chunk(J, (blockIdx.x - J.block0) * kListThreads + threadIdx.x, at0, flag));
+  for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+  if ((threadIdx.x & 31) == 0) warp_n[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < kListThreads / 32; ++w) t += warp_n[w];
+    scratch[blockIdx.x] = t;
+  }
 }
 
 // one block per job: exclusive scan of the job's block counts in place; the
@@ -448,13 +462,50 @@ __global__ void __launch_bounds__(1024) list_scan_all_kernel(const ListJob* __re
   list_scan_block(scratch + J.block0, (int)J.nblocks, J.count);
 }
 
+// The block's entries in slot order: each thread places its chunk's members
+// at its exclusive prefix in shared memory, then the block writes them out
+// contiguously from the block's offset in the list.
 __global__ void __launch_bounds__(kListThreads) list_write_all_kernel(const ListJob* __restrict__ jobs, int njobs,
                                                                       const uint32_t* __restrict__ scratch) {
   __shared__ int js;
+  __shared__ unsigned warp_base[kListThreads / 32 + 1];
+  __shared__ uint32_t stage[kListThreads << kListChunkShift];
   if (threadIdx.x == 0) js = find_job(jobs, njobs, blockIdx.x);
   __syncthreads();
   const ListJob& J = jobs[js];
-  list_write_block(J.g, J.code, J.colour, J.bit, J.seg_shift, scratch[blockIdx.x], blockIdx.x - J.block0, J.list);
+  long long at0 = 0;
+  uint32_t flag = 0;
+  unsigned m = list_chunk(J, (blockIdx.x - J.block0) * kListThreads + threadIdx.x, at0, flag);
+  const unsigned cnt = __popc(m);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned incl = cnt;
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) warp_base[w] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int i = 0; i < kListThreads / 32; ++i) {
+      const unsigned c = warp_base[i];
+      warp_base[i] = run;
+      run += c;
+    }
+    warp_base[kListThreads / 32] = run;
+  }
+  __syncthreads();
+  unsigned pos = warp_base[w] + incl - cnt;
+  const int sh = J.seg_shift;
+  while (m) {
+    const int c = __ffs((int)m) - 1;
+    m &= m - 1u;
+    stage[pos++] = (uint32_t)(at0 + (c << sh)) | flag;
+  }
+  __syncthreads();
+  const unsigned total = warp_base[kListThreads / 32];
+  uint32_t* out = J.list + scratch[blockIdx.x];
+  for (unsigned i = threadIdx.x; i < total; i += kListThreads) out[i] = stage[i];
 }
 
 // Many device buffers zeroed, or converted FP64 -> FP32, in one launch:

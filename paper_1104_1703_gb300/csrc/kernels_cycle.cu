@@ -547,19 +547,46 @@ struct NormArgs {
   double* partials;
 };
 
-// sum of b^2 over the active cells (the residual of Phi = 0 is -b)
+// sum of b^2 over the active cells (the residual of Phi = 0 is -b).  A
+// thread takes 16-slot chunks of the colours' rows (rows are padded to a
+// multiple of 16 slots): one 16-byte load of the codes, then the right-hand
+// side of the chunk's active slots in pairs, summed in slot order.
 __global__ void __launch_bounds__(kNormThreads) rhsnorm_kernel(NormArgs a) {
   pdl_wait();
   const Geom g = a.g;
-  const long long per_colour = (long long)g.hx * g.ny * g.nz;
+  const unsigned per_row = (unsigned)(g.hx + 15) >> 4;
+  const unsigned nch = per_row * (unsigned)g.ny * (unsigned)g.nz;  // chunks per colour
+  const int p = a.bit == 1 ? 0 : (a.bit == 2 ? 1 : 31 - __clz((int)a.bit));
   double acc = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * per_colour;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = e >= per_colour;
-    const long long r = e - c * per_colour;
-    const unsigned u = (unsigned)r, t = u / (unsigned)g.hx, k = t / (unsigned)g.ny;
-    const long long at = g.at((int)(u - t * (unsigned)g.hx), (int)(t - k * (unsigned)g.ny), (int)k);
-    if (a.code[c][at] & a.bit) acc = fma(a.rhs[c][at], a.rhs[c][at], acc);
+  for (unsigned x = blockIdx.x * blockDim.x + threadIdx.x; x < 2 * nch; x += gridDim.x * blockDim.x) {
+    const int c = x >= nch;
+    const unsigned y = x - (c ? nch : 0u);
+    const unsigned row = y / per_row;
+    const int q0 = (int)(y - row * per_row) << 4;
+    const int k = (int)(row / (unsigned)g.ny);
+    const int j = (int)(row - (unsigned)k * (unsigned)g.ny);
+    const long long at0 = g.at(q0, j, k);
+    const uint4 w = *reinterpret_cast<const uint4*>((c ? a.code[1] : a.code[0]) + at0);
+    const unsigned word[4] = {w.x, w.y, w.z, w.w};
+    unsigned bits = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned v = (word[i] >> p) & 0x01010101u;
+      bits |= ((v & 1u) | ((v >> 7) & 2u) | ((v >> 14) & 4u) | ((v >> 21) & 8u)) << (4 * i);
+    }
+    const int nv = g.hx - q0;
+    if (nv < 16) bits &= (1u << nv) - 1u;
+    if (!bits) continue;
+    const double2* r2 = reinterpret_cast<const double2*>((c ? a.rhs[1] : a.rhs[0]) + at0);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const unsigned pb = (bits >> (2 * h)) & 3u;
+      if (pb) {
+        const double2 v = r2[h];
+        if (pb & 1u) acc = fma(v.x, v.x, acc);
+        if (pb & 2u) acc = fma(v.y, v.y, acc);
+      }
+    }
   }
   block_reduce_store(acc, a.partials + blockIdx.x);
 }
@@ -1105,15 +1132,24 @@ struct CoarseMatArgs {
   T* out;
 };
 
+template <typename T>
+struct CoarseMatSmem {
+  int8_t map[2][kCmMaxSlots];
+  int8_t nbr[2][kCoarseMatMax][6];
+  T id[2][kCoarseMatMax];
+  T xs[kCmWarps][2][kCoarseMatMax];
+};
+
 template <int KIND, typename T>
-__global__ void __launch_bounds__(kCmWarps * 32) coarse_matrix_kernel(CoarseMatArgs<T> a) {
-  __shared__ int8_t map[2][kCmMaxSlots];
-  __shared__ int8_t nbr[2][kCoarseMatMax][6];
-  __shared__ T id[2][kCoarseMatMax];
-  __shared__ T xs[kCmWarps][2][kCoarseMatMax];
+__device__ void coarse_matrix_body(const CoarseMatArgs<T>& a, CoarseMatSmem<T>& sm) {
+  auto& map = sm.map;
+  auto& nbr = sm.nbr;
+  auto& id = sm.id;
+  auto& xs = sm.xs;
   const Geom& g = a.g;
   const uint32_t nr = a.n[0], nb = a.n[1], nt = nr + nb, ncol = nt + nb;
   if (g.total > kCmMaxSlots || nt > (uint32_t)kCoarseMatMax) return;
+  if (blockIdx.x * kCmWarps >= ncol) return;  // the other order's map needs more CTAs
   for (long long e = threadIdx.x; e < 2 * g.total; e += blockDim.x) map[e >= g.total][e % g.total] = -1;
   __syncthreads();
   for (uint32_t e = threadIdx.x; e < nt; e += blockDim.x) {
@@ -1158,6 +1194,16 @@ __global__ void __launch_bounds__(kCmWarps * 32) coarse_matrix_kernel(CoarseMatA
       __syncwarp();
     }
   for (uint32_t i = lane; i < nt; i += 32) a.out[(size_t)i * ncol + j] = i < nr ? x[0][i] : x[1][i - nr];
+}
+
+// Both orders' maps in one launch: blockIdx.y = 0 builds order 1's (the
+// first-order operator, D = 6), 1 order 2's; an order with no map has no
+// columns.
+template <typename T>
+__global__ void __launch_bounds__(kCmWarps * 32) coarse_matrix_kernel(CoarseMatArgs<T> a1, CoarseMatArgs<T> a2) {
+  __shared__ CoarseMatSmem<T> sm;
+  if (blockIdx.y == 0) coarse_matrix_body<2, T>(a1, sm);
+  else coarse_matrix_body<1, T>(a2, sm);
 }
 
 // b / D of the level-0 unknowns (D = 6 + ghost faces), for SCALED sweeps;
@@ -1369,29 +1415,37 @@ size_t coarse_map_bytes(int prec) {
 }
 
 template <typename T>
-cudaError_t coarse_map_t(const LevelDev& L, int order, int sweeps, T* out, cudaStream_t s) {
-  const Fields<T> f = fields(L, T());
-  CoarseMatArgs<T> a;
-  a.g = L.g;
-  for (int c = 0; c < 2; ++c) {
-    a.list[c] = L.list[order][c];
-    a.invd[c] = f.invd[c];
-    a.n[c] = L.hcount[order * 2 + c];
-  }
+CoarseMatArgs<T> coarse_map_args(const LevelDev* L, int order, int sweeps, T* out) {
+  CoarseMatArgs<T> a = {};
   a.sweeps = sweeps;
   a.out = out;
-  const uint32_t ncol = a.n[0] + 2 * a.n[1];
-  const unsigned grid = (ncol + kCmWarps - 1) / kCmWarps;
+  if (!L) return a;  // no map for this order: no columns
+  const Fields<T> f = fields(*L, T());
+  a.g = L->g;
+  for (int c = 0; c < 2; ++c) {
+    a.list[c] = L->list[order][c];
+    a.invd[c] = f.invd[c];
+    a.n[c] = L->hcount[order * 2 + c];
+  }
+  return a;
+}
+
+template <typename T>
+cudaError_t coarse_maps_t(const LevelDev* L1, const LevelDev* L2, int sweeps, T* out1, T* out2, cudaStream_t s) {
+  const CoarseMatArgs<T> a1 = coarse_map_args(L1, 1, sweeps, out1), a2 = coarse_map_args(L2, 2, sweeps, out2);
+  const uint32_t n1 = a1.n[0] + 2 * a1.n[1], n2 = a2.n[0] + 2 * a2.n[1];
+  const unsigned grid = ((n1 > n2 ? n1 : n2) + kCmWarps - 1) / kCmWarps;
   if (grid == 0) return cudaSuccess;
   count_launch();
-  if (order == 1) coarse_matrix_kernel<2, T><<<grid, kCmWarps * 32, 0, s>>>(a);
-  else coarse_matrix_kernel<1, T><<<grid, kCmWarps * 32, 0, s>>>(a);
+  coarse_matrix_kernel<T><<<dim3(grid, 2), kCmWarps * 32, 0, s>>>(a1, a2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_map(const LevelDev& L, int order, int sweeps, int prec, void* out, cudaStream_t s) {
-  return prec == kFP32 ? coarse_map_t<float>(L, order, sweeps, static_cast<float*>(out), s)
-                       : coarse_map_t<double>(L, order, sweeps, static_cast<double*>(out), s);
+cudaError_t launch_coarse_maps(const LevelDev* L1, const LevelDev* L2, int sweeps, int prec, void* out1, void* out2,
+                               cudaStream_t s) {
+  return prec == kFP32 ? coarse_maps_t<float>(L1, L2, sweeps, static_cast<float*>(out1), static_cast<float*>(out2), s)
+                       : coarse_maps_t<double>(L1, L2, sweeps, static_cast<double*>(out1),
+                                               static_cast<double*>(out2), s);
 }
 
 bool mid_level(const Geom& g) { return (long long)g.hx * g.ny * g.nz <= kMidSlots; }

@@ -556,16 +556,20 @@ mg_status zero_split(mg_hierarchy* H, const Geom& g, double* const* a) {
 
 // Hierarchy build (mask sums, codes, diagonals, counts) from H->mask_dev.
 // fine_built: level 0's codes and counts were already built from that mask.
-mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
+// Level 0's codes (unless fine_built: already built from `mask`), the coarse
+// levels, the lists and the coarsest maps from `mask` (the hierarchy's own
+// when null); one host synchronisation, for the counts.
+mg_status build_levels(mg_hierarchy* H, bool fine_built = false, const int8_t* mask = nullptr) {
   cudaStream_t s = H->stream;
+  if (!mask) mask = H->mask_dev;
   if (!fine_built) {
     CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2 * kMaxLevels, s));
-    CKS(launch_ok(H, launch_build_fine(H->L[0], H->mask_dev, H->counts, s), "fine build"));
+    CKS(launch_ok(H, launch_build_fine(H->L[0], mask, H->counts, s), "fine build"));
   } else {
     CK(H, cudaMemsetAsync(H->counts + 2, 0, sizeof(unsigned long long) * 2 * (kMaxLevels - 1), s));
   }
   for (int l = 0; l + 1 < H->nlev; ++l) {
-    CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? H->mask_dev : nullptr, H->L[l + 1], s), "mask R1"));
+    CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? mask : nullptr, H->L[l + 1], s), "mask R1"));
     CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
   }
   // FP32 copies of the coarse diagonals for the mixed form (one launch)
@@ -591,17 +595,21 @@ mg_status build_levels(mg_hierarchy* H, bool fine_built = false) {
     H->deepest[o] = -1;
     for (int l = 0; l < H->nlev && H->active[o][l] > 0; ++l) H->deepest[o] = l;
   }
-  // the coarsest solve's map of each order, for the W-cycle's bottom
+  // the coarsest solve's map of each order, for the bottom cycle (one launch)
+  const LevelDev* mapped[3] = {nullptr, nullptr, nullptr};
   for (int o = 1; o <= 2; ++o) {
     H->cmat_ok[o] = false;
     const int d = H->deepest[o];
     if (!H->cmat[o] || d < 1 || !small_level(H->L[d].g) || !coarse_map_fits(H->L[d], o)) continue;
-    CKS(launch_ok(H, launch_coarse_map(H->L[d], o, H->opt.coarse_sweeps, H->cmat_prec, H->cmat[o], s),
-                  "coarsest-solve map"));
+    mapped[o] = &H->L[d];
     H->cmat_n[o][0] = H->L[d].hcount[o * 2];
     H->cmat_n[o][1] = H->L[d].hcount[o * 2 + 1];
     H->cmat_ok[o] = true;
   }
+  if (mapped[1] || mapped[2])
+    CKS(launch_ok(H, launch_coarse_maps(mapped[1], mapped[2], H->opt.coarse_sweeps, H->cmat_prec, H->cmat[1], H->cmat[2],
+                                        s),
+                  "coarsest-solve maps"));
   return MG_OK;
 }
 
@@ -821,7 +829,7 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
         ListJob j = {};
         j.g = g;
         j.seg_shift = o == 0 ? seg_shift : 0;
-        const unsigned nb = (unsigned)((list_job_slots(g, j.seg_shift) + 255) / 256);
+        const unsigned nb = (unsigned)((list_job_chunks(g) + 255) / 256);  // one chunk per thread
         j.block0 = lblocks;
         j.nblocks = nb;
         j.colour = c;
@@ -1016,17 +1024,14 @@ mg_status mg_update_mask(mg_hierarchy* H, const int8_t* mask, mg_mem where) {
   CKS(ensure_staging(H, g0.ncells()));
   CK(H, cudaMemcpyAsync(H->staging, mask, g0.ncells(),
                         where == MG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, H->stream));
-  CK(H, cudaMemsetAsync(H->counts, 0, sizeof(unsigned long long) * 2, H->stream));
-  CKS(launch_ok(H, launch_build_fine(H->L[0], (const int8_t*)H->staging, H->counts, H->stream), "fine build"));
-  unsigned long long n_act = 0;
-  CK(H, cudaMemcpyAsync(&n_act, H->counts, sizeof(n_act), cudaMemcpyDeviceToHost, H->stream));
-  CK(H, cudaStreamSynchronize(H->stream));
-  if (n_act == 0) {
-    CKS(build_levels(H));  // restore the level-0 codes of the old mask
+  // the whole hierarchy is built from the copy; the old mask stays in force
+  // (and is rebuilt) if the new one has no active cell
+  CKS(build_levels(H, false, (const int8_t*)H->staging));
+  if (H->active[2][0] == 0) {
+    CKS(build_levels(H));
     return fail(H, MG_ERR_EMPTY_DOMAIN, "the mask has no active cell");
   }
   CK(H, cudaMemcpyAsync(H->mask_dev, H->staging, g0.ncells(), cudaMemcpyDeviceToDevice, H->stream));
-  CKS(build_levels(H, true));  // level 0 was just built from the same mask
   return reset_fields(H);
 }
 

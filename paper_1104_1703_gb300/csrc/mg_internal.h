@@ -183,6 +183,14 @@ __host__ __device__ inline long long list_job_slots(const Geom& g, int seg_shift
   const long long per_row = seg_shift ? (g.hx + (1 << seg_shift) - 1) >> seg_shift : g.hx;
   return per_row * g.ny * g.nz;
 }
+// The list build scans a level's rows in chunks of 16 slots, one chunk per
+// thread (one 16-byte load of the codes; rows are padded to a multiple of 16
+// slots), so a chunk holds 16 cell candidates or 16 >> seg_shift segments.
+constexpr int kListChunkShift = 4;
+static_assert(kSegShiftMax <= kListChunkShift, "a row segment must fit in one list-build chunk");
+__host__ __device__ inline long long list_job_chunks(const Geom& g) {
+  return (long long)((g.hx + (1 << kListChunkShift) - 1) >> kListChunkShift) * g.ny * g.nz;
+}
 cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_blocks, uint32_t* scratch,
                                cudaStream_t s);
 // Buffers of `words` 8-byte words to zero, and FP64 -> FP32 copies, many
@@ -250,15 +258,17 @@ cudaError_t launch_residual_norm2(const LevelDev& L0, bool red_only, bool with_p
 // 2 or more: W) on levels lb .. deepest in one CTA, for small levels (every
 // level lb..deepest satisfies small_level); lb >= 1.
 // cmat / cmat_n (nullable): the coarsest solve's precomputed map and its
-// red and black unknown counts (launch_coarse_map builds it)
+// red and black unknown counts (launch_coarse_maps builds it)
 cudaError_t launch_bottom(const LevelDev* levels, int lb, int deepest, int order, int n_pre, int n_post,
                           int coarse_sweeps, int n_cycles, int prec, const void* cmat, const uint32_t* cmat_n,
                           cudaStream_t s);
 // The coarsest solve of level L (order) as a map, for the bottom cycle:
-// whether it fits, the bytes of one map, and its build (one launch).
+// whether it fits, the bytes of one map, and the build of both orders' maps
+// in one launch (L1 / L2: the deepest level of order 1 / 2, null for no map).
 bool coarse_map_fits(const LevelDev& L, int order);
 size_t coarse_map_bytes(int prec);
-cudaError_t launch_coarse_map(const LevelDev& L, int order, int sweeps, int prec, void* out, cudaStream_t s);
+cudaError_t launch_coarse_maps(const LevelDev* L1, const LevelDev* L2, int sweeps, int prec, void* out1, void* out2,
+                               cudaStream_t s);
 int residual_norm_blocks(const Geom& g);
 // Middle levels (more than 4096, at most kMidSlots cells per colour): the
 // V-cycle from level m (1 <= m < lb) through levels m .. lb-1, and the bottom
