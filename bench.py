@@ -319,7 +319,8 @@ class Form:
         self.pass_on = precision == 1 and self.H.smoother_pass
         d = B.mg_default_options()
         # FP32 level-0 sweeps over row segments; FP64 ones with the integer neighbour sum
-        self.seg_on = precision == 1 and not self.pass_on and int(extra.get("fine_segments", d.fine_segments)) >= 1
+        seg = int(extra.get("fine_segments", d.fine_segments))
+        self.seg_on = seg if (precision == 1 and not self.pass_on) else 0  # 0: cell lists
         self.exact_on = precision == 0 and int(extra.get("fp64_sum", d.fp64_sum)) == 1
         self.kinds = (self.pass_on, self.seg_on, self.exact_on)
 
@@ -450,11 +451,17 @@ def roofline(st, n_active, precision, peaks, fp64_rate=None, pass_on=False, seg_
                 "traffic": profiled_traffic("smooth_pass_fp32_level0_sphere_union_256.md"),
                 "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
     ach = 13.0 * half / gs_s / 1e9
-    if seg_on:
-        return {"bound": "hbm", "kernel": "gs_seg_kernel<float> (level-0 red/black Gauss-Seidel over 8-slot row "
-                                          "segments, FP32 inner cycle)",
+    if seg_on == 3:
+        return {"bound": "hbm", "kernel": "gs_seg_pair_kernel (level-0 red/black Gauss-Seidel over 16-slot row "
+                                          "segments, two slots per thread, FP32 inner cycle)",
                 "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": profiled_traffic("gs_seg_fp32_level0_sphere_union_256.md"),
+                "traffic": profiled_traffic("gs_seg_pair_fp32_level0_sphere_union_256.md"),
+                "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
+    if seg_on:
+        return {"bound": "hbm", "kernel": "gs_seg_kernel<float> (level-0 red/black Gauss-Seidel over %d-slot row "
+                                          "segments, FP32 inner cycle)" % (8 if seg_on == 1 else 16),
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": profiled_traffic("gs_seg_fp32_level0_sphere_union_256.md") if seg_on == 1 else None,
                 "launches": st["gs_n"], "avg_launch_us": gs_s * 1e6, "peak_source": src}
     return {"bound": "hbm", "kernel": "gs_list_kernel<0,float> (level-0 red/black Gauss-Seidel, FP32 inner cycle)",
             "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,

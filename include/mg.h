@@ -109,10 +109,11 @@ typedef enum { MG_MEM_HOST = 0, MG_MEM_DEVICE = 1 } mg_mem;
  *  fine_segments   mixed form, level-0 FP32 Gauss-Seidel sweeps: 1, 2 = one
  *                  thread per slot of the row segments (8, 16 slots of one
  *                  colour's half-row) that hold an active cell, so that a
- *                  warp reads whole runs of every array; 0 = one thread per
- *                  active cell of the colour's compact list.  The results
- *                  are bit-identical.  (The FP64 sweeps always use the cell
- *                  lists.)
+ *                  warp reads whole runs of every array; 3 = 16-slot
+ *                  segments with two consecutive slots per thread (8-byte
+ *                  loads); 0 = one thread per active cell of the colour's
+ *                  compact list.  The results are bit-identical.  (The FP64
+ *                  sweeps always use the cell lists.)
  *  coarse_matrix   1 = solve the coarsest level, when it has at most 64
  *                  unknowns and runs inside the one-CTA bottom cycle, through
  *                  the precomputed affine map of its coarse_sweeps red-black
@@ -154,7 +155,7 @@ typedef struct {
 /* Fills *opt with the paper's parameters: n_pre = n_post = 2, n_cycles = 1,
  * coarse_sweeps = 50, hold_solves = 10, eta = 0.5, order = 0, use_graphs = 1,
  * precision = 0 (FP64), inner_cycles = 1, coarse_cluster = 0, smoother_pass = 0,
- * fp64_sum = 1, fine_segments = 1, coarse_matrix = 1. */
+ * fp64_sum = 1, fine_segments = 3, coarse_matrix = 1. */
 void mg_default_options(mg_options* opt);
 
 /* Builds the multigrid hierarchy of one AMR level (Section 2, Fig. 2):

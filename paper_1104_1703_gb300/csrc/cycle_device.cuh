@@ -181,7 +181,8 @@ __device__ __forceinline__ int x_offset(int c, int j, int k) { return ((c ^ j ^ 
 // away; divide by 64 for the correction).  The corners are addressed from
 // one coarse row base with 32-bit offsets: a step along y or z moves by the
 // pitch or the plane stride, and every axis step flips the colour.  `ld`
-// loads one coarse value.  Out-of-box corners read the zero halo.
+// loads one coarse value.  Out-of-box corners read the zero halo (the one
+// corner that has no halo slot is taken as 0).
 struct PlainLoad {
   template <typename T>
   __device__ __forceinline__ T operator()(const T* p) const {
@@ -204,7 +205,11 @@ __device__ __forceinline__ T p2_sum(const Geom& gc, const T* c0, const T* c1, in
   const T e0 = ld(cp + sn);
   const T e1 = (ld(cq + sf) + ld(cq + sn + dY)) + ld(cq + sn + dZ);
   const T e2 = (ld(cp + sn + dY + dZ) + ld(cp + sf + dZ)) + ld(cp + sf + dY);
-  const T e3 = ld(cq + sf + dY + dZ);
+  // the corner three steps away of fine cell (0, 0, 0) is coarse cell
+  // (-1, -1, -1), outside the box and, alone of all corners, before the first
+  // element of its colour array (offset -1): it holds 0 and is not read
+  const int i3 = sf + dY + dZ;
+  const T e3 = i3 >= 0 ? ld(cq + i3) : T(0);
   return fma(T(3), e2, fma(T(27), e0, T(9) * e1)) + e3;
 }
 

@@ -58,8 +58,6 @@ struct mg_hierarchy {
   unsigned list_blocks = 0;
   gbmg::ZeroJob* zero_jobs = nullptr;
   int n_zero_jobs = 0;
-  gbmg::F32Job* f32_jobs = nullptr;
-  int n_f32_jobs = 0;
   bool bc_zero = true;  // the folded boundary terms are all 0
   bool rhsd_valid = false;  // level 0's b / D matches its b
   // the coarsest solve's precomputed map per order (option coarse_matrix):

@@ -157,6 +157,10 @@ __global__ void coarse_coeffs_kernel(LevelDev L, unsigned long long* counts2) {
       L.code[c][at] = code;
       L.invd[c][at] = invd;
       L.diag[c][at] = diag;
+      if (L.invd32[0]) {  // the mixed form's FP32 copies (round to nearest)
+        L.invd32[c][at] = (float)invd;
+        L.diag32[c][at] = (float)diag;
+      }
     }
     n2 += a2;
     n1 += a1;
@@ -508,19 +512,12 @@ __global__ void __launch_bounds__(kListThreads) list_write_all_kernel(const List
   for (unsigned i = threadIdx.x; i < total; i += kListThreads) out[i] = stage[i];
 }
 
-// Many device buffers zeroed, or converted FP64 -> FP32, in one launch:
-// blockIdx.y selects the buffer.
+// Many device buffers zeroed in one launch: blockIdx.y selects the buffer.
 __global__ void zero_many_kernel(const ZeroJob* __restrict__ jobs) {
   const ZeroJob J = jobs[blockIdx.y];
   unsigned long long* p = (unsigned long long*)J.ptr;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.words; e += (long long)gridDim.x * blockDim.x)
     p[e] = 0ull;
-}
-
-__global__ void to_f32_many_kernel(const F32Job* __restrict__ jobs) {
-  const F32Job J = jobs[blockIdx.y];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < J.n; e += (long long)gridDim.x * blockDim.x)
-    J.dst[e] = (float)J.src[e];
 }
 
 int grid_for(long long n) {
@@ -567,13 +564,6 @@ cudaError_t launch_zero_many(const ZeroJob* jobs, int njobs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   count_launch();
   zero_many_kernel<<<dim3(device_sms() * 2, njobs), 256, 0, s>>>(jobs);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_to_f32_many(const F32Job* jobs, int njobs, cudaStream_t s) {
-  if (njobs <= 0) return cudaSuccess;
-  count_launch();
-  to_f32_many_kernel<<<dim3(device_sms() * 2, njobs), 256, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

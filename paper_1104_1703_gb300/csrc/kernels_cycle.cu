@@ -190,6 +190,90 @@ __global__ void __launch_bounds__(kListBlock) gs_seg_kernel(ListArgs<T> a) {
   }
 }
 
+// The same sweep over 16-slot row segments with two consecutive slots per
+// lane (8-byte loads and stores): lane l of a group of 8 takes slots
+// q0 + 2l and q0 + 2l + 1.  The x-neighbour that is not in the lane's own
+// pair is the adjacent lane's (a shuffle within the group) or, for the
+// group's first or last lane, one extra load.  Per cell the sum and the
+// update are gs_list_kernel's, in the same order, so the results are
+// bit-identical.  Groups of a warp run their rounds together (the shuffles
+// need every lane); a group without a segment works on slot (0, 0, 0) of the
+// level, whose stencil lies inside the arrays, and stores nothing.
+template <bool UPDATE>
+__global__ void __launch_bounds__(kListBlock) gs_seg_pair_kernel(ListArgs<float> a) {
+  constexpr int PER = 1;  // two slots per lane already
+  constexpr int GROUPS = 4;  // segments per warp and round
+  __shared__ float tab[16];
+  init_tab(tab);
+  const uint32_t n = *a.count;
+  const int lane = threadIdx.x & 31;
+  const int l = lane & 7;
+  const uint32_t warp_group = ((blockIdx.x * kListBlock + threadIdx.x) >> 5) * GROUPS;
+  const uint32_t mine = (uint32_t)(lane >> 3);
+  const uint32_t ngroups = (gridDim.x * kListBlock >> 5) * GROUPS;
+  const uint32_t step = PER * ngroups;
+  const uint32_t P = (uint32_t)a.g.P, Z = (uint32_t)a.g.sz, safe = (uint32_t)a.g.off0;
+  uint32_t next[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t i = warp_group + mine + u * ngroups;
+    next[u] = i < n ? a.list[i] : 0u;
+  }
+  pdl_wait();
+  for (uint32_t wb = warp_group; wb < n; wb += step) {
+    uint32_t cur[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      cur[u] = next[u];
+      const uint32_t i = wb + step + mine + u * ngroups;
+      next[u] = i < n ? a.list[i] : 0u;
+    }
+    uint32_t at[PER];
+    bool ok[PER], plus[PER];
+    float2 oh[PER], ym[PER], yp[PER], zm[PER], zp[PER], bb[PER];
+    float edge[PER];
+    uint16_t cd[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t e = cur[u];
+      ok[u] = wb + mine + u * ngroups < n && entry_ok(a.g, e & kListAt, 9);
+      plus[u] = ok[u] && (e & kListPlusX) != 0;
+      at[u] = (ok[u] ? (e & kListAt) : safe) + 2u * (uint32_t)l;
+      oh[u] = *reinterpret_cast<const float2*>(a.other + at[u]);
+      ym[u] = *reinterpret_cast<const float2*>(a.other + (at[u] - P));
+      yp[u] = *reinterpret_cast<const float2*>(a.other + (at[u] + P));
+      zm[u] = *reinterpret_cast<const float2*>(a.other + (at[u] - Z));
+      zp[u] = *reinterpret_cast<const float2*>(a.other + (at[u] + Z));
+      bb[u] = *reinterpret_cast<const float2*>(a.rhs + at[u]);
+      cd[u] = *reinterpret_cast<const uint16_t*>(a.code + at[u]);
+      edge[u] = 0.f;
+      if (plus[u] ? l == 7 : l == 0) edge[u] = a.other[plus[u] ? at[u] + 2u : at[u] - 1u];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const float up = __shfl_up_sync(0xffffffffu, oh[u].y, 1, 8);    // o[at - 1]
+      const float dn = __shfl_down_sync(0xffffffffu, oh[u].x, 1, 8);  // o[at + 2]
+      // x-neighbours of the pair's two cells: dx = +1 (plus) or -1
+      const float x0 = plus[u] ? oh[u].y : (l == 0 ? edge[u] : up);
+      const float x1 = plus[u] ? (l == 7 ? edge[u] : dn) : oh[u].x;
+      const float s0 = ((oh[u].x + x0) + (ym[u].x + yp[u].x)) + (zm[u].x + zp[u].x);
+      const float s1 = ((oh[u].y + x1) + (ym[u].y + yp[u].y)) + (zm[u].y + zp[u].y);
+      const unsigned c0 = cd[u] & 0xffu, c1 = cd[u] >> 8;
+      const bool a0 = (c0 & kActive2) != 0, a1 = (c1 & kActive2) != 0;
+      const float v0 = (s0 - bb[u].x) * tab[__popc(c0 >> kGhostShift)];
+      const float v1 = (s1 - bb[u].y) * tab[__popc(c1 >> kGhostShift)];
+      if (!ok[u]) continue;
+      *reinterpret_cast<float2*>(a.self + at[u]) = make_float2(a0 ? v0 : 0.f, a1 ? v1 : 0.f);
+      if (UPDATE && (a0 || a1)) {
+        double2 ph = *reinterpret_cast<const double2*>(a.phi64 + at[u]);
+        if (a0) ph.x += widen_f32(v0);
+        if (a1) ph.y += widen_f32(v1);
+        *reinterpret_cast<double2*>(a.phi64 + at[u]) = ph;
+      }
+    }
+  }
+}
+
 // K9, first pass: the sum of r^2 per block into partials[blockIdx.x], r^ =
 // sum_nbr Phi_j - D Phi_i - b the scaled residual of the listed unknowns
 // (the grid is fixed per level, so the partials do not depend on scheduling).
@@ -506,20 +590,20 @@ __global__ void __launch_bounds__(kListBlock) prolong_list_kernel(ProlongArgs<T>
   entries(base);
   pdl_wait();
   for (; base < n; base += PER * stride) {
-    long long at[PER];
+    uint32_t at[PER];
     int cc[PER];
     T w[PER], old[PER];
     bool ok[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
+      // every entry's loads are issued; a missing entry reads around slot
+      // (0, 0, 0), whose coarse corners lie inside the arrays
       const uint32_t i = base + u * stride;
-      ok[u] = i < n;
-      if (!ok[u]) continue;
       const int c = i >= n0;
       cc[u] = c;
       at[u] = e[u] & kListAt;
-      ok[u] = entry_ok(gf, at[u], 6);
-      if (!ok[u]) continue;
+      ok[u] = i < n && entry_ok(gf, at[u], 6);
+      if (!ok[u]) at[u] = (uint32_t)gf.off0;
       int q, j, k;
       gf.slot_of(at[u], &q, &j, &k);
       w[u] = p2_sum(a.gc, a.cphi[0], a.cphi[1], q, j, k, c, PlainLoad());
@@ -785,6 +869,13 @@ cudaError_t half_sweep_seg(const LevelDev& L, int colour, bool update, cudaStrea
   a.phi64 = L.phi[colour];
   a.list = L.list[0][colour];
   a.count = L.count + colour;
+  if (SHIFT == 4 && L.seg_pairs) {  // 8 lanes per 16-slot segment: the grid of 8-slot segments
+    const int grid = seg_grid(L.hcount[colour], 3);
+    count_launch();
+    if (update) launch_pdl(gs_seg_pair_kernel<true>, dim3(grid), dim3(kListBlock), 0, s, a);
+    else launch_pdl(gs_seg_pair_kernel<false>, dim3(grid), dim3(kListBlock), 0, s, a);
+    return cudaGetLastError();
+  }
   const int grid = seg_grid(L.hcount[colour], SHIFT);
   count_launch();
   if (update)

@@ -181,7 +181,7 @@ bool valid_options(const mg_options& o) {
          o.hold_solves >= 0 && std::isfinite(o.eta) && o.eta > 0 && (o.order == 0 || o.order == 1 || o.order == 2) &&
          (o.precision == 0 || o.precision == 1) && o.inner_cycles >= 1 && o.inner_cycles <= 16 &&
          (o.coarse_cluster == 0 || o.coarse_cluster == 1) && (o.smoother_pass == 0 || o.smoother_pass == 1) &&
-         (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 1 &&
+         (o.fp64_sum == 0 || o.fp64_sum == 1) && o.fine_segments >= 0 && o.fine_segments <= kSegShiftMax - kSegShiftMin + 2 &&
          (o.coarse_matrix == 0 || o.coarse_matrix == 1);
 }
 
@@ -572,8 +572,6 @@ mg_status build_levels(mg_hierarchy* H, bool fine_built = false, const int8_t* m
     CKS(launch_ok(H, launch_mask_coarsen(H->L[l], l == 0 ? mask : nullptr, H->L[l + 1], s), "mask R1"));
     CKS(launch_ok(H, launch_coarse_coeffs(H->L[l + 1], H->counts + 2 * (l + 1), s), "coarse coefficients"));
   }
-  // FP32 copies of the coarse diagonals for the mixed form (one launch)
-  CKS(launch_ok(H, launch_to_f32_many(H->f32_jobs, H->n_f32_jobs, s), "fp32 copy"));
   // compact lists of the unknowns, per order and colour (level 0: one set),
   // all in three launches
   CKS(launch_ok(H, launch_build_lists(H->list_jobs, H->n_list_jobs, H->list_blocks, H->list_scratch, s),
@@ -698,7 +696,7 @@ void mg_default_options(mg_options* opt) {
   opt->coarse_cluster = 0;
   opt->smoother_pass = 0;
   opt->fp64_sum = 1;
-  opt->fine_segments = 1;
+  opt->fine_segments = 3;
   opt->coarse_matrix = 1;
 }
 
@@ -790,9 +788,10 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     size_t f_phi[2], f_rhs[2], f_invd[2], f_diag[2];
   } off[kMaxLevels];
   const bool mixed = o.precision == 1;
-  // fine_segments 1, 2: row segments of 8, 16 slots for the FP32 sweeps
+  // fine_segments 1, 2: row segments of 8, 16 slots for the FP32 sweeps;
+  // 3: 16-slot segments, two slots per lane
   const bool seg = mixed && o.fine_segments >= 1;
-  const int seg_shift = seg ? kSegShiftMin + o.fine_segments - 1 : 0;
+  const int seg_shift = seg ? (o.fine_segments >= 3 ? kSegShiftMax : kSegShiftMin + o.fine_segments - 1) : 0;
   for (int l = 0; l < H->nlev; ++l) {
     Geom g = make_geom(dims[l][0], dims[l][1], dims[l][2]);
     H->L[l].g = g;
@@ -842,11 +841,9 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   // one-CTA smoother's and a second FP32 correction buffer
   const bool pass = mixed && o.smoother_pass == 1 && !small_level(H->L[0].g) && H->nlev >= 2;
   const int n_zero = 4 * H->nlev + 4 + (mixed ? 2 * H->nlev : 0) + (pass ? 2 : 0);
-  const int n_f32 = mixed ? 4 * (H->nlev - 1) : 0;
   const size_t o_lscr = A.reserve(sizeof(uint32_t) * ((size_t)lblocks + 1));
   const size_t o_ljobs = A.reserve(sizeof(ListJob) * ljobs.size());
   const size_t o_zjobs = A.reserve(sizeof(ZeroJob) * n_zero);
-  const size_t o_fjobs = A.reserve(sizeof(F32Job) * (n_f32 > 0 ? n_f32 : 1));
   const Geom& g0 = H->L[0].g;
   size_t o_rhoh2[2], o_bc[2], o_save[2], o_rhsd[2] = {0, 0};
   for (int c = 0; c < 2; ++c) {
@@ -914,12 +911,12 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
   H->list_scratch = (uint32_t*)(base + o_lscr);
   H->list_jobs = (ListJob*)(base + o_ljobs);
   H->zero_jobs = (ZeroJob*)(base + o_zjobs);
-  H->f32_jobs = (F32Job*)(base + o_fjobs);
   H->list_blocks = lblocks;
   for (int l = 0; l < H->nlev; ++l) {
     H->L[l].rhsd[0] = H->L[l].rhsd[1] = nullptr;
     H->L[l].exact_sum = (l == 0 && o.fp64_sum == 1) ? 1 : 0;
     H->L[l].seg_shift = l == 0 ? seg_shift : 0;
+    H->L[l].seg_pairs = (l == 0 && seg && o.fine_segments >= 3) ? 1 : 0;
   }
   for (int c = 0; c < 2; ++c) {
     H->L[0].rhsd[c] = mixed ? nullptr : (double*)(base + o_rhsd[c]);
@@ -977,22 +974,12 @@ mg_status mg_create_hierarchy(const int8_t* mask, mg_mem where, int nx, int ny, 
     for (int c = 0; c < 2 && pass; ++c) zjobs.push_back({H->phi32_alt[c], g0.total / 2});
     for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.rhoh2[c], g0.total});
     for (int c = 0; c < 2; ++c) zjobs.push_back({H->F.bc[c], g0.total});  // last: skipped when already 0
-    std::vector<F32Job> fjobs;
-    for (int l = 1; mixed && l < H->nlev; ++l)
-      for (int c = 0; c < 2; ++c) {
-        fjobs.push_back({H->L[l].invd[c], H->L[l].invd32[c], H->L[l].g.total});
-        fjobs.push_back({H->L[l].diag[c], H->L[l].diag32[c], H->L[l].g.total});
-      }
     H->n_list_jobs = (int)ljobs.size();
     H->n_zero_jobs = (int)zjobs.size();
-    H->n_f32_jobs = (int)fjobs.size();
     cudaError_t ej = cudaMemcpyAsync(H->list_jobs, ljobs.data(), sizeof(ListJob) * ljobs.size(),
                                      cudaMemcpyHostToDevice, H->stream);
     if (ej == cudaSuccess)
       ej = cudaMemcpyAsync(H->zero_jobs, zjobs.data(), sizeof(ZeroJob) * zjobs.size(), cudaMemcpyHostToDevice,
-                           H->stream);
-    if (ej == cudaSuccess && !fjobs.empty())
-      ej = cudaMemcpyAsync(H->f32_jobs, fjobs.data(), sizeof(F32Job) * fjobs.size(), cudaMemcpyHostToDevice,
                            H->stream);
     if (ej == cudaSuccess) ej = cudaStreamSynchronize(H->stream);  // the host tables go out of scope
     if (ej != cudaSuccess) st = cuda_fail(H, ej, "job tables");

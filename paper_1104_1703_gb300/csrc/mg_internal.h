@@ -110,6 +110,7 @@ struct LevelDev {
   double* rhsd[2];     // level 0 of the FP64 method: b / D (nullptr elsewhere)
   int exact_sum = 0;   // level 0: FP64 neighbour sums in integer arithmetic (exact_sum.cuh)
   int seg_shift = 0;   // level 0: log2 of the row-segment length (0: no segment lists)
+  int seg_pairs = 0;   // level 0, 16-slot segments: two slots per lane (gs_seg_pair_kernel)
   // FP32 copies for the inner cycles of the mixed-precision form (nullptr
   // when the hierarchy was created for FP64 only); level 0: phi32 is the
   // correction e, rhs32 is -r^ of the FP64 residual.
@@ -193,19 +194,12 @@ __host__ __device__ inline long long list_job_chunks(const Geom& g) {
 }
 cudaError_t launch_build_lists(const ListJob* jobs, int njobs, unsigned total_blocks, uint32_t* scratch,
                                cudaStream_t s);
-// Buffers of `words` 8-byte words to zero, and FP64 -> FP32 copies, many
-// per launch.
+// Buffers of `words` 8-byte words to zero, many per launch.
 struct ZeroJob {
   void* ptr;
   long long words;
 };
-struct F32Job {
-  const double* src;
-  float* dst;
-  long long n;
-};
 cudaError_t launch_zero_many(const ZeroJob* jobs, int njobs, cudaStream_t s);
-cudaError_t launch_to_f32_many(const F32Job* jobs, int njobs, cudaStream_t s);
 
 // ---- data movement and boundary data (kernels_build.cu) ----
 // natural (nx*ny*nz) <-> split; `scale` multiplies, `mask_bit` zeroes cells

@@ -187,6 +187,26 @@ def test_prolongation_parity(dev, name, level, order):
     assert relerr(H.level_get(level, B.MG_FIELD_PHI), R.phi(level)) < TOL
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_prolongation_reaches_the_corner_cell(dev, order):
+    """Fine cell (0, 0, 0) active and corrected: its P2 corner three axis
+    steps away is coarse cell (-1, -1, -1), outside the box, worth 0."""
+    shape = (9, 10, 12)
+    w = {"mask": np.ones(shape, np.int8), "rho": W.random_field(shape, 501), "h": 0.1,
+         "faces": W.random_faces(shape, 502)}
+    H, R = make_pair(w, dev)
+    _level_state(w, H, R, 0, order, seed=503)
+    Sc = R.S(1)
+    ec = np.where(active_of(Sc, 1, order), W.random_field(Sc.shape, 504), 0.0)
+    H.level_set(1, B.MG_FIELD_PHI, ec)
+    R.set_level_phi(1, ec)
+    H.prolong_from(0, order)
+    R.prolong_from(0, order)
+    got, ref = H.level_get(0, B.MG_FIELD_PHI), R.phi(0)
+    assert relerr(got, ref) < TOL
+    assert abs(got[0, 0, 0] - ref[0, 0, 0]) <= TOL * np.abs(ref).max()
+
+
 # ---------------------------------------------------------------------------
 # Whole V-cycles and solves
 # ---------------------------------------------------------------------------

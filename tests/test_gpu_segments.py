@@ -1,4 +1,5 @@
-"""Level-0 sweeps by row segments of 8 and 16 slots (option fine_segments)
+"""Level-0 sweeps by row segments of 8 and 16 slots, one or two slots per
+thread (option fine_segments)
 against the per-cell compact lists, in the mixed form's FP32 cycles: the
 two visit the same cells with the same arithmetic, so whole solves and
 their residual histories are bit-identical.  Cases cover
@@ -41,7 +42,7 @@ ALL = dict(CASES, **extra_cases())
 def test_solves_bit_identical(dev, name, inner):
     w = ALL[name]
     res = []
-    for seg in (0, 1, 2):
+    for seg in (0, 1, 2, 3):
         H, _ = make_pair(w, dev, fine_segments=seg, precision=1, inner_cycles=inner)
         st, info = H.solve(1e-9, 100)
         assert st == 0
@@ -53,11 +54,12 @@ def test_solves_bit_identical(dev, name, inner):
         assert np.array_equal(s0.view(np.uint64), s1.view(np.uint64))
 
 
-def test_segment_lists_follow_a_mask_update(dev):
+@pytest.mark.parametrize("seg", [2, 3])
+def test_segment_lists_follow_a_mask_update(dev, seg):
     """After update_mask the segment lists are rebuilt: a solve on the new
     mask equals a fresh hierarchy's bit for bit."""
     a, b = ALL["blob48x32x40"], W.blob_patch((40, 32, 48), seed=105)
-    H, _ = make_pair(a, dev, fine_segments=2, precision=1)
+    H, _ = make_pair(a, dev, fine_segments=seg, precision=1)
     H.solve(1e-9, 100)
     H.update_mask(torch.from_numpy(b["mask"]).to(dev))
     H.set_rhs(torch.from_numpy(b["rho"]).to(dev))
