@@ -46,6 +46,27 @@ def test_default_options_are_the_papers():
                                                                                                 0.5, 0)
 
 
+def test_appended_option_defaults_and_ranges():
+    """The options appended after the paper's (precision and kernel
+    choices): their defaults, and every out-of-range value refused on the
+    host before any device work."""
+    o = B.mg_default_options()
+    assert (o.precision, o.inner_cycles, o.use_graphs, o.coarse_cluster, o.smoother_pass) == (0, 1, 1, 0, 0)
+    assert (o.fp64_sum, o.fine_segments, o.coarse_matrix) == (1, 3, 1)
+    lib = B.lib()
+    out = ctypes.c_void_p(123)
+    mask = np.ones((4, 4, 4), np.int8)
+    p = mask.ctypes.data_as(ctypes.c_void_p)
+    for field, value in [("fine_segments", -1), ("fine_segments", 4), ("coarse_matrix", 2), ("coarse_matrix", -1),
+                         ("fp64_sum", 2), ("inner_cycles", 0), ("inner_cycles", 17), ("smoother_pass", 2),
+                         ("n_cycles", 0), ("n_cycles", 5)]:
+        bad = B.mg_default_options()
+        setattr(bad, field, value)
+        assert lib.mg_create_hierarchy(p, 0, 4, 4, 4, 0.25, ctypes.byref(bad), None, ctypes.byref(out)) == \
+            B.MG_ERR_INVALID_ARG, (field, value)
+        assert "invalid options" in B.mg_last_error()
+
+
 def test_invalid_arguments_rejected_on_host():
     lib = B.lib()
     out = ctypes.c_void_p(123)
